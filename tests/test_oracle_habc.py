@@ -1,0 +1,148 @@
+"""Pins of the Pade coefficients, the edge / corner algebra and LSERK4."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import habc
+from oracle.mesh import dof_count
+from oracle.solver import LSERK_A, LSERK_B, LSERK_C
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ Pade
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 6, 8])
+def test_pade_two_representations_agree(P):
+    X = np.linspace(-0.95, 5.0, 101)
+    assert np.allclose(habc.pade_sqrt(X, P), habc.pade_sqrt_ab(X, P), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_pade_matches_taylor_to_order_2P(P):
+    # f_P(X) - sqrt(1+X) = O(X^(2P+1)): halving X divides the error by 2^(2P+1)
+    e1 = abs(habc.pade_sqrt(0.1, P) - math.sqrt(1.1))
+    e2 = abs(habc.pade_sqrt(0.05, P) - math.sqrt(1.05))
+    order = math.log2(e1 / e2)
+    assert order > 2 * P + 0.5
+
+
+@pytest.mark.parametrize("P", [0, 1, 2, 3, 5])
+def test_plane_wave_reflection_closed_form(P):
+    """Continuous HABC reflection for a plane wave at incidence theta:
+    R = |cos - f_P(-sin^2)| / (cos + f_P(-sin^2)) = tan(theta/2)^(2(2P+1))."""
+    th = np.linspace(0.05, 1.5, 30)
+    f = habc.pade_sqrt(-np.sin(th) ** 2, P) if P else np.ones_like(th)
+    R = np.abs(np.cos(th) - f) / (np.cos(th) + f)
+    assert np.allclose(R, np.tan(th / 2) ** (2 * (2 * P + 1)), rtol=1e-10, atol=1e-15)
+
+
+# ------------------------------------------------------------------ edge system
+@pytest.mark.parametrize("P", [1, 2, 3, 6])
+def test_edge_matrix_block_structure(P):
+    """The matrix has the form [[D, E], [E, D]] with D diagonal,
+    D_a = M + sum_b c_a c_b / (1 + c_a + c_b), E_ab = -c_b (1+c_a)/(1+c_a+c_b)
+    (derived by substituting r^- + r^+ = p_ab into eqs. proc:edgeBC1-2)."""
+    c, M = habc.pade_coefficients(P)
+    A = habc.edge_matrix(c, M) * M
+    ca, cb = c[:, None], c[None, :]
+    D = np.diag(M + (ca * cb / (1 + ca + cb)).sum(1))
+    E = -cb * (1 + ca) / (1 + ca + cb)
+    assert np.allclose(A, np.block([[D, E], [E, D]]), atol=1e-12)
+
+
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_edge_solution_satisfies_integrated_bcs(P):
+    """Plug the solution into the first-order BCs of Sec. 2.3 written with
+    p and rho c v (eqs. HABCsyst:BClev2a-b) and the time-integrated 1D relation
+    (eq. HABCsyst:GovLev2):  (1+c_a+c_b) p_ab - (1+c_b) p_A,a - (1+c_a) p_B,b
+    = (1+c_a+c_b) p*_ab,  p - rho c v = 2 r^-."""
+    c, M = habc.pade_coefficients(P)
+    rng = np.random.default_rng(7)
+    n = 5
+    rpA, rpB, ps = rng.standard_normal((n, P)), rng.standard_normal((n, P)), rng.standard_normal((n, P, P))
+    rmA, rmB = habc.edge_solve(rpA, rpB, ps, c, M)
+    for i in range(n):
+        pA, pB = rmA[i] + rpA[i], rmB[i] + rpB[i]          # fluxed 2D pressures at the edge
+        zvA, zvB = rpA[i] - rmA[i], rpB[i] - rmB[i]          # rho c v of the 2D fields
+        pab = np.empty((P, P))
+        for a in range(P):
+            for b in range(P):
+                pab[a, b] = ((1 + c[a] + c[b]) * ps[i, a, b] + (1 + c[b]) * pA[a] + (1 + c[a]) * pB[b]) / (1 + c[a] + c[b])
+        for a in range(P):   # L^y p_i00 = 0 on the edge, face A sets
+            assert abs((pA[a] - zvA[a]) - (2.0 / M) * sum(c[b] * (pab[a, b] - pA[a]) for b in range(P))) < 1e-12
+        for b in range(P):   # L^x p_0j0 = 0 on the edge, face B sets
+            assert abs((pB[b] - zvB[b]) - (2.0 / M) * sum(c[a] * (pab[a, b] - pB[b]) for a in range(P))) < 1e-12
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_corner_solution_satisfies_integrated_bcs(P):
+    """Corner: build p_ijk from the 0D relation (eq. lev3:ijkCorner) and check
+    the integrated corner BCs (eqs. bc3:1-3):  p - rho c u = (2/M) sum c (p_ijk - p)."""
+    c, M = habc.pade_coefficients(P)
+    rng = np.random.default_rng(11)
+    rYZ, rXZ, rXY = (rng.standard_normal(P * P) for _ in range(3))
+    xYZ, xXZ, xXY = habc.corner_solve(rYZ, rXZ, rXY, c, M)
+    p0jk = (xYZ + rYZ).reshape(P, P)
+    pi0k = (xXZ + rXZ).reshape(P, P)
+    pij0 = (xXY + rXY).reshape(P, P)
+    zu = [(rYZ - xYZ).reshape(P, P), (rXZ - xXZ).reshape(P, P), (rXY - xXY).reshape(P, P)]
+    pijk = np.empty((P, P, P))
+    for i in range(P):
+        for j in range(P):
+            for k in range(P):
+                pijk[i, j, k] = ((1 + c[i]) * p0jk[j, k] + (1 + c[j]) * pi0k[i, k] + (1 + c[k]) * pij0[i, j]) / (1 + c[i] + c[j] + c[k])
+    for j in range(P):
+        for k in range(P):
+            assert abs(p0jk[j, k] - zu[0][j, k] - (2 / M) * sum(c[i] * (pijk[i, j, k] - p0jk[j, k]) for i in range(P))) < 1e-12
+    for i in range(P):
+        for k in range(P):
+            assert abs(pi0k[i, k] - zu[1][i, k] - (2 / M) * sum(c[j] * (pijk[i, j, k] - pi0k[i, k]) for j in range(P))) < 1e-12
+    for i in range(P):
+        for j in range(P):
+            assert abs(pij0[i, j] - zu[2][i, j] - (2 / M) * sum(c[k] * (pijk[i, j, k] - pij0[i, j]) for k in range(P))) < 1e-12
+
+
+# ------------------------------------------------------------------ LSERK4
+def test_lserk_stability_polynomial():
+    """s <- a s + dt*lam*y, y <- y + b s on y' = lam y: the amplification
+    factor is 1 + z + z^2/2 + z^3/6 + z^4/24 + z^5/200 (z = lam dt)."""
+    P = np.polynomial.Polynomial
+    y, s = P([1.0]), P([0.0])
+    z = P([0.0, 1.0])
+    for a, b in zip(LSERK_A, LSERK_B):
+        s = a * s + z * y
+        y = y + b * s
+    assert np.allclose(y.coef, [1, 1, 1 / 2, 1 / 6, 1 / 24, 1 / 200], atol=1e-14)
+
+
+def test_lserk_stage_times_and_order():
+    # y' = f(t) integrates t^3 exactly and stages see the right times
+    for deg in range(4):
+        y, s, t, dt = 0.0, 0.0, 0.3, 0.1
+        for a, b, c in zip(LSERK_A, LSERK_B, LSERK_C):
+            s = a * s + dt * (t + c * dt) ** deg
+            y = y + b * s
+        exact = ((t + dt) ** (deg + 1) - t ** (deg + 1)) / (deg + 1)
+        assert abs(y - exact) < 1e-15
+    # temporal order 4 on y' = -y + cos(t)
+    def run(nsteps):
+        y, t, dt = 1.0, 0.0, 1.0 / nsteps
+        s = 0.0
+        for _ in range(nsteps):
+            for a, b, c in zip(LSERK_A, LSERK_B, LSERK_C):
+                s = a * s + dt * (-y + math.cos(t + c * dt))
+                y = y + b * s
+            t += dt
+        return y
+    exact = 0.5 * (math.cos(1.0) + math.sin(1.0)) + 0.5 * math.exp(-1.0)
+    e1, e2 = abs(run(10) - exact), abs(run(20) - exact)
+    assert math.log2(e1 / e2) > 3.8
+
+
+# ------------------------------------------------------------------ Table 3
+def test_dof_count_matches_table3():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table3_dofs.txt")) if l.strip() and not l.startswith("#")]
+    for P, Ktet, Ktri, Klin, N, total in (map(int, r) for r in rows):
+        assert dof_count(Ktet, Ktri, Klin, N, P) == total
