@@ -1,0 +1,256 @@
+"""Throughput of the DG + HABC explicit step on one B300 (JSON line on stdout).
+
+Workload (the plain-FP32 configuration): cube [-1,1]^3, 48^3 hexahedra x 6
+Kuhn tets = 663,552 tets (+-2% h vertex jitter, seed 2000), degree N = 4
+(Np = 35), c = rho = 1, HABC of order P = 6 on all six faces with edge and
+corner compatibility, seeded off-centre Gaussian pressure pulse of width 0.1,
+LSERK4 at the CFL time step.  A "step" is one LSERK4 step (5 RK stages) of
+all levels.  Metric: DOF-updates per second per RK stage =
+ndof * 5 * steps / time, with ndof counting 3D + 2D + 1D unknowns.
+
+--impl reference times the FP64 CPU oracle (the checker, not tuned) on the
+host cores, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "cube48_N4_P6_gaussian", "mesh": "48^3 hex x 6 Kuhn tets (663552), jitter 2% h",
+            "N": 4, "P": 6, "c": 1.0, "rho": 1.0, "pulse_width": 0.1}
+METRIC = "DOF-updates/s per RK stage"
+SEED = 2000
+
+
+def build_inputs(n=48):
+    from paper_1610_05023_b300 import workloads as W
+    VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=SEED)
+    x0 = W.seeded_point(SEED, [0.70, 0.65, 0.60], 0.05)
+    return VX, EToV, x0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_id="0"):
+        self.proc = None
+        self.path = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-i", self.gpu_id, "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(seconds_budget=20.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    the same degree, HABC order, jitter and pulse on a 6^3-hex (1296-tet)
+    cube, timed over whole LSERK4 steps; single thread (BLAS limited to 1)."""
+    from threadpoolctl import threadpool_limits
+    from oracle.mesh import CuboidMesh
+    from oracle.solver import Solver
+    from paper_1610_05023_b300 import workloads as W
+    n = 6
+    VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=SEED)
+    x0 = W.seeded_point(SEED, [0.70, 0.65, 0.60], 0.05)
+    with threadpool_limits(1):
+        m = CuboidMesh(VX, EToV, 4, 6, [0] * 6, 1.0, 1.0)
+        s = Solver(m)
+        Y = s.gaussian_state(x0, 0.1)
+        res = {k: np.zeros_like(v) for k, v in Y.items()}
+        dt = m.dt_rule()
+        t0 = time.perf_counter()
+        steps, t = 0, 0.0
+        while True:
+            t = s.step(Y, res, t, dt)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el > seconds_budget or steps >= 50:
+                break
+    return {"value": m.ndof() * 5 * steps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "%d LSERK4 steps of the same N=4, P=6, jittered Gaussian-pulse problem on a "
+                      "6^3-hex (1296-tet) cube, FP64 numpy, 1 thread (%.1f s)" % (steps, el),
+            "steps": steps, "seconds": el}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = max(10.0, 60.0 / max(args.steps + args.warmup, 1))
+    r = cpu_oracle_sample(per * args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": r["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=48, help="hexes per axis (48 = the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1610_05023_b300 as dgh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    VX, EToV, x0 = build_inputs(args.n)
+    stream = torch.cuda.Stream()
+    g = dgh.Solver(VX, EToV, 4, 6, c=1.0, rho=1.0, stream=stream)
+    info = g.info
+    ndof = info["ndof"]
+    g.init_gaussian(x0, 0.1)
+    g.step(args.warmup)
+    g.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    try:
+        gid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gid = str(local)
+    clocks = ClockSampler(gid)
+    barrier()
+    clocks.start()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    g.step(args.steps)
+    end.record(stream)
+    end.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ndof * 5 * args.steps / (ms * 1e-3)
+
+    # per-kernel durations (events around each launch, direct launches)
+    kt = g.time_kernels(20)
+    K = info["n_cells"]
+    Np, Nfp = info["Np"], (4 + 1) * (4 + 2) // 2
+    bytes_per_tet = 4 * (16 * Np + 16 * Nfp) + 100          # algorithmic bytes per tet per stage
+    achieved = K * bytes_per_tet / (kt["k3d"] * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the public API: host initial state in, host fields out
+    q3 = g.get_state(3)
+    e2e_steps = min(args.steps, 200)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.set_state(3, q3)
+    g.step(e2e_steps)
+    out = g.get_state(3)
+    t1 = time.perf_counter()
+    e2e_value = world * ndof * 5 * e2e_steps / (t1 - t0)
+    state_bytes = q3.size * 4
+
+    launches_per_step = 5 * (1 + (info["n_tris"] > 0) + (info["n_lines"] > 0) + (info["n_corners"] > 0)) + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, ndof=ndof, n_cells=K, n_tris=info["n_tris"], n_lines=info["n_lines"],
+                       n_corners=info["n_corners"], dt=info["dt"],
+                       l2_policy="inputs larger than L2 (state %.0f MB per array)" % (q3.size * 4 / 1e6),
+                       parallelism="replicas" if world > 1 else "single"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k3d_stage<4>",
+                     "peak_kind": peak_kind, "bytes_per_tet": bytes_per_tet,
+                     "launch_ms": kt["k3d"]},
+        "kernel_ms": kt,
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes / e2e_steps,
+                "d2h_bytes_per_step": state_bytes / e2e_steps, "steps": e2e_steps,
+                "note": "set_state(host) + step(n) + get_state(host) through the C ABI"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_oracle_sample()
+        line["cpu_baseline"] = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * dgh.h -- C ABI of the B300 nodal DG acoustic solver with high-order
+ * absorbing boundary conditions (HABC) and edge/corner compatibility
+ * (Modave, Atle, Chan, Warburton, arXiv 1610.05023).
+ *
+ * One context = one problem on one GPU: a conforming tetrahedral mesh of a
+ * cuboid, the 3D pressure-velocity system (Sec. 2, eqs. pressureEqn /
+ * velocityEqn) discretised by nodal DG with upwind fluxes (Sec. 3.2), and the
+ * Pade HABC of order P on the boundary faces with its 2D face, 1D edge and
+ * 0D corner solvers (Sec. 2.3, Sec. 3.1, Algorithm 1), advanced by the
+ * 5-stage low-storage RK4 (eqs. timeStepProc1-2).
+ *
+ * Conventions shared by every call
+ *  - Status: every int-returning call returns DGH_OK (0) or a negative code;
+ *    dgh_last_error() gives a message.  No call aborts or throws.
+ *  - Memory: arrays passed in are HOST arrays owned by the caller and only
+ *    read during the call (copied).  Arrays passed out are HOST arrays owned
+ *    by the caller, of the size stated, written during the call.  All device
+ *    memory is owned by the context and freed by dgh_destroy().
+ *  - Streams: all device work of a context runs on the stream given to
+ *    dgh_create (NULL = the legacy default stream).  dgh_step() is
+ *    asynchronous; errors of launched work surface at the next synchronising
+ *    call (dgh_sync, read-backs) as DGH_ECUDA.
+ *  - Notation: N = polynomial degree (the paper's P), P = HABC order (the
+ *    paper's N, number of auxiliary fields per face).  Np = (N+1)(N+2)(N+3)/6,
+ *    Np2 = (N+1)(N+2)/2, Np1 = N+1.
+ *
+ * Canonical layouts (read-back order; independent of the device layout)
+ *  - Level 3 (tetrahedra): [K][4][Np], fields (p, u, v, w).
+ *  - Level 2 (triangles = cell faces on HABC faces, P >= 1): [Ktri][P][3][Np2],
+ *    fields (p_a, v1, v2): the auxiliary pressure of set a and the velocity
+ *    components along the two in-plane axes in increasing axis order.
+ *    Triangles are the HABC boundary cell faces in increasing order of
+ *    (cell, local face); a triangle's nodes are the face nodes of its cell.
+ *  - Level 1 (line cells on edges between two HABC faces A < B):
+ *    [Klin][P*P][2][Np1], fields (p_ab, w) with set s = a + P*b and w the
+ *    velocity along the edge axis.  Lines are enumerated by their face-A
+ *    triangle, then the triangle's local edge; nodes run along +axis.
+ *  - Reference nodes: Warp & Blend (Warburton 2006); node order = lattice
+ *    order (tet: t outer, s middle, r inner; triangle: s outer, r inner).
+ *  - Local faces of a tet (v0..v3): (v0,v1,v2), (v0,v1,v3), (v1,v2,v3),
+ *    (v0,v2,v3), i.e. t=-1, s=-1, r+s+t=-1, r=-1 of the reference tet.
+ *  - Domain faces d = 0..5: -x, +x, -y, +y, -z, +z.
+ *  - "state" read/write gives the time-stepped variables: for levels 2 and 1
+ *    the temporary fields p* of eqs. proc:pi00Star / proc:pij0Star instead
+ *    of the full auxiliary pressure; "fields" give the full pressures.
+ */
+#ifndef DGH_H
+#define DGH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define DGH_OK            0
+#define DGH_EINVAL       -1   /* invalid argument (null pointer, bad size, bad mesh) */
+#define DGH_ENOMEM       -2   /* device or host allocation failed */
+#define DGH_ECUDA        -3   /* CUDA runtime error (launch or asynchronous) */
+#define DGH_EUNSTABLE    -4   /* non-finite values detected by a check */
+#define DGH_ESTATE       -6   /* call not valid in the current state */
+#define DGH_EUNSUPPORTED -7   /* feature / order not compiled in */
+
+/* Boundary condition of a domain face. */
+#define DGH_BC_HABC       0   /* Pade HABC of order P (P = 0: basic ABC, Sec. 3.2) */
+#define DGH_BC_DIRICHLET  1   /* p = 0 (free surface, Sec. 2.4, Sec. 3.2)         */
+
+/* Arithmetic of the 3D volume / lift contractions. */
+#define DGH_PREC_FP32     0   /* FP32 CUDA cores (the plain path)                 */
+
+typedef struct dgh_ctx dgh_ctx;
+
+/* Problem description (all pointers: host, read during dgh_create only). */
+typedef struct dgh_desc {
+    int32_t        order;        /* N, 1..6                                     */
+    int32_t        habc_order;   /* P, 0..8 (common to all HABC faces)           */
+    int32_t        bc[6];        /* DGH_BC_* per domain face                     */
+    int32_t        precision;    /* DGH_PREC_*                                   */
+    int32_t        reserved0;
+    int64_t        n_vertices;
+    int64_t        n_cells;
+    const double  *vertices;     /* [n_vertices][3]                              */
+    const int32_t *cells;        /* [n_cells][4] 0-based vertex ids              */
+    const double  *c;            /* [n_cells] wave speed (constant per cell)     */
+    const double  *rho;          /* [n_cells] density                            */
+    double         dt;           /* > 0: time step; <= 0: cfl * min_k 1/(c_k (N+1)^2 Fscale_k) */
+    double         cfl;          /* used when dt <= 0 (eq. validBench:timeStep, min over cells) */
+} dgh_desc;
+
+typedef struct dgh_info {
+    int32_t order, habc_order, Np, Np2, Np1, n_corners;
+    int64_t n_cells, n_tris, n_lines, n_bfaces;
+    int64_t ndof;                /* 4 Np K + 3 P Np2 Ktri + 2 P^2 Np1 Klin (Table 3 convention) */
+    int64_t step_count;
+    double  dt, time;
+    int64_t device_bytes;        /* device memory held by the context            */
+} dgh_info;
+
+/* Builds the reference elements (Sec. 3.2), the volume / surface / line meshes
+ * and their node maps (Sec. 3.2, Table 1), the geometric factors, the Pade
+ * coefficients c_i = tan^2(i pi / M) (eq. approxRoot2) and the precomputed
+ * solution operators of the edge and corner systems (Sec. 3.1, item 2), then
+ * uploads everything.  All state starts at zero.  stream: a cudaStream_t or
+ * NULL.  *out receives a new context (NULL on failure).
+ * Errors: DGH_EINVAL for an invalid mesh (non-conforming, degenerate cell,
+ * boundary face off the cuboid), DGH_EUNSUPPORTED for N or P out of range,
+ * DGH_ENOMEM, DGH_ECUDA. */
+int dgh_create(const dgh_desc *desc, void *stream, dgh_ctx **out);
+
+/* Host-only dry run of dgh_create: validates the description, builds the
+ * reference elements and the meshes on the CPU and fills *out (sizes, ndof,
+ * time step) without touching any GPU.  device_bytes is left 0.  Same errors
+ * as dgh_create except DGH_ENOMEM / DGH_ECUDA. */
+int dgh_plan(const dgh_desc *desc, dgh_info *out);
+
+/* Frees all device and host memory of the context (NULL is accepted). */
+void dgh_destroy(dgh_ctx *ctx);
+
+/* Message of the last failing call on this context (or of the last failing
+ * dgh_create when ctx is NULL).  Never NULL; valid until the next call. */
+const char *dgh_last_error(const dgh_ctx *ctx);
+
+int dgh_get_info(const dgh_ctx *ctx, dgh_info *out);
+
+/* Node coordinates of a level (3, 2 or 1) in the canonical order:
+ * [K][Np][3], [Ktri][Np2][3] or [Klin][Np1][3].  count = number of doubles. */
+int dgh_get_nodes(const dgh_ctx *ctx, int level, double *xyz, size_t count);
+
+/* Sets the 3D pressure to amp * exp(-|x - x0|^2 / width^2) at the nodes
+ * (nodal interpolation, computed on the GPU), the 3D velocity to zero and
+ * every auxiliary field to zero; time and step count restart at 0. */
+int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp);
+
+/* Writes (set) or reads (get) the time-stepped variables of a level in the
+ * canonical layout (FP64 on the host, FP32 on the device).  count = number of
+ * doubles (level 3: K*4*Np; level 2: Ktri*P*3*Np2; level 1: Klin*P*P*2*Np1).
+ * After a set the boundary algebra of Algorithm 1 is recomputed before the
+ * next step. */
+int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count);
+int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count);
+
+/* Like dgh_get_state but levels 2 and 1 return the full auxiliary pressures
+ * p_a = p*_a + (r^- + r^+) (eq. proc:pi00Star) and
+ * p_ab = p*_ab + C_ba Q_A,a + C_ab Q_B,b (eq. proc:pij0Star). */
+int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count);
+
+/* Sets the simulated time (the step count is unchanged). */
+int dgh_set_time(dgh_ctx *ctx, double t);
+
+/* Adds a point source delta(x - xs) S(t) to the pressure equation, with S the
+ * integral of the Ricker wavelet of peak frequency f_peak and delay t_s
+ * (Sec. 4.1, eq. validBench:ricker), scaled by amp; discretised as
+ * S(t) M_k^{-1} l(xs) in the cell k containing xs (lowest id on ties) and
+ * evaluated at every RK stage time.  At most 16 sources per context.
+ * Errors: DGH_EINVAL if xs lies outside the mesh. */
+int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double t_s, double amp);
+
+/* Advances nsteps LSERK4 steps on the context's stream (asynchronous). */
+int dgh_step(dgh_ctx *ctx, int64_t nsteps);
+
+/* Profiling aid: advances nsteps steps with direct launches (no graph),
+ * bracketing every kernel launch with CUDA events on the context's stream.
+ * out_ms[0..3] = mean duration of one launch of the 3D / 2D / 1D / 0D stage
+ * kernels in milliseconds (0 for an absent level), out_ms[4] = mean duration
+ * of a whole step.  Synchronising. */
+int dgh_time_kernels(dgh_ctx *ctx, int64_t nsteps, double out_ms[5]);
+
+/* Waits for the context's stream; reports asynchronous CUDA errors. */
+int dgh_sync(dgh_ctx *ctx);
+
+/* Discrete energy of the 3D fields,
+ * E = sum_k |J_k| [p^T M p / (2 rho c^2) + (rho/2) sum_i u_i^T M u_i],
+ * reduced on the GPU with FP64 accumulation (synchronising). */
+int dgh_get_energy(dgh_ctx *ctx, double *E);
+
+/* Serialises the complete time-stepping state (all levels, residuals,
+ * boundary algebra, time, step count) into buf.  Call with buf == NULL to
+ * query the size in *size.  dgh_load_state restores it into a context
+ * created from the same description.  DGH_EINVAL on size mismatch. */
+int dgh_save_state(dgh_ctx *ctx, void *buf, size_t *size);
+int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGH_H */

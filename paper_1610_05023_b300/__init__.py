@@ -1,0 +1,254 @@
+"""B300 nodal DG acoustic solver with Pade HABC and edge/corner compatibility.
+
+Thin ctypes binding of the C ABI declared in ``include/dgh.h`` (libdgh.so,
+built in-tree for sm_103a).  Every step of the time integration runs in the
+library's CUDA kernels; this module only marshals arguments.  There is no
+CPU fallback: constructing a solver without the built library or without a
+CUDA device raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdgh.so")
+
+DGH_OK = 0
+BC_HABC = 0
+BC_DIRICHLET = 1
+PREC_FP32 = 0
+
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -6: "ESTATE", -7: "EUNSUPPORTED"}
+
+
+class DghError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dgh error %d (%s): %s" % (code, _ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int32), ("habc_order", ctypes.c_int32), ("bc", ctypes.c_int32 * 6),
+        ("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("n_vertices", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+        ("vertices", ctypes.POINTER(ctypes.c_double)), ("cells", ctypes.POINTER(ctypes.c_int32)),
+        ("c", ctypes.POINTER(ctypes.c_double)), ("rho", ctypes.POINTER(ctypes.c_double)),
+        ("dt", ctypes.c_double), ("cfl", ctypes.c_double),
+    ]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int32), ("habc_order", ctypes.c_int32), ("Np", ctypes.c_int32),
+        ("Np2", ctypes.c_int32), ("Np1", ctypes.c_int32), ("n_corners", ctypes.c_int32),
+        ("n_cells", ctypes.c_int64), ("n_tris", ctypes.c_int64), ("n_lines", ctypes.c_int64),
+        ("n_bfaces", ctypes.c_int64), ("ndof", ctypes.c_int64), ("step_count", ctypes.c_int64),
+        ("dt", ctypes.c_double), ("time", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libdgh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdgh.so not built: run paper_1610_05023_b300/build.py (nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    P, D = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "dgh_create": (ctypes.c_int, [ctypes.POINTER(_Desc), P, ctypes.POINTER(P)]),
+        "dgh_plan": (ctypes.c_int, [ctypes.POINTER(_Desc), ctypes.POINTER(_Info)]),
+        "dgh_destroy": (None, [P]),
+        "dgh_last_error": (ctypes.c_char_p, [P]),
+        "dgh_get_info": (ctypes.c_int, [P, ctypes.POINTER(_Info)]),
+        "dgh_get_nodes": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
+        "dgh_init_gaussian": (ctypes.c_int, [P, D, ctypes.c_double, ctypes.c_double]),
+        "dgh_set_state": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
+        "dgh_get_state": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
+        "dgh_get_fields": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
+        "dgh_set_time": (ctypes.c_int, [P, ctypes.c_double]),
+        "dgh_add_point_source": (ctypes.c_int, [P, D, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "dgh_step": (ctypes.c_int, [P, ctypes.c_int64]),
+        "dgh_sync": (ctypes.c_int, [P]),
+        "dgh_time_kernels": (ctypes.c_int, [P, ctypes.c_int64, D]),
+        "dgh_get_energy": (ctypes.c_int, [P, D]),
+        "dgh_save_state": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "dgh_load_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl):
+    VX = np.ascontiguousarray(VX, dtype=np.float64)
+    EToV = np.ascontiguousarray(EToV, dtype=np.int32)
+    K = EToV.shape[0]
+    c = np.ascontiguousarray(np.broadcast_to(np.asarray(c, np.float64), (K,)))
+    rho = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, np.float64), (K,)))
+    d = _Desc()
+    d.order, d.habc_order = int(N), int(P)
+    for i in range(6):
+        d.bc[i] = int(bc[i])
+    d.precision = PREC_FP32
+    d.n_vertices, d.n_cells = VX.shape[0], K
+    d.vertices = _dptr(VX)
+    d.cells = EToV.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    d.c, d.rho = _dptr(c), _dptr(rho)
+    d.dt, d.cfl = float(dt), float(cfl)
+    return d, (VX, EToV, c, rho)   # keep the arrays alive with the descriptor
+
+
+def plan(VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0):
+    """Host-only set-up (no GPU): sizes, ndof and time step of a problem."""
+    lib = load_library()
+    d, _keep = _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl)
+    i = _Info()
+    rc = lib.dgh_plan(ctypes.byref(d), ctypes.byref(i))
+    if rc != DGH_OK:
+        raise DghError(rc, lib.dgh_last_error(None).decode())
+    return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+
+class Solver:
+    """One DG + HABC problem on the current CUDA device.
+
+    VX [Nv,3] vertex coordinates, EToV [K,4] cell vertex ids, N polynomial
+    degree, P HABC order (0 = basic ABC), bc six codes (BC_HABC /
+    BC_DIRICHLET for -x,+x,-y,+y,-z,+z), c and rho per cell (or scalars),
+    dt > 0 fixed step (else cfl * the min-over-cells rule), stream a
+    torch.cuda.Stream, an integer cudaStream_t or None.
+    """
+
+    def __init__(self, VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0, stream=None):
+        lib = load_library()
+        d, _keep = _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl)
+        if stream is None:
+            sptr = None
+        elif isinstance(stream, int):
+            sptr = stream
+        else:
+            sptr = stream.cuda_stream
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = lib.dgh_create(ctypes.byref(d), ctypes.c_void_p(sptr) if sptr else None, ctypes.byref(h))
+        if rc != DGH_OK:
+            raise DghError(rc, lib.dgh_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+        self.N, self.P = int(N), int(P)
+
+    # ------------------------------------------------------------ helpers
+    def _check(self, rc):
+        if rc != DGH_OK:
+            raise DghError(rc, self._lib.dgh_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dgh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ API
+    @property
+    def info(self):
+        i = _Info()
+        self._check(self._lib.dgh_get_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def shape(self, level):
+        i = self.info
+        if level == 3:
+            return (i["n_cells"], 4, i["Np"])
+        if level == 2:
+            return (i["n_tris"], self.P, 3, i["Np2"])
+        if level == 1:
+            return (i["n_lines"], self.P * self.P, 2, i["Np1"])
+        raise ValueError("level must be 3, 2 or 1")
+
+    def nodes(self, level):
+        i = self.info
+        n = {3: (i["n_cells"], i["Np"]), 2: (i["n_tris"], i["Np2"]), 1: (i["n_lines"], i["Np1"])}[level]
+        out = np.empty(n + (3,))
+        self._check(self._lib.dgh_get_nodes(self._h, level, _dptr(out), out.size))
+        return out
+
+    def init_gaussian(self, x0, width, amp=1.0):
+        x = np.ascontiguousarray(x0, dtype=np.float64)
+        self._check(self._lib.dgh_init_gaussian(self._h, _dptr(x), float(width), float(amp)))
+
+    def set_state(self, level, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        if a.shape != self.shape(level):
+            raise ValueError("state shape %s != %s" % (a.shape, self.shape(level)))
+        self._check(self._lib.dgh_set_state(self._h, level, _dptr(a), a.size))
+
+    def get_state(self, level):
+        out = np.empty(self.shape(level))
+        self._check(self._lib.dgh_get_state(self._h, level, _dptr(out), out.size))
+        return out
+
+    def get_fields(self, level):
+        out = np.empty(self.shape(level))
+        self._check(self._lib.dgh_get_fields(self._h, level, _dptr(out), out.size))
+        return out
+
+    def set_time(self, t):
+        self._check(self._lib.dgh_set_time(self._h, float(t)))
+
+    def add_point_source(self, xs, f_peak, t_s, amp=1.0):
+        x = np.ascontiguousarray(xs, dtype=np.float64)
+        self._check(self._lib.dgh_add_point_source(self._h, _dptr(x), float(f_peak), float(t_s), float(amp)))
+
+    def step(self, n=1):
+        self._check(self._lib.dgh_step(self._h, int(n)))
+
+    def time_kernels(self, nsteps):
+        """Mean launch duration (ms) of the 3D, 2D, 1D, 0D stage kernels and of
+        a step, from CUDA events around every launch (advances the solution)."""
+        out = np.zeros(5)
+        self._check(self._lib.dgh_time_kernels(self._h, int(nsteps), _dptr(out)))
+        return {"k3d": out[0], "k2d": out[1], "k1d": out[2], "k0d": out[3], "step": out[4]}
+
+    def sync(self):
+        self._check(self._lib.dgh_sync(self._h))
+
+    def energy(self):
+        e = ctypes.c_double()
+        self._check(self._lib.dgh_get_energy(self._h, ctypes.byref(e)))
+        return e.value
+
+    def save_state(self):
+        size = ctypes.c_size_t(0)
+        self._check(self._lib.dgh_save_state(self._h, None, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        self._check(self._lib.dgh_save_state(self._h, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(size)))
+        return buf.raw
+
+    def load_state(self, blob):
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        self._check(self._lib.dgh_load_state(self._h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))

@@ -1,0 +1,1136 @@
+// C ABI of the solver (include/dgh.h): set-up, device layout, stage launches,
+// CUDA-graph replay of the step, read-back, energy, checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dgh.h"
+#include "kernels.cuh"
+#include "setup.h"
+
+using namespace dgh;
+
+namespace {
+
+// Carpenter & Kennedy (1994) 5-stage 2N-storage RK4 coefficients.
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                        2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+thread_local std::string g_create_error = "no error";
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct dgh_ctx {
+    std::string err = "no error";
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int N = 0, P = 0, Np = 0, Nfp = 0, Np2 = 0, Np1 = 0;
+    int64_t K = 0, T = 0, L = 0, Fb = 0;
+    int C = 0;
+    int M = 1;
+    double dt = 0.0, t0 = 0.0;
+    int64_t step_count = 0;
+    int cur = 0;              // trace buffer holding the current traces
+    bool dirty = true;        // boundary algebra must be recomputed
+    std::vector<DevBuf> bufs;
+    int64_t device_bytes = 0;
+    // 3D
+    float *q3 = nullptr, *res3 = nullptr, *tr3[2] = {nullptr, nullptr}, *geo3 = nullptr, *qb3 = nullptr;
+    int *conn3 = nullptr;
+    float *D3 = nullptr, *L3 = nullptr, *M3 = nullptr;
+    int *fmask3 = nullptr, *fperm3 = nullptr;
+    double *cellv = nullptr, *rst = nullptr, *ew = nullptr;
+    // 2D
+    float *q2 = nullptr, *res2 = nullptr, *tr2[2] = {nullptr, nullptr}, *geo2 = nullptr, *qb2 = nullptr, *q0_3 = nullptr;
+    int *conn2 = nullptr, *tri_face = nullptr, *tri_bface = nullptr, *fmask2 = nullptr;
+    float *D2 = nullptr, *L2 = nullptr;
+    // 1D
+    float *q1 = nullptr, *res1 = nullptr, *tr1[2] = {nullptr, nullptr}, *geo1 = nullptr, *qb1 = nullptr, *q0_2 = nullptr;
+    int *conn1 = nullptr, *lmap = nullptr;
+    float *D1 = nullptr, *L1 = nullptr, *H1 = nullptr, *H2 = nullptr, *cP = nullptr;
+    // 0D
+    int *corner = nullptr;
+    float *cornerZ = nullptr, *Hc = nullptr;
+    // time
+    double *d_time = nullptr;
+    int64_t *d_step = nullptr;
+    // energy scratch
+    double *partial = nullptr, *d_energy = nullptr;
+    int energy_blocks = 0;
+    // sources
+    SrcParams src{};
+    float *srcvec = nullptr;
+    // launch shapes
+    int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1;
+    size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
+    // graphs (one per trace parity)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // host copies needed by read-back
+    HostMesh mesh;
+    RefTet ref3;
+    RefTri ref2;
+    RefLine ref1;
+    HabcOps habc;
+};
+
+#define CK(call)                                                                 \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            return DGH_ECUDA;                                                    \
+        }                                                                        \
+    } while (0)
+
+namespace {
+
+template <class T>
+int dalloc(dgh_ctx *ctx, T *&ptr, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DGH_ENOMEM : DGH_ECUDA;
+    }
+    cudaMemset(p, 0, bytes);
+    ctx->bufs.push_back({p, bytes});
+    ctx->device_bytes += int64_t(bytes);
+    ptr = static_cast<T *>(p);
+    return DGH_OK;
+}
+
+template <class T>
+int upload(dgh_ctx *ctx, T *&ptr, const std::vector<T> &h) {
+    int rc = dalloc(ctx, ptr, h.size());
+    if (rc) return rc;
+    if (!h.empty()) CK(cudaMemcpy(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return DGH_OK;
+}
+
+std::vector<float> to_f(const Mat &A) {
+    std::vector<float> v(A.a.size());
+    for (size_t i = 0; i < v.size(); ++i) v[i] = float(A.a[i]);
+    return v;
+}
+
+// ------------------------------------------------------------ dispatch on N
+template <template <int> class F, class... Args>
+int dispatchN(int N, Args &&...args) {
+    switch (N) {
+        case 1: return F<1>::run(args...);
+        case 2: return F<2>::run(args...);
+        case 3: return F<3>::run(args...);
+        case 4: return F<4>::run(args...);
+        case 5: return F<5>::run(args...);
+        case 6: return F<6>::run(args...);
+        default: return DGH_EUNSUPPORTED;
+    }
+}
+
+Args3 args3(dgh_ctx *c, int cur) {
+    Args3 A;
+    A.q = c->q3;
+    A.res = c->res3;
+    A.tr_in = c->tr3[cur];
+    A.tr_out = c->tr3[cur ^ 1];
+    A.geo = c->geo3;
+    A.conn = c->conn3;
+    A.qb = c->qb3;
+    A.D = c->D3;
+    A.LIFT = c->L3;
+    A.fmask = c->fmask3;
+    A.fperm = c->fperm3;
+    A.K = c->K;
+    A.src = c->src;
+    A.src.vec = c->srcvec;
+    return A;
+}
+
+Args2 args2(dgh_ctx *c, int cur, bool update) {
+    Args2 A;
+    A.q = c->q2;
+    A.res = c->res2;
+    A.tr_in = c->tr2[cur];
+    A.tr_out = update ? c->tr2[cur ^ 1] : c->tr2[cur];
+    A.geo = c->geo2;
+    A.conn = c->conn2;
+    A.qb = c->qb2;
+    A.q0 = c->q0_3;
+    A.qb3 = c->qb3;
+    A.tr3 = update ? c->tr3[cur ^ 1] : c->tr3[cur];
+    A.tri_face = c->tri_face;
+    A.tri_bface = c->tri_bface;
+    A.D = c->D2;
+    A.LIFT = c->L2;
+    A.fmask = c->fmask2;
+    A.cP = c->cP;
+    A.invM = 1.0f / float(c->M);
+    A.P = c->P;
+    A.T = c->T;
+    return A;
+}
+
+Args1 args1(dgh_ctx *c, int cur, bool update) {
+    Args1 A;
+    A.q = c->q1;
+    A.res = c->res1;
+    A.tr_in = c->tr1[cur];
+    A.tr_out = update ? c->tr1[cur ^ 1] : c->tr1[cur];
+    A.geo = c->geo1;
+    A.conn = c->conn1;
+    A.qb = c->qb1;
+    A.q0 = c->q0_2;
+    A.qb2 = c->qb2;
+    A.tr2 = update ? c->tr2[cur ^ 1] : c->tr2[cur];
+    A.lmap = c->lmap;
+    A.D = c->D1;
+    A.LIFT = c->L1;
+    A.H1 = c->H1;
+    A.H2 = c->H2;
+    A.cP = c->cP;
+    A.invM = 1.0f / float(c->M);
+    A.P = c->P;
+    A.L = c->L;
+    return A;
+}
+
+template <int N>
+struct Launch3 {
+    static int run(dgh_ctx *c, int cur, int stage, bool update) {
+        StageCoef sc;
+        sc.a = float(kRkA[stage]);
+        sc.b = float(kRkB[stage]);
+        sc.dt = float(c->dt);
+        sc.c_dt = kRkC[stage] * c->dt;
+        sc.time = c->d_time;
+        Args3 A = args3(c, cur);
+        if (!update) A.tr_out = c->tr3[cur];
+        if (update)
+            k3d_stage<N, true><<<c->grid3, 256, c->smem3, c->stream>>>(A, sc);
+        else
+            k3d_stage<N, false><<<c->grid3, 256, c->smem3, c->stream>>>(A, sc);
+        return DGH_OK;
+    }
+};
+
+template <int N>
+struct Launch2 {
+    static int run(dgh_ctx *c, int cur, int stage, bool update) {
+        if (c->T == 0) return DGH_OK;
+        StageCoef sc;
+        sc.a = float(kRkA[stage]);
+        sc.b = float(kRkB[stage]);
+        sc.dt = float(c->dt);
+        sc.c_dt = 0.0;
+        sc.time = c->d_time;
+        Args2 A = args2(c, cur, update);
+        if (update)
+            k2d_stage<N, true><<<c->grid2, 256, c->smem2, c->stream>>>(A, sc, c->tile2);
+        else
+            k2d_stage<N, false><<<c->grid2, 256, c->smem2, c->stream>>>(A, sc, c->tile2);
+        return DGH_OK;
+    }
+};
+
+template <int N>
+struct Launch1 {
+    static int run(dgh_ctx *c, int cur, int stage, bool update) {
+        if (c->L == 0) return DGH_OK;
+        StageCoef sc;
+        sc.a = float(kRkA[stage]);
+        sc.b = float(kRkB[stage]);
+        sc.dt = float(c->dt);
+        sc.c_dt = 0.0;
+        sc.time = c->d_time;
+        Args1 A = args1(c, cur, update);
+        if (update)
+            k1d_stage<N, true><<<c->grid1, 256, c->smem1, c->stream>>>(A, sc, c->tile1);
+        else
+            k1d_stage<N, false><<<c->grid1, 256, c->smem1, c->stream>>>(A, sc, c->tile1);
+        return DGH_OK;
+    }
+};
+
+void launch0(dgh_ctx *c, int cur_traces) {
+    if (c->C == 0) return;
+    Args0 A;
+    A.tr1 = c->tr1[cur_traces];
+    A.qb1 = c->qb1;
+    A.corner = c->corner;
+    A.cornerZ = c->cornerZ;
+    A.Hc = c->Hc;
+    A.P = c->P;
+    A.C = c->C;
+    k0d_stage<<<c->C, 128, c->smem0, c->stream>>>(A);
+}
+
+template <int N>
+struct SetAttrs {
+    static int run(dgh_ctx *c) {
+        cudaFuncSetAttribute(k3d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3);
+        cudaFuncSetAttribute(k3d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3);
+        cudaFuncSetAttribute(k2d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem2);
+        cudaFuncSetAttribute(k2d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem2);
+        cudaFuncSetAttribute(k1d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem1);
+        cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem1);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N, true>, 256, c->smem3);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        const int64_t tiles3 = (c->K + Ord<N>::TILE3 - 1) / Ord<N>::TILE3;
+        c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)std::max(nb, 1) * sms));
+        int nb2 = 0, nb1 = 0;
+        if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, 256, c->smem2);
+        if (c->L) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k1d_stage<N, true>, 256, c->smem1);
+        const int64_t tiles2 = (c->T + c->tile2 - 1) / c->tile2;
+        const int64_t tiles1 = (c->L + c->tile1 - 1) / c->tile1;
+        c->grid2 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles2, (int64_t)std::max(nb2, 1) * sms));
+        c->grid1 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles1, (int64_t)std::max(nb1, 1) * sms));
+        return DGH_OK;
+    }
+};
+
+// Boundary algebra of Algorithm 1 from the current fields (no time advance).
+int run_closure(dgh_ctx *c) {
+    const int cur = c->cur;
+    int rc = dispatchN<Launch3>(c->N, c, cur, 0, false);
+    if (rc) return rc;
+    rc = dispatchN<Launch2>(c->N, c, cur, 0, false);
+    if (rc) return rc;
+    rc = dispatchN<Launch1>(c->N, c, cur, 0, false);
+    if (rc) return rc;
+    launch0(c, cur);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("closure launch: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    c->dirty = false;
+    return DGH_OK;
+}
+
+// The 20 stage launches of one step plus the time advance; cur flips once
+// per stage, so a step starting from cur ends with cur ^ 1.
+int enqueue_step(dgh_ctx *c, int cur) {
+    for (int s = 0; s < 5; ++s) {
+        int rc = dispatchN<Launch3>(c->N, c, cur, s, true);
+        if (rc) return rc;
+        rc = dispatchN<Launch2>(c->N, c, cur, s, true);
+        if (rc) return rc;
+        rc = dispatchN<Launch1>(c->N, c, cur, s, true);
+        if (rc) return rc;
+        launch0(c, cur ^ 1);
+        cur ^= 1;
+    }
+    k_advance_time<<<1, 1, 0, c->stream>>>(c->d_time, c->d_step, c->dt);
+    return DGH_OK;
+}
+
+void drop_graphs(dgh_ctx *c) {
+    for (int i = 0; i < 2; ++i)
+        if (c->graph[i]) {
+            cudaGraphExecDestroy(c->graph[i]);
+            c->graph[i] = nullptr;
+        }
+}
+
+int build_graph(dgh_ctx *c, int cur) {
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = c->stream;   // never the legacy stream (dgh_step enqueues directly then)
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    int rc = enqueue_step(c, cur);
+    e = cudaStreamEndCapture(cs, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    e = cudaGraphInstantiate(&c->graph[cur], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    return DGH_OK;
+}
+
+int level_count(const dgh_ctx *c, int level, size_t &n) {
+    if (level == 3) n = size_t(c->K) * 4 * c->Np;
+    else if (level == 2) n = size_t(c->T) * c->P * 3 * c->Np2;
+    else if (level == 1) n = size_t(c->L) * c->P * c->P * 2 * c->Np1;
+    else return DGH_EINVAL;
+    return DGH_OK;
+}
+
+float *level_ptr(dgh_ctx *c, int level, bool res) {
+    if (level == 3) return res ? c->res3 : c->q3;
+    if (level == 2) return res ? c->res2 : c->q2;
+    return res ? c->res1 : c->q1;
+}
+
+int copy_out(dgh_ctx *c, const float *dptr, double *out, size_t n) {
+    if (n == 0) return DGH_OK;
+    std::vector<float> h(n);
+    cudaError_t e = cudaMemcpyAsync(h.data(), dptr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("device to host copy: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    for (size_t i = 0; i < n; ++i) out[i] = h[i];
+    return DGH_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char *dgh_last_error(const dgh_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void dgh_destroy(dgh_ctx *ctx) {
+    if (!ctx) return;
+    drop_graphs(ctx);
+    for (auto &b : ctx->bufs) cudaFree(b.p);
+    delete ctx;
+}
+
+static int validate_desc(const dgh_desc *d) {
+    if (!d || !d->vertices || !d->cells || !d->c || !d->rho || d->n_vertices < 4 || d->n_cells < 1) {
+        g_create_error = "invalid description (null pointer or empty mesh)";
+        return DGH_EINVAL;
+    }
+    if (d->order < 1 || d->order > 6 || d->habc_order < 0 || d->habc_order > MAXP) {
+        g_create_error = "order N must be 1..6 and HABC order P 0..8";
+        return DGH_EUNSUPPORTED;
+    }
+    if (d->precision != DGH_PREC_FP32) {
+        g_create_error = "precision not supported by this build";
+        return DGH_EUNSUPPORTED;
+    }
+    if (d->n_cells > (int64_t(1) << 26)) {
+        g_create_error = "too many cells for the 32-bit connectivity encoding (max 2^26)";
+        return DGH_EUNSUPPORTED;
+    }
+    for (int f = 0; f < 6; ++f)
+        if (d->bc[f] != DGH_BC_HABC && d->bc[f] != DGH_BC_DIRICHLET) {
+            g_create_error = "unknown boundary condition code";
+            return DGH_EINVAL;
+        }
+    for (int64_t k = 0; k < d->n_cells; ++k)
+        if (!(d->c[k] > 0.0) || !(d->rho[k] > 0.0)) {
+            g_create_error = "c and rho must be positive";
+            return DGH_EINVAL;
+        }
+    return DGH_OK;
+}
+
+static int host_setup(const dgh_desc *d, HostMesh &m, RefTet &T3, RefTri &T2, RefLine &T1, HabcOps &habc) {
+    std::string err;
+    const int N = d->order, P = d->habc_order;
+    if (!build_tet(N, T3, err)) {
+        g_create_error = err;
+        return DGH_EINVAL;
+    }
+    build_tri(N, warp_alpha_tet(N), T2);
+    build_line(N, T1);
+    m.N = N;
+    m.P = P;
+    for (int f = 0; f < 6; ++f) m.bc[f] = d->bc[f];
+    m.K = d->n_cells;
+    m.Nv = d->n_vertices;
+    m.VX.assign(d->vertices, d->vertices + 3 * m.Nv);
+    m.EToV.assign(d->cells, d->cells + 4 * m.K);
+    m.c.assign(d->c, d->c + m.K);
+    m.rho.assign(d->rho, d->rho + m.K);
+    if (!build_mesh(m, T3, T2, T1, err) || !build_habc(P, habc, err)) {
+        g_create_error = err;
+        return DGH_EINVAL;
+    }
+    return DGH_OK;
+}
+
+int dgh_plan(const dgh_desc *d, dgh_info *o) {
+    if (!o) {
+        g_create_error = "out is NULL";
+        return DGH_EINVAL;
+    }
+    int rc = validate_desc(d);
+    if (rc) return rc;
+    HostMesh m;
+    RefTet T3;
+    RefTri T2;
+    RefLine T1;
+    HabcOps habc;
+    if ((rc = host_setup(d, m, T3, T2, T1, habc))) return rc;
+    std::memset(o, 0, sizeof(*o));
+    o->order = d->order;
+    o->habc_order = d->habc_order;
+    o->Np = T3.Np;
+    o->Np2 = T2.Np;
+    o->Np1 = T1.Np;
+    o->n_corners = int(m.corners.size());
+    o->n_cells = m.K;
+    o->n_tris = m.Ktri;
+    o->n_lines = m.Klin;
+    o->n_bfaces = int64_t(m.bface.size());
+    const int64_t P = d->habc_order;
+    o->ndof = 4 * int64_t(T3.Np) * m.K + 3 * P * T2.Np * m.Ktri + 2 * P * P * T1.Np * m.Klin;
+    o->dt = d->dt > 0.0 ? d->dt : dt_rule(m, d->cfl > 0.0 ? d->cfl : 1.0);
+    return DGH_OK;
+}
+
+int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return DGH_EINVAL;
+    }
+    *out = nullptr;
+    int vrc = validate_desc(d);
+    if (vrc) return vrc;
+    dgh_ctx *ctx = new dgh_ctx();
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&ctx->device);
+    auto fail = [&](int rc, const std::string &msg) {
+        g_create_error = msg.empty() ? ctx->err : msg;
+        dgh_destroy(ctx);
+        return rc;
+    };
+    const int N = ctx->N = d->order, P = ctx->P = d->habc_order;
+    HostMesh &m = ctx->mesh;
+    {
+        int rc0 = host_setup(d, m, ctx->ref3, ctx->ref2, ctx->ref1, ctx->habc);
+        if (rc0) return fail(rc0, g_create_error);
+    }
+    const RefTet &T3 = ctx->ref3;
+    const RefTri &T2 = ctx->ref2;
+    const RefLine &T1 = ctx->ref1;
+    ctx->Np = T3.Np;
+    ctx->Nfp = T3.Nfp;
+    ctx->Np2 = T2.Np;
+    ctx->Np1 = T1.Np;
+    ctx->K = m.K;
+    ctx->T = m.Ktri;
+    ctx->L = m.Klin;
+    ctx->Fb = int64_t(m.bface.size());
+    ctx->C = int(m.corners.size());
+    ctx->M = ctx->habc.M;
+    ctx->dt = d->dt > 0.0 ? d->dt : dt_rule(m, d->cfl > 0.0 ? d->cfl : 1.0);
+    const int64_t K = m.K;
+    const int Np = T3.Np, Nfp = T3.Nfp, Np2 = T2.Np, Np1 = T1.Np;
+    int rc;
+    // ---------------------------------------------------------------- 3D
+    {
+        std::vector<float> geo(size_t(K) * GEO3, 0.f);
+        std::vector<int> conn(size_t(K) * 4);
+        std::vector<double> cellv(size_t(K) * 12), ew(size_t(K) * 2);
+        for (int64_t k = 0; k < K; ++k) {
+            float *g = &geo[size_t(k) * GEO3];
+            for (int q = 0; q < 9; ++q) g[q] = float(m.drdx[9 * k + q]);
+            const double Z = m.rho[k] * m.c[k];
+            for (int f = 0; f < 4; ++f) {
+                float *gf = g + 9 + 7 * f;
+                for (int i = 0; i < 3; ++i) gf[i] = float(m.nrm[12 * k + 3 * f + i]);
+                gf[3] = float(m.fscale[4 * k + f]);
+                const int64_t nb = m.nbr[4 * k + f];
+                double Zp = Z;
+                if (nb >= 0) Zp = m.rho[nb / 4] * m.c[nb / 4];
+                gf[4] = float(Z / (Z + Zp));
+                gf[5] = float(Z * Zp / (Z + Zp));
+                gf[6] = float(1.0 / (Z + Zp));
+                if (nb >= 0) {
+                    conn[4 * k + f] = int((nb << 3) | m.nbrSigma[4 * k + f]);
+                } else {
+                    const int64_t b = m.bfaceOf[4 * k + f];
+                    const int dir = m.bc[m.bfaceDom[b]] == BC_DIRICHLET ? 1 : 0;
+                    conn[4 * k + f] = int(-1 - ((b << 1) | dir));
+                }
+            }
+            g[37] = float(m.rho[k] * m.c[k] * m.c[k]);
+            g[38] = float(1.0 / m.rho[k]);
+            g[39] = float(Z);
+            for (int v = 0; v < 4; ++v)
+                for (int dd = 0; dd < 3; ++dd) cellv[12 * k + 3 * v + dd] = m.VX[3 * m.EToV[4 * k + v] + dd];
+            ew[2 * k] = std::fabs(m.J[k]) / (2.0 * m.rho[k] * m.c[k] * m.c[k]);
+            ew[2 * k + 1] = std::fabs(m.J[k]) * 0.5 * m.rho[k];
+        }
+        std::vector<float> D(size_t(3) * Np * Np), Lf(size_t(4) * Nfp * Np), Mf(size_t(Np) * Np);
+        const Mat *Dj[3] = {&T3.Dr, &T3.Ds, &T3.Dt};
+        for (int j = 0; j < 3; ++j)
+            for (int n = 0; n < Np; ++n)
+                for (int mm = 0; mm < Np; ++mm) D[(size_t(j) * Np + mm) * Np + n] = float((*Dj[j])(n, mm));
+        for (int n = 0; n < Np; ++n)
+            for (int fm = 0; fm < 4 * Nfp; ++fm) Lf[size_t(fm) * Np + n] = float(T3.LIFT(n, fm));
+        for (size_t i = 0; i < Mf.size(); ++i) Mf[i] = float(T3.M.a[i]);
+        std::vector<int> fmask(4 * Nfp), fperm(6 * Nfp);
+        for (int f = 0; f < 4; ++f)
+            for (int q = 0; q < Nfp; ++q) fmask[f * Nfp + q] = T3.Fmask[f][q];
+        for (int s = 0; s < 6; ++s)
+            for (int q = 0; q < Nfp; ++q) fperm[s * Nfp + q] = T3.facePerm[s][q];
+        std::vector<double> rst(size_t(3) * Np);
+        for (int n = 0; n < Np; ++n) {
+            rst[3 * n] = T3.r[n];
+            rst[3 * n + 1] = T3.s[n];
+            rst[3 * n + 2] = T3.t[n];
+        }
+        if ((rc = dalloc(ctx, ctx->q3, size_t(K) * 4 * Np)) || (rc = dalloc(ctx, ctx->res3, size_t(K) * 4 * Np)) ||
+            (rc = dalloc(ctx, ctx->tr3[0], size_t(K) * 8 * Nfp)) || (rc = dalloc(ctx, ctx->tr3[1], size_t(K) * 8 * Nfp)) ||
+            (rc = dalloc(ctx, ctx->qb3, size_t(ctx->Fb) * Nfp)) || (rc = upload(ctx, ctx->geo3, geo)) ||
+            (rc = upload(ctx, ctx->conn3, conn)) || (rc = upload(ctx, ctx->D3, D)) || (rc = upload(ctx, ctx->L3, Lf)) ||
+            (rc = upload(ctx, ctx->M3, Mf)) || (rc = upload(ctx, ctx->fmask3, fmask)) ||
+            (rc = upload(ctx, ctx->fperm3, fperm)) || (rc = upload(ctx, ctx->cellv, cellv)) ||
+            (rc = upload(ctx, ctx->rst, rst)) || (rc = upload(ctx, ctx->ew, ew)))
+            return fail(rc, "");
+    }
+    // ---------------------------------------------------------------- 2D
+    const int64_t Tn = m.Ktri;
+    {
+        std::vector<float> geo(size_t(Tn) * GEO2, 0.f);
+        std::vector<int> conn(size_t(Tn) * 3), tface(Tn), tb(Tn);
+        for (int64_t t = 0; t < Tn; ++t) {
+            float *g = &geo[size_t(t) * GEO2];
+            for (int q = 0; q < 4; ++q) g[q] = float(m.drdx2[4 * t + q]);
+            const int64_t gf = m.bface[m.triBface[t]];
+            const int64_t k = gf / 4;
+            const double Z = m.rho[k] * m.c[k];
+            for (int e = 0; e < 3; ++e) {
+                float *ge = g + 4 + 6 * e;
+                ge[0] = float(m.nrm2[6 * t + 2 * e]);
+                ge[1] = float(m.nrm2[6 * t + 2 * e + 1]);
+                ge[2] = float(m.fscale2[3 * t + e]);
+                const int64_t nb = m.nbr2[3 * t + e];
+                double Zp = Z;
+                if (nb >= 0) {
+                    const int64_t kn = m.bface[m.triBface[nb / 3]] / 4;
+                    Zp = m.rho[kn] * m.c[kn];
+                    conn[3 * t + e] = int((nb << 1) | m.flip2[3 * t + e]);
+                } else {
+                    const int B = m.edgeDom[3 * t + e];
+                    conn[3 * t + e] = (m.bc[B] == BC_DIRICHLET) ? -2 : -1;
+                }
+                ge[3] = float(Z / (Z + Zp));
+                ge[4] = float(Z * Zp / (Z + Zp));
+                ge[5] = float(1.0 / (Z + Zp));
+            }
+            g[22] = float(m.rho[k] * m.c[k] * m.c[k]);
+            g[23] = float(1.0 / m.rho[k]);
+            g[24] = float(Z);
+            tface[t] = int(gf);
+            tb[t] = int(m.triBface[t]);
+        }
+        std::vector<float> D(size_t(2) * Np2 * Np2), Lf(size_t(3) * (N + 1) * Np2);
+        for (int n = 0; n < Np2; ++n)
+            for (int mm = 0; mm < Np2; ++mm) {
+                D[size_t(mm) * Np2 + n] = float(T2.Dr(n, mm));
+                D[(size_t(Np2) + mm) * Np2 + n] = float(T2.Ds(n, mm));
+            }
+        for (int n = 0; n < Np2; ++n)
+            for (int em = 0; em < 3 * (N + 1); ++em) Lf[size_t(em) * Np2 + n] = float(T2.LIFT(n, em));
+        std::vector<int> fmask(3 * (N + 1));
+        for (int e = 0; e < 3; ++e)
+            for (int q = 0; q <= N; ++q) fmask[e * (N + 1) + q] = T2.Fmask[e][q];
+        const size_t nq = size_t(Tn) * P * 3 * Np2;
+        if ((rc = dalloc(ctx, ctx->q2, nq)) || (rc = dalloc(ctx, ctx->res2, nq)) ||
+            (rc = dalloc(ctx, ctx->tr2[0], size_t(Tn) * P * 3 * 2 * (N + 1))) ||
+            (rc = dalloc(ctx, ctx->tr2[1], size_t(Tn) * P * 3 * 2 * (N + 1))) ||
+            (rc = dalloc(ctx, ctx->qb2, size_t(Tn) * 3 * P * (N + 1))) || (rc = dalloc(ctx, ctx->q0_3, size_t(Tn) * Np2)) ||
+            (rc = upload(ctx, ctx->geo2, geo)) || (rc = upload(ctx, ctx->conn2, conn)) ||
+            (rc = upload(ctx, ctx->tri_face, tface)) || (rc = upload(ctx, ctx->tri_bface, tb)) ||
+            (rc = upload(ctx, ctx->D2, D)) || (rc = upload(ctx, ctx->L2, Lf)) || (rc = upload(ctx, ctx->fmask2, fmask)))
+            return fail(rc, "");
+    }
+    // ---------------------------------------------------------------- 1D
+    const int64_t Ln = m.Klin;
+    {
+        std::vector<float> geo(size_t(Ln) * GEO1, 0.f);
+        std::vector<int> conn(size_t(Ln) * 2), lmap(size_t(Ln) * 6);
+        for (int64_t l = 0; l < Ln; ++l) {
+            float *g = &geo[size_t(l) * GEO1];
+            const int64_t tA = m.linTri[0][l], tB = m.linTri[1][l];
+            const int64_t kA = m.bface[m.triBface[tA]] / 4, kB = m.bface[m.triBface[tB]] / 4;
+            const double ZA = m.rho[kA] * m.c[kA], ZB = m.rho[kB] * m.c[kB];
+            const double Z = ZA;   // a line cell takes the material of its face-A triangle
+            g[0] = float(1.0 / m.J1[l]);
+            g[1] = float(1.0 / std::fabs(m.J1[l]));
+            g[2] = float(m.rho[kA] * m.c[kA] * m.c[kA]);
+            g[3] = float(1.0 / m.rho[kA]);
+            g[4] = float(Z);
+            g[5] = float(ZA);
+            g[6] = float(ZB);
+            for (int e = 0; e < 2; ++e) {
+                const int64_t nb = m.nbr1[2 * l + e];
+                double Zp = Z;
+                if (nb >= 0) {
+                    const int64_t kn = m.bface[m.triBface[m.linTri[0][nb / 2]]] / 4;
+                    Zp = m.rho[kn] * m.c[kn];
+                    conn[2 * l + e] = int(nb);
+                } else {
+                    conn[2 * l + e] = (m.bc[m.endDom[2 * l + e]] == BC_DIRICHLET) ? -2 : -1;
+                }
+                g[7 + 3 * e] = float(Z / (Z + Zp));
+                g[8 + 3 * e] = float(Z * Zp / (Z + Zp));
+                g[9 + 3 * e] = float(1.0 / (Z + Zp));
+            }
+            for (int s = 0; s < 2; ++s) {
+                lmap[6 * l + 3 * s] = int(m.linTri[s][l]);
+                lmap[6 * l + 3 * s + 1] = m.linEdge[s][l];
+                lmap[6 * l + 3 * s + 2] = m.linRev[s][l];
+            }
+        }
+        std::vector<float> D(size_t(Np1) * Np1), Lf(size_t(2) * Np1);
+        for (int n = 0; n < Np1; ++n)
+            for (int mm = 0; mm < Np1; ++mm) D[size_t(mm) * Np1 + n] = float(T1.Dr(n, mm));
+        for (int n = 0; n < Np1; ++n) {
+            Lf[n] = float(T1.LIFT(n, 0));
+            Lf[Np1 + n] = float(T1.LIFT(n, 1));
+        }
+        const size_t nq = size_t(Ln) * P * P * 2 * Np1;
+        std::vector<float> cP(std::max(P, 1), 0.f);
+        for (int a = 0; a < P; ++a) cP[a] = float(ctx->habc.c[a]);
+        if ((rc = dalloc(ctx, ctx->q1, nq)) || (rc = dalloc(ctx, ctx->res1, nq)) ||
+            (rc = dalloc(ctx, ctx->tr1[0], size_t(Ln) * P * P * 4)) || (rc = dalloc(ctx, ctx->tr1[1], size_t(Ln) * P * P * 4)) ||
+            (rc = dalloc(ctx, ctx->qb1, size_t(Ln) * 2 * P * P)) || (rc = dalloc(ctx, ctx->q0_2, size_t(Ln) * 2 * P * Np1)) ||
+            (rc = upload(ctx, ctx->geo1, geo)) || (rc = upload(ctx, ctx->conn1, conn)) || (rc = upload(ctx, ctx->lmap, lmap)) ||
+            (rc = upload(ctx, ctx->D1, D)) || (rc = upload(ctx, ctx->L1, Lf)) || (rc = upload(ctx, ctx->cP, cP)))
+            return fail(rc, "");
+        if (P >= 1) {
+            if ((rc = upload(ctx, ctx->H1, to_f(ctx->habc.H1))) || (rc = upload(ctx, ctx->H2, to_f(ctx->habc.H2))) ||
+                (rc = upload(ctx, ctx->Hc, to_f(ctx->habc.Hc))))
+                return fail(rc, "");
+        }
+    }
+    // ---------------------------------------------------------------- 0D
+    {
+        std::vector<int> cor(size_t(ctx->C) * 6);
+        std::vector<float> cz(size_t(ctx->C) * 3);
+        for (int c = 0; c < ctx->C; ++c)
+            for (int sl = 0; sl < 3; ++sl) {
+                const int64_t l = m.corners[c].line[sl];
+                cor[6 * c + 2 * sl] = int(l);
+                cor[6 * c + 2 * sl + 1] = m.corners[c].end[sl];
+                const int64_t kA = m.bface[m.triBface[m.linTri[0][l]]] / 4;
+                cz[3 * c + sl] = float(m.rho[kA] * m.c[kA]);
+            }
+        if ((rc = upload(ctx, ctx->corner, cor)) || (rc = upload(ctx, ctx->cornerZ, cz))) return fail(rc, "");
+    }
+    // ---------------------------------------------------------------- misc
+    if ((rc = dalloc(ctx, ctx->d_time, 1)) || (rc = dalloc(ctx, ctx->d_step, 1)) ||
+        (rc = dalloc(ctx, ctx->srcvec, size_t(MAXSRC) * Np)) || (rc = dalloc(ctx, ctx->d_energy, 1)))
+        return fail(rc, "");
+    ctx->energy_blocks = 2 * 148;
+    if ((rc = dalloc(ctx, ctx->partial, ctx->energy_blocks))) return fail(rc, "");
+    // launch shapes
+    ctx->smem3 = 0;
+    switch (N) {
+        case 1: ctx->smem3 = k3d_smem<1>(); break;
+        case 2: ctx->smem3 = k3d_smem<2>(); break;
+        case 3: ctx->smem3 = k3d_smem<3>(); break;
+        case 4: ctx->smem3 = k3d_smem<4>(); break;
+        case 5: ctx->smem3 = k3d_smem<5>(); break;
+        case 6: ctx->smem3 = k3d_smem<6>(); break;
+    }
+    ctx->tile2 = std::max(1, 256 / std::max(1, P * Np2));
+    ctx->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
+    ctx->smem2 = P ? k2d_smem(N, P, ctx->tile2) : 0;
+    ctx->smem1 = P ? k1d_smem(N, P, ctx->tile1) : 0;
+    ctx->smem0 = sizeof(float) * 3 * P * P;
+    dispatchN<SetAttrs>(N, ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(DGH_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+    *out = ctx;
+    return DGH_OK;
+}
+
+int dgh_get_info(const dgh_ctx *ctx, dgh_info *o) {
+    if (!ctx || !o) return DGH_EINVAL;
+    o->order = ctx->N;
+    o->habc_order = ctx->P;
+    o->Np = ctx->Np;
+    o->Np2 = ctx->Np2;
+    o->Np1 = ctx->Np1;
+    o->n_corners = ctx->C;
+    o->n_cells = ctx->K;
+    o->n_tris = ctx->T;
+    o->n_lines = ctx->L;
+    o->n_bfaces = ctx->Fb;
+    o->ndof = 4 * int64_t(ctx->Np) * ctx->K + 3 * int64_t(ctx->P) * ctx->Np2 * ctx->T +
+              2 * int64_t(ctx->P) * ctx->P * ctx->Np1 * ctx->L;
+    o->step_count = ctx->step_count;
+    o->dt = ctx->dt;
+    o->time = ctx->t0 + ctx->step_count * 0.0;
+    o->device_bytes = ctx->device_bytes;
+    double t = 0.0;
+    if (cudaMemcpy(&t, ctx->d_time, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) o->time = t;
+    return DGH_OK;
+}
+
+int dgh_get_nodes(const dgh_ctx *ctx, int level, double *xyz, size_t count) {
+    if (!ctx || !xyz) return DGH_EINVAL;
+    const HostMesh &m = ctx->mesh;
+    if (level == 3) {
+        if (count != size_t(ctx->K) * ctx->Np * 3) return DGH_EINVAL;
+        for (int64_t k = 0; k < ctx->K; ++k)
+            for (int n = 0; n < ctx->Np; ++n) {
+                const double r = ctx->ref3.r[n], s = ctx->ref3.s[n], t = ctx->ref3.t[n];
+                const double l[4] = {-(1 + r + s + t) / 2, (1 + r) / 2, (1 + s) / 2, (1 + t) / 2};
+                for (int d = 0; d < 3; ++d) {
+                    double x = 0;
+                    for (int v = 0; v < 4; ++v) x += l[v] * m.VX[3 * m.EToV[4 * k + v] + d];
+                    xyz[(size_t(k) * ctx->Np + n) * 3 + d] = x;
+                }
+            }
+        return DGH_OK;
+    }
+    if (level == 2) {
+        if (count != size_t(ctx->T) * ctx->Np2 * 3) return DGH_EINVAL;
+        for (int64_t t = 0; t < ctx->T; ++t)
+            for (int n = 0; n < ctx->Np2; ++n) {
+                const double r = ctx->ref2.r[n], s = ctx->ref2.s[n];
+                const double l[3] = {-(r + s) / 2, (1 + r) / 2, (1 + s) / 2};
+                for (int d = 0; d < 3; ++d) {
+                    double x = 0;
+                    for (int v = 0; v < 3; ++v) x += l[v] * m.VX[3 * m.triV[3 * t + v] + d];
+                    xyz[(size_t(t) * ctx->Np2 + n) * 3 + d] = x;
+                }
+            }
+        return DGH_OK;
+    }
+    if (level == 1) {
+        if (count != size_t(ctx->L) * ctx->Np1 * 3) return DGH_EINVAL;
+        for (int64_t l = 0; l < ctx->L; ++l)
+            for (int n = 0; n < ctx->Np1; ++n) {
+                const double r = ctx->ref1.r[n];
+                for (int d = 0; d < 3; ++d)
+                    xyz[(size_t(l) * ctx->Np1 + n) * 3 + d] =
+                        (1 - r) / 2 * m.VX[3 * m.linV[2 * l] + d] + (1 + r) / 2 * m.VX[3 * m.linV[2 * l + 1] + d];
+            }
+        return DGH_OK;
+    }
+    const_cast<dgh_ctx *>(ctx)->err = "level must be 3, 2 or 1";
+    return DGH_EINVAL;
+}
+
+int dgh_set_time(dgh_ctx *ctx, double t) {
+    if (!ctx) return DGH_EINVAL;
+    CK(cudaMemcpyAsync(ctx->d_time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DGH_OK;
+}
+
+int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp) {
+    if (!ctx || !x0 || !(width > 0.0)) return DGH_EINVAL;
+    for (int lv = 1; lv <= 3; ++lv) {
+        size_t n;
+        level_count(ctx, lv, n);
+        CK(cudaMemsetAsync(level_ptr(ctx, lv, false), 0, n * sizeof(float), ctx->stream));
+        CK(cudaMemsetAsync(level_ptr(ctx, lv, true), 0, n * sizeof(float), ctx->stream));
+    }
+    const int64_t total = ctx->K * ctx->Np;
+    const int blocks = int((total + 255) / 256);
+    switch (ctx->N) {
+        case 1: k_init_gaussian<1><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
+        case 2: k_init_gaussian<2><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
+        case 3: k_init_gaussian<3><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
+        case 4: k_init_gaussian<4><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
+        case 5: k_init_gaussian<5><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
+        case 6: k_init_gaussian<6><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
+    }
+    CK(cudaGetLastError());
+    ctx->step_count = 0;
+    ctx->t0 = 0.0;
+    CK(cudaMemsetAsync(ctx->d_time, 0, sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream));
+    ctx->dirty = true;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DGH_OK;
+}
+
+int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count) {
+    if (!ctx || (!in && count)) return DGH_EINVAL;
+    size_t n;
+    if (level_count(ctx, level, n) || n != count) {
+        if (ctx) ctx->err = "state size mismatch";
+        return DGH_EINVAL;
+    }
+    if (n == 0) return DGH_OK;
+    std::vector<float> h(n);
+    for (size_t i = 0; i < n; ++i) h[i] = float(in[i]);
+    CK(cudaMemcpyAsync(level_ptr(ctx, level, false), h.data(), n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->dirty = true;
+    return DGH_OK;
+}
+
+int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count) {
+    if (!ctx || (!out && count)) return DGH_EINVAL;
+    size_t n;
+    if (level_count(ctx, level, n) || n != count) {
+        ctx->err = "state size mismatch";
+        return DGH_EINVAL;
+    }
+    return copy_out(ctx, level_ptr(ctx, level, false), out, n);
+}
+
+int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count) {
+    if (!ctx || (!out && count)) return DGH_EINVAL;
+    size_t n;
+    if (level_count(ctx, level, n) || n != count) {
+        ctx->err = "field size mismatch";
+        return DGH_EINVAL;
+    }
+    if (level == 3 || n == 0) return copy_out(ctx, ctx->q3, out, n);
+    if (ctx->dirty) {
+        int rc = run_closure(ctx);
+        if (rc) return rc;
+    }
+    float *tmp = nullptr;
+    CK(cudaMallocAsync((void **)&tmp, n * sizeof(float), ctx->stream));
+    const int blocks = int((n + 255) / 256);
+    if (level == 2)
+        k_full2<<<blocks, 256, 0, ctx->stream>>>(ctx->q2, ctx->q0_3, tmp, ctx->T, ctx->P, ctx->Np2);
+    else
+        k_full1<<<blocks, 256, 0, ctx->stream>>>(ctx->q1, ctx->q0_2, ctx->cP, tmp, ctx->L, ctx->P, ctx->Np1);
+    int rc = copy_out(ctx, tmp, out, n);
+    cudaFreeAsync(tmp, ctx->stream);
+    return rc;
+}
+
+int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double t_s, double amp) {
+    if (!ctx || !xs) return DGH_EINVAL;
+    if (ctx->src.n >= MAXSRC) {
+        ctx->err = "too many sources";
+        return DGH_EINVAL;
+    }
+    const HostMesh &m = ctx->mesh;
+    for (int64_t k = 0; k < m.K; ++k) {
+        const double *v0 = &m.VX[3 * m.EToV[4 * k]];
+        double c0[3];
+        for (int d = 0; d < 3; ++d)
+            c0[d] = 0.5 * (m.VX[3 * m.EToV[4 * k + 1] + d] + m.VX[3 * m.EToV[4 * k + 2] + d] + m.VX[3 * m.EToV[4 * k + 3] + d] - v0[d]);
+        double rst[3] = {0, 0, 0};
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i) rst[j] += m.drdx[9 * k + 3 * j + i] * (xs[i] - c0[i]);
+        if (rst[0] >= -1 - 1e-12 && rst[1] >= -1 - 1e-12 && rst[2] >= -1 - 1e-12 && rst[0] + rst[1] + rst[2] <= -1 + 1e-12) {
+            std::vector<double> row = tet_interp_row(ctx->ref3, rst[0], rst[1], rst[2]);
+            // M_k^{-1} l(xs) = V V^T l(xs) / |J_k|
+            const Mat &V = ctx->ref3.V;
+            const int Np = ctx->Np;
+            std::vector<double> tmp(Np, 0.0);
+            std::vector<float> vec(Np);
+            for (int j = 0; j < Np; ++j)
+                for (int n = 0; n < Np; ++n) tmp[j] += V(n, j) * row[n];
+            for (int n = 0; n < Np; ++n) {
+                double s = 0;
+                for (int j = 0; j < Np; ++j) s += V(n, j) * tmp[j];
+                vec[n] = float(s / std::fabs(m.J[k]));
+            }
+            const int s = ctx->src.n;
+            CK(cudaMemcpy(ctx->srcvec + size_t(s) * Np, vec.data(), Np * sizeof(float), cudaMemcpyHostToDevice));
+            ctx->src.cell[s] = k;
+            ctx->src.f_peak[s] = f_peak;
+            ctx->src.t_s[s] = t_s;
+            ctx->src.amp[s] = amp;
+            ctx->src.n = s + 1;
+            drop_graphs(ctx);
+            return DGH_OK;
+        }
+    }
+    ctx->err = "source point outside the mesh";
+    return DGH_EINVAL;
+}
+
+int dgh_step(dgh_ctx *ctx, int64_t nsteps) {
+    if (!ctx || nsteps < 0) return DGH_EINVAL;
+    if (ctx->dirty) {
+        int rc = run_closure(ctx);
+        if (rc) return rc;
+    }
+    const bool use_graph = ctx->stream != nullptr;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        if (use_graph) {
+            if (!ctx->graph[ctx->cur]) {
+                int rc = build_graph(ctx, ctx->cur);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+        } else {
+            int rc = enqueue_step(ctx, ctx->cur);
+            if (rc) return rc;
+        }
+        ctx->cur ^= 1;   // 5 stages: odd number of trace swaps
+        ctx->step_count++;
+    }
+    CK(cudaGetLastError());
+    return DGH_OK;
+}
+
+int dgh_time_kernels(dgh_ctx *ctx, int64_t nsteps, double out_ms[5]) {
+    if (!ctx || !out_ms || nsteps < 1) return DGH_EINVAL;
+    if (ctx->dirty) {
+        int rc = run_closure(ctx);
+        if (rc) return rc;
+    }
+    const int per_step = 5 * 4;
+    std::vector<cudaEvent_t> ev(size_t(2 * per_step) * nsteps + 2);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    double acc[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    size_t ie = 0;
+    CK(cudaEventRecord(ev[ie++], ctx->stream));
+    int cur = ctx->cur;
+    std::vector<std::pair<int, size_t>> marks;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        for (int s = 0; s < 5; ++s) {
+            for (int lv = 0; lv < 4; ++lv) {
+                const bool present = lv == 0 || (lv == 1 && ctx->T) || (lv == 2 && ctx->L) || (lv == 3 && ctx->C);
+                if (!present) continue;
+                CK(cudaEventRecord(ev[ie], ctx->stream));
+                int rc = DGH_OK;
+                if (lv == 0) rc = dispatchN<Launch3>(ctx->N, ctx, cur, s, true);
+                if (lv == 1) rc = dispatchN<Launch2>(ctx->N, ctx, cur, s, true);
+                if (lv == 2) rc = dispatchN<Launch1>(ctx->N, ctx, cur, s, true);
+                if (lv == 3) launch0(ctx, cur ^ 1);
+                if (rc) return rc;
+                CK(cudaEventRecord(ev[ie + 1], ctx->stream));
+                marks.push_back({lv, ie});
+                ie += 2;
+            }
+            cur ^= 1;
+        }
+        k_advance_time<<<1, 1, 0, ctx->stream>>>(ctx->d_time, ctx->d_step, ctx->dt);
+        ctx->cur ^= 1;
+        ctx->step_count++;
+    }
+    CK(cudaEventRecord(ev[ie], ctx->stream));
+    CK(cudaEventSynchronize(ev[ie]));
+    for (auto &mk : marks) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[mk.second], ev[mk.second + 1]));
+        acc[mk.first] += ms;
+        cnt[mk.first]++;
+    }
+    float total = 0.f;
+    CK(cudaEventElapsedTime(&total, ev[0], ev[ie]));
+    for (int lv = 0; lv < 4; ++lv) out_ms[lv] = cnt[lv] ? acc[lv] / cnt[lv] : 0.0;
+    out_ms[4] = total / double(nsteps);
+    for (auto &e : ev) cudaEventDestroy(e);
+    return DGH_OK;
+}
+
+int dgh_sync(dgh_ctx *ctx) {
+    if (!ctx) return DGH_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DGH_OK;
+}
+
+int dgh_get_energy(dgh_ctx *ctx, double *E) {
+    if (!ctx || !E) return DGH_EINVAL;
+    const int nb = ctx->energy_blocks;
+    switch (ctx->N) {
+        case 1: k_energy_partial<1><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
+        case 2: k_energy_partial<2><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
+        case 3: k_energy_partial<3><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
+        case 4: k_energy_partial<4><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
+        case 5: k_energy_partial<5><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
+        case 6: k_energy_partial<6><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
+    }
+    k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, nb, ctx->d_energy);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DGH_OK;
+}
+
+// Checkpoint blob: header (magic, sizes, time, step) then q/res of levels 3, 2, 1.
+int dgh_save_state(dgh_ctx *ctx, void *buf, size_t *size) {
+    if (!ctx || !size) return DGH_EINVAL;
+    size_t n3, n2, n1;
+    level_count(ctx, 3, n3);
+    level_count(ctx, 2, n2);
+    level_count(ctx, 1, n1);
+    const size_t header = 8 * sizeof(int64_t);
+    const size_t need = header + 2 * (n3 + n2 + n1) * sizeof(float);
+    if (!buf) {
+        *size = need;
+        return DGH_OK;
+    }
+    if (*size < need) {
+        ctx->err = "checkpoint buffer too small";
+        return DGH_EINVAL;
+    }
+    double t = 0.0;
+    CK(cudaMemcpyAsync(&t, ctx->d_time, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int64_t h[8] = {0x4447484350543031LL, int64_t(n3), int64_t(n2), int64_t(n1), ctx->step_count, 0, 0, 0};
+    std::memcpy(&h[5], &t, sizeof(double));
+    char *p = static_cast<char *>(buf);
+    std::memcpy(p, h, header);
+    p += header;
+    const size_t ns[3] = {n3, n2, n1};
+    for (int i = 0; i < 3; ++i)
+        for (int r = 0; r < 2; ++r) {
+            if (ns[i]) CK(cudaMemcpyAsync(p, level_ptr(ctx, 3 - i, r), ns[i] * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+            p += ns[i] * sizeof(float);
+        }
+    CK(cudaStreamSynchronize(ctx->stream));
+    *size = need;
+    return DGH_OK;
+}
+
+int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size) {
+    if (!ctx || !buf) return DGH_EINVAL;
+    size_t n3, n2, n1;
+    level_count(ctx, 3, n3);
+    level_count(ctx, 2, n2);
+    level_count(ctx, 1, n1);
+    const size_t header = 8 * sizeof(int64_t);
+    const size_t need = header + 2 * (n3 + n2 + n1) * sizeof(float);
+    int64_t h[8];
+    if (size != need) {
+        ctx->err = "checkpoint size mismatch";
+        return DGH_EINVAL;
+    }
+    std::memcpy(h, buf, header);
+    if (h[0] != 0x4447484350543031LL || h[1] != int64_t(n3) || h[2] != int64_t(n2) || h[3] != int64_t(n1)) {
+        ctx->err = "checkpoint does not match this context";
+        return DGH_EINVAL;
+    }
+    double t;
+    std::memcpy(&t, &h[5], sizeof(double));
+    const char *p = static_cast<const char *>(buf) + header;
+    const size_t ns[3] = {n3, n2, n1};
+    for (int i = 0; i < 3; ++i)
+        for (int r = 0; r < 2; ++r) {
+            if (ns[i]) CK(cudaMemcpyAsync(level_ptr(ctx, 3 - i, r), p, ns[i] * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+            p += ns[i] * sizeof(float);
+        }
+    CK(cudaMemcpyAsync(ctx->d_time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_step, &h[4], sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->step_count = h[4];
+    ctx->dirty = true;
+    return DGH_OK;
+}
+
+}  // extern "C"

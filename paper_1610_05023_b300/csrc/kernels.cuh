@@ -1,0 +1,723 @@
+// Device kernels of one LSERK4 stage of the multidimensional DG + HABC solver.
+//
+// Per stage (Algorithm 1, with the volume/surface/update work of each level
+// fused into one kernel):
+//   k3d_stage  3D volume term, upwind surface flux + lift, LSERK update, new
+//              3D traces (Sec. 3.2, eq. dgLocalRhs, eqs. timeStepProc1-2)
+//   k2d_stage  2D face systems (eqs. proc:2Dpvsyst1-3) for all P sets, then
+//              the face BC: r^+_3D from the new 3D traces, r^-_3D =
+//              (1/M) sum c_a p*_a (eq. proc:faceBC), q0 = r^- + r^+,
+//              p_a = p*_a + q0 (eq. proc:pi00Star), new 2D traces
+//   k1d_stage  1D edge systems (eqs. proc:1Dpvsyst1-2) for all P^2 sets, then
+//              the edge BCs (eqs. proc:edgeBC1-2) through the precomputed
+//              solution operator, p_ab (eq. proc:pij0Star), new 1D traces
+//   k0d_stage  corner BCs (eqs. proc:cornerBC1-3) through the precomputed
+//              solution operator
+// Traces are double-buffered (read tr_in, write tr_out); q and res are
+// updated in place because cells only read their neighbours' traces.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgh {
+
+template <int N>
+struct Ord {
+    static constexpr int NP = (N + 1) * (N + 2) * (N + 3) / 6;
+    static constexpr int NFP = (N + 1) * (N + 2) / 2;
+    static constexpr int NP2 = (N + 1) * (N + 2) / 2;
+    static constexpr int NFP2 = N + 1;
+    static constexpr int NP1 = N + 1;
+    static constexpr int TILE3 = (256 / NP) > 0 ? (256 / NP) : 1;
+};
+
+constexpr int GEO3 = 40;   // per tet: drdx[9], 4 x (nx,ny,nz,fscale,wm,zz,iz), rho c^2, 1/rho, Z
+constexpr int GEO2 = 28;   // per tri: drdx[4], 3 x (nx,ny,fscale,wm,zz,iz), rho c^2, 1/rho, Z, pad[3]
+constexpr int GEO1 = 16;   // per line: rx, fscale, rho c^2, 1/rho, Z, ZA, ZB, 2 x (wm,zz,iz), pad[3]
+constexpr int MAXP = 8;
+constexpr int MAXSRC = 16;
+
+struct SrcParams {
+    int n;
+    int64_t cell[MAXSRC];
+    double f_peak[MAXSRC], t_s[MAXSRC], amp[MAXSRC];
+    const float *vec;       // [MAXSRC][Np]
+};
+
+struct StageCoef {
+    float a, b, dt;
+    double c_dt;            // C_s * dt (stage time offset)
+    const double *time;     // device: time at the start of the step
+};
+
+struct Args3 {
+    float *q, *res;
+    const float *tr_in;
+    float *tr_out;
+    const float *geo;
+    const int *conn;        // >=0: (k'*4+f')<<3 | sigma ; <0: -1 - (bidx<<1 | dirichlet)
+    const float *qb;        // [Fb][Nfp]
+    const float *D;         // [3][Np(m)][Np(n)]  D_j[n][m] stored at (j*Np + m)*Np + n
+    const float *LIFT;      // [4Nfp(fm)][Np(n)]
+    const int *fmask;       // [4][Nfp]
+    const int *fperm;       // [6][Nfp]
+    int64_t K;
+    SrcParams src;
+};
+
+struct Args2 {
+    float *q, *res;         // [T][P][3][Np2]
+    const float *tr_in;     // [T][P][3][2][Nfp2]
+    float *tr_out;
+    const float *geo;       // [T][GEO2]
+    const int *conn;        // >=0: (t'*3+e')<<1 | flip ; -1: HABC edge (qb2) ; -2: Dirichlet edge
+    const float *qb;        // [T][3][P][Nfp2]  incoming 2D characteristic at domain-edge nodes
+    float *q0;              // [T][Np2]         r^- + r^+ of the 3D field at the triangle nodes
+    float *qb3;             // [Fb][Nfp]        out: incoming 3D characteristic
+    const float *tr3;       // new 3D traces [K][4][2][Nfp]
+    const int *tri_face;    // [T] global face id k*4+f of the owning tet face
+    const int *tri_bface;   // [T] boundary face index
+    const float *D;         // [2][Np2(m)][Np2(n)]
+    const float *LIFT;      // [3Nfp2][Np2]
+    const int *fmask;       // [3][Nfp2]
+    const float *cP;        // [P] Pade coefficients
+    float invM;
+    int P;
+    int64_t T;
+};
+
+struct Args1 {
+    float *q, *res;         // [L][P^2][2][Np1]
+    const float *tr_in;     // [L][P^2][2 ends][2]
+    float *tr_out;
+    const float *geo;       // [L][GEO1]
+    const int *conn;        // [L][2] >=0: l'*2+e' ; -1: HABC corner (qb1) ; -2: Dirichlet corner
+    const float *qb;        // [L][2][P^2]  incoming 1D characteristic at corner ends
+    float *q0;              // [L][2][P][Np1] r^- + r^+ of the 2D fields of faces A, B at the line nodes
+    float *qb2;             // out: incoming 2D characteristic [T][3][P][Nfp2]
+    const float *tr2;       // new 2D traces [T][P][3][2][Nfp2]
+    const int *lmap;        // [L][6]: triA, edgeA, revA, triB, edgeB, revB
+    const float *D;         // [Np1(m)][Np1(n)]
+    const float *LIFT;      // [2][Np1]
+    const float *H1;        // [2P][2P]
+    const float *H2;        // [2P][P^2]
+    const float *cP;
+    float invM;
+    int P;
+    int64_t L;
+};
+
+struct Args0 {
+    const float *tr1;       // new 1D traces
+    float *qb1;             // [L][2][P^2]
+    const int *corner;      // [C][6]: (line, end) x 3 slots (YZ, XZ, XY)
+    const float *cornerZ;   // [C][3]
+    const float *Hc;        // [3P^2][3P^2]
+    int P;
+    int C;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double ricker_integral_d(double t, double f, double ts) {
+    const double a = 3.14159265358979323846 * f * (t - ts);
+    return (t - ts) * exp(-a * a);
+}
+
+// ==================================================================== 3D
+// Contravariant fluxes fr, fs, ft; face flux terms; volume + lift; update.
+template <int N, bool UPDATE>
+__global__ void __launch_bounds__(256) k3d_stage(Args3 A, StageCoef sc) {
+    using O = Ord<N>;
+    constexpr int NP = O::NP, NFP = O::NFP, TILE = O::TILE3, NF = 4 * NFP;
+    extern __shared__ float sm[];
+    float *sD = sm;                        // 3*NP*NP
+    float *sL = sD + 3 * NP * NP;          // NF*NP
+    float *sq = sL + NF * NP;              // TILE*4*NP
+    float *sf = sq + TILE * 4 * NP;        // TILE*3*NP
+    float *sx = sf + TILE * 3 * NP;        // TILE*2*NF
+    float *sg = sx + TILE * 2 * NF;        // TILE*GEO3
+    int *sfm = reinterpret_cast<int *>(sg + TILE * GEO3);  // 4*NFP
+    int *sfp = sfm + 4 * NFP;              // 6*NFP
+    const int tid = threadIdx.x, nth = blockDim.x;
+
+    if (UPDATE) {
+        for (int i = tid; i < 3 * NP * NP; i += nth) sD[i] = A.D[i];
+        for (int i = tid; i < NF * NP; i += nth) sL[i] = A.LIFT[i];
+    }
+    for (int i = tid; i < 4 * NFP; i += nth) sfm[i] = A.fmask[i];
+    for (int i = tid; i < 6 * NFP; i += nth) sfp[i] = A.fperm[i];
+    const int64_t ntiles = (A.K + TILE - 1) / TILE;
+    double tstage = 0.0;
+    if (UPDATE && A.src.n > 0) tstage = sc.time[0] + sc.c_dt;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t k0 = tile * TILE;
+        const int ne = (int)((A.K - k0) < TILE ? (A.K - k0) : TILE);
+        __syncthreads();
+        {
+            const float *src = A.q + k0 * 4 * NP;
+            for (int i = tid; i < ne * 4 * NP; i += nth) sq[i] = src[i];
+            const float *gsrc = A.geo + k0 * GEO3;
+            for (int i = tid; i < ne * GEO3; i += nth) sg[i] = gsrc[i];
+        }
+        __syncthreads();
+        if (!UPDATE) {
+            // traces of the current fields only
+            for (int i = tid; i < ne * NF; i += nth) {
+                const int e = i / NF, fm = i % NF, f = fm / NFP, m = fm % NFP;
+                const int n = sfm[f * NFP + m];
+                const float *g = sg + e * GEO3 + 9 + 7 * f;
+                const float *qe = sq + e * 4 * NP;
+                const float un = g[0] * qe[NP + n] + g[1] * qe[2 * NP + n] + g[2] * qe[3 * NP + n];
+                float *dst = A.tr_out + ((k0 + e) * 4 + f) * 2 * NFP;
+                dst[m] = qe[n];
+                dst[NFP + m] = un;
+            }
+            continue;
+        }
+        // contravariant fluxes f_j = sum_i dr_j/dx_i u_i
+        for (int i = tid; i < ne * NP; i += nth) {
+            const int e = i / NP, n = i % NP;
+            const float *qe = sq + e * 4 * NP;
+            const float *g = sg + e * GEO3;
+            const float u = qe[NP + n], v = qe[2 * NP + n], w = qe[3 * NP + n];
+            float *fe = sf + e * 3 * NP;
+            fe[n] = g[0] * u + g[1] * v + g[2] * w;
+            fe[NP + n] = g[3] * u + g[4] * v + g[5] * w;
+            fe[2 * NP + n] = g[6] * u + g[7] * v + g[8] * w;
+        }
+        // upwind flux differences at the face nodes
+        for (int i = tid; i < ne * NF; i += nth) {
+            const int e = i / NF, fm = i % NF, f = fm / NFP, m = fm % NFP;
+            const int64_t k = k0 + e;
+            const int n = sfm[f * NFP + m];
+            const float *qe = sq + e * 4 * NP;
+            const float *g = sg + e * GEO3 + 9 + 7 * f;
+            const float pm = qe[n];
+            const float unm = g[0] * qe[NP + n] + g[1] * qe[2 * NP + n] + g[2] * qe[3 * NP + n];
+            const int c = A.conn[k * 4 + f];
+            float pp, unp;
+            if (c >= 0) {
+                const int nb = c >> 3, sg_ = c & 7;
+                const int mm = sfp[sg_ * NFP + m];
+                const float *tr = A.tr_in + (int64_t)nb * 2 * NFP;
+                pp = tr[mm];
+                unp = -tr[NFP + mm];
+            } else {
+                const int code = -1 - c;
+                if (code & 1) {          // p = 0: mirror state
+                    pp = -pm;
+                    unp = unm;
+                } else {                 // incoming characteristic r^- (0 for the basic ABC)
+                    pp = 2.0f * A.qb[(int64_t)(code >> 1) * NFP + m];
+                    unp = 0.0f;
+                }
+            }
+            const float fs = g[3], wm = g[4], zz = g[5], iz = g[6];
+            const float dP = wm * (pp - pm) + zz * (unm - unp);
+            const float dUn = (1.0f - wm) * (unp - unm) + iz * (pm - pp);
+            sx[e * 2 * NF + fm] = fs * dUn;
+            sx[e * 2 * NF + NF + fm] = fs * dP;
+        }
+        __syncthreads();
+        float qn[4];
+        int my_e = -1, my_n = 0;
+        for (int i = tid; i < ne * NP; i += nth) {   // one item per thread (nth >= TILE*NP)
+            const int e = i / NP, n = i % NP;
+            my_e = e;
+            my_n = n;
+            const float *qe = sq + e * 4 * NP;
+            const float *fe = sf + e * 3 * NP;
+            float div = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
+#pragma unroll 5
+            for (int m = 0; m < NP; ++m) {
+                const float dr = sD[m * NP + n], ds = sD[(NP + m) * NP + n], dt = sD[(2 * NP + m) * NP + n];
+                const float p = qe[m];
+                div += dr * fe[m] + ds * fe[NP + m] + dt * fe[2 * NP + m];
+                dpr += dr * p;
+                dps += ds * p;
+                dpt += dt * p;
+            }
+            const float *xe = sx + e * 2 * NF;
+            float lun = 0.f, lp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+#pragma unroll 5
+                for (int m = 0; m < NFP; ++m) {
+                    const float l = sL[(f * NFP + m) * NP + n];
+                    lun += l * xe[f * NFP + m];
+                    lp[f] += l * xe[NF + f * NFP + m];
+                }
+            }
+            const float *g = sg + e * GEO3;
+            const float rc2 = g[37], irho = g[38];
+            float rhs[4];
+            rhs[0] = -rc2 * (div + lun);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float grad = g[d] * dpr + g[3 + d] * dps + g[6 + d] * dpt;
+                const float lift = g[9 + d] * lp[0] + g[16 + d] * lp[1] + g[23 + d] * lp[2] + g[30 + d] * lp[3];
+                rhs[1 + d] = -irho * (grad + lift);
+            }
+            const int64_t k = k0 + e;
+            for (int s = 0; s < A.src.n; ++s)
+                if (A.src.cell[s] == k)
+                    rhs[0] += (float)(A.src.amp[s] * ricker_integral_d(tstage, A.src.f_peak[s], A.src.t_s[s])) *
+                              A.src.vec[s * NP + n];
+            float *qg = A.q + k * 4 * NP;
+            float *rg = A.res + k * 4 * NP;
+#pragma unroll
+            for (int fl = 0; fl < 4; ++fl) {
+                const float r = sc.a * rg[fl * NP + n] + sc.dt * rhs[fl];
+                rg[fl * NP + n] = r;
+                qn[fl] = qe[fl * NP + n] + sc.b * r;
+                qg[fl * NP + n] = qn[fl];
+            }
+        }
+        __syncthreads();
+        if (my_e >= 0)
+#pragma unroll
+            for (int fl = 0; fl < 4; ++fl) sq[my_e * 4 * NP + fl * NP + my_n] = qn[fl];
+        __syncthreads();
+        for (int i = tid; i < ne * NF; i += nth) {
+            const int e = i / NF, fm = i % NF, f = fm / NFP, m = fm % NFP;
+            const int n = sfm[f * NFP + m];
+            const float *g = sg + e * GEO3 + 9 + 7 * f;
+            const float *qe = sq + e * 4 * NP;
+            const float un = g[0] * qe[NP + n] + g[1] * qe[2 * NP + n] + g[2] * qe[3 * NP + n];
+            float *dst = A.tr_out + ((k0 + e) * 4 + f) * 2 * NFP;
+            dst[m] = qe[n];
+            dst[NFP + m] = un;
+        }
+    }
+}
+
+template <int N>
+constexpr size_t k3d_smem() {
+    using O = Ord<N>;
+    return sizeof(float) * (3 * O::NP * O::NP + 4 * O::NFP * O::NP + O::TILE3 * (4 * O::NP + 3 * O::NP + 2 * 4 * O::NFP + GEO3)) +
+           sizeof(int) * (4 * O::NFP + 6 * O::NFP);
+}
+
+// ==================================================================== 2D
+// One block handles a tile of triangles; items are (tri, set, node).
+template <int N, bool UPDATE>
+__global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile_tris) {
+    using O = Ord<N>;
+    constexpr int NP2 = O::NP2, NFP2 = O::NFP2, NE = 3 * NFP2;
+    const int P = A.P;
+    extern __shared__ float sm[];
+    float *sD = sm;                                   // 2*NP2*NP2
+    float *sL = sD + 2 * NP2 * NP2;                   // NE*NP2
+    float *sq = sL + NE * NP2;                        // tile*P*3*NP2 (p*, v1, v2)
+    float *sp = sq + tile_tris * P * 3 * NP2;         // tile*P*NP2 full p
+    float *sx = sp + tile_tris * P * NP2;             // tile*P*2*NE
+    float *sg = sx + tile_tris * P * 2 * NE;          // tile*GEO2
+    float *s0 = sg + tile_tris * GEO2;                // tile*NP2 q0
+    float *sn = s0 + tile_tris * NP2;                 // tile*P*3*NP2 new (p*, v1, v2)
+    int *sfm = reinterpret_cast<int *>(sn + tile_tris * P * 3 * NP2);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    if (UPDATE) {
+        for (int i = tid; i < 2 * NP2 * NP2; i += nth) sD[i] = A.D[i];
+        for (int i = tid; i < NE * NP2; i += nth) sL[i] = A.LIFT[i];
+    }
+    for (int i = tid; i < NE; i += nth) sfm[i] = A.fmask[i];
+    const int64_t ntiles = (A.T + tile_tris - 1) / tile_tris;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t t0 = tile * tile_tris;
+        const int nt = (int)((A.T - t0) < tile_tris ? (A.T - t0) : tile_tris);
+        __syncthreads();
+        for (int i = tid; i < nt * P * 3 * NP2; i += nth) sq[i] = A.q[t0 * P * 3 * NP2 + i];
+        for (int i = tid; i < nt * GEO2; i += nth) sg[i] = A.geo[t0 * GEO2 + i];
+        for (int i = tid; i < nt * NP2; i += nth) s0[i] = A.q0[t0 * NP2 + i];
+        __syncthreads();
+        if (UPDATE) {
+            for (int i = tid; i < nt * P * NP2; i += nth) {
+                const int t = i / (P * NP2), r = i % (P * NP2), a = r / NP2, n = r % NP2;
+                sp[i] = sq[(t * P + a) * 3 * NP2 + n] + s0[t * NP2 + n];
+            }
+            __syncthreads();
+            // edge flux differences
+            for (int i = tid; i < nt * P * NE; i += nth) {
+                const int t = i / (P * NE), r = i % (P * NE), a = r / NE, em = r % NE, e = em / NFP2, m = em % NFP2;
+                const int n = sfm[em];
+                const float *g = sg + t * GEO2;
+                const float *qa = sq + (t * P + a) * 3 * NP2;
+                const float nx = g[4 + 6 * e], ny = g[5 + 6 * e];
+                const float pm = sp[(t * P + a) * NP2 + n];
+                const float vnm = nx * qa[NP2 + n] + ny * qa[2 * NP2 + n];
+                const int64_t tg = t0 + t;
+                const int c = A.conn[tg * 3 + e];
+                float pp, vnp;
+                if (c >= 0) {
+                    const int nb = c >> 1;
+                    const int mm = (c & 1) ? (NFP2 - 1 - m) : m;
+                    const int tn = nb / 3, en = nb % 3;
+                    const float *tr = A.tr_in + (((int64_t)tn * P + a) * 3 + en) * 2 * NFP2;
+                    pp = tr[mm];
+                    vnp = -tr[NFP2 + mm];
+                } else if (c == -2) {
+                    pp = -pm;
+                    vnp = vnm;
+                } else {
+                    pp = 2.0f * A.qb[((tg * 3 + e) * P + a) * NFP2 + m];
+                    vnp = 0.0f;
+                }
+                const float fs = g[6 + 6 * e], wm = g[7 + 6 * e], zz = g[8 + 6 * e], iz = g[9 + 6 * e];
+                const float dP = wm * (pp - pm) + zz * (vnm - vnp);
+                const float dVn = (1.0f - wm) * (vnp - vnm) + iz * (pm - pp);
+                sx[(t * P + a) * 2 * NE + em] = fs * dVn;
+                sx[(t * P + a) * 2 * NE + NE + em] = fs * dP;
+            }
+            __syncthreads();
+            // volume + lift + update
+            for (int i = tid; i < nt * P * NP2; i += nth) {
+                const int t = i / (P * NP2), r = i % (P * NP2), a = r / NP2, n = r % NP2;
+                const float *g = sg + t * GEO2;
+                const float *qa = sq + (t * P + a) * 3 * NP2;
+                const float *pa = sp + (t * P + a) * NP2;
+                float div = 0.f, dpr = 0.f, dps = 0.f;
+                for (int m = 0; m < NP2; ++m) {
+                    const float dr = sD[m * NP2 + n], ds = sD[(NP2 + m) * NP2 + n];
+                    const float v1 = qa[NP2 + m], v2 = qa[2 * NP2 + m];
+                    div += dr * (g[0] * v1 + g[1] * v2) + ds * (g[2] * v1 + g[3] * v2);
+                    dpr += dr * pa[m];
+                    dps += ds * pa[m];
+                }
+                const float *xa = sx + (t * P + a) * 2 * NE;
+                float lvn = 0.f, lp[3] = {0.f, 0.f, 0.f};
+                for (int e = 0; e < 3; ++e)
+                    for (int m = 0; m < NFP2; ++m) {
+                        const float l = sL[(e * NFP2 + m) * NP2 + n];
+                        lvn += l * xa[e * NFP2 + m];
+                        lp[e] += l * xa[NE + e * NFP2 + m];
+                    }
+                const float rc2 = g[22], irho = g[23];
+                const float wa = 1.0f / (1.0f + A.cP[a]);
+                float rhs[3];
+                rhs[0] = -rc2 * wa * (div + lvn);
+                rhs[1] = -irho * (g[0] * dpr + g[2] * dps + g[4] * lp[0] + g[10] * lp[1] + g[16] * lp[2]);
+                rhs[2] = -irho * (g[1] * dpr + g[3] * dps + g[5] * lp[0] + g[11] * lp[1] + g[17] * lp[2]);
+                const int64_t base = ((t0 + t) * P + a) * 3 * NP2;
+                for (int fl = 0; fl < 3; ++fl) {
+                    const float rr = sc.a * A.res[base + fl * NP2 + n] + sc.dt * rhs[fl];
+                    A.res[base + fl * NP2 + n] = rr;
+                    const float qv = qa[fl * NP2 + n] + sc.b * rr;
+                    A.q[base + fl * NP2 + n] = qv;
+                    sn[(t * P + a) * 3 * NP2 + fl * NP2 + n] = qv;
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < nt * P * 3 * NP2; i += nth) sq[i] = sn[i];
+            __syncthreads();
+        }
+        // face BC: r^+ from the new 3D traces, r^- = (1/M) sum c_a p*_a, q0 = r^- + r^+
+        for (int i = tid; i < nt * NP2; i += nth) {
+            const int t = i / NP2, n = i % NP2;
+            const int64_t tg = t0 + t;
+            const float *tr = A.tr3 + (int64_t)A.tri_face[tg] * 2 * NP2;   // tet face traces (Nfp == Np2)
+            const float Z = sg[t * GEO2 + 24];
+            const float rp = 0.5f * (tr[n] + Z * tr[NP2 + n]);
+            float rm = 0.f;
+            for (int a = 0; a < P; ++a) rm += A.cP[a] * sq[(t * P + a) * 3 * NP2 + n];
+            rm *= A.invM;
+            A.qb3[(int64_t)A.tri_bface[tg] * NP2 + n] = rm;
+            const float q0 = rm + rp;
+            A.q0[tg * NP2 + n] = q0;
+            s0[t * NP2 + n] = q0;
+        }
+        __syncthreads();
+        // new 2D traces (full pressure, in-plane normal velocity)
+        for (int i = tid; i < nt * P * NE; i += nth) {
+            const int t = i / (P * NE), r = i % (P * NE), a = r / NE, em = r % NE, e = em / NFP2, m = em % NFP2;
+            const int n = sfm[em];
+            const float *g = sg + t * GEO2;
+            const float *qa = sq + (t * P + a) * 3 * NP2;
+            float *dst = A.tr_out + (((t0 + t) * P + a) * 3 + e) * 2 * NFP2;
+            dst[m] = qa[n] + s0[t * NP2 + n];
+            dst[NFP2 + m] = g[4 + 6 * e] * qa[NP2 + n] + g[5 + 6 * e] * qa[2 * NP2 + n];
+        }
+    }
+}
+
+inline size_t k2d_smem(int N, int P, int tile) {
+    const int NP2 = (N + 1) * (N + 2) / 2, NFP2 = N + 1, NE = 3 * NFP2;
+    return sizeof(float) * (2 * NP2 * NP2 + NE * NP2 + tile * (2 * P * 3 * NP2 + P * NP2 + P * 2 * NE + GEO2 + NP2)) +
+           sizeof(int) * NE;
+}
+
+// ==================================================================== 1D
+template <int N, bool UPDATE>
+__global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile_lines) {
+    constexpr int NP1 = N + 1;
+    const int P = A.P, S = P * P;
+    extern __shared__ float sm[];
+    float *sD = sm;                                   // NP1*NP1
+    float *sL = sD + NP1 * NP1;                       // 2*NP1
+    float *sq = sL + 2 * NP1;                         // tile*S*2*NP1
+    float *sp = sq + tile_lines * S * 2 * NP1;        // tile*S*NP1 full p
+    float *sx = sp + tile_lines * S * NP1;            // tile*S*2*2
+    float *s0 = sx + tile_lines * S * 4;              // tile*2*P*NP1
+    float *sg = s0 + tile_lines * 2 * P * NP1;        // tile*GEO1
+    float *sn = sg + tile_lines * GEO1;               // tile*S*2*NP1 new (p*, w)
+    float *sH = sn + tile_lines * S * 2 * NP1;        // 2P*2P + 2P*S
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < NP1 * NP1; i += nth) sD[i] = A.D[i];
+    for (int i = tid; i < 2 * NP1; i += nth) sL[i] = A.LIFT[i];
+    for (int i = tid; i < 4 * P * P; i += nth) sH[i] = A.H1[i];
+    for (int i = tid; i < 2 * P * S; i += nth) sH[4 * P * P + i] = A.H2[i];
+    const int64_t ntiles = (A.L + tile_lines - 1) / tile_lines;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t l0 = tile * tile_lines;
+        const int nl = (int)((A.L - l0) < tile_lines ? (A.L - l0) : tile_lines);
+        __syncthreads();
+        for (int i = tid; i < nl * S * 2 * NP1; i += nth) sq[i] = A.q[l0 * S * 2 * NP1 + i];
+        for (int i = tid; i < nl * 2 * P * NP1; i += nth) s0[i] = A.q0[l0 * 2 * P * NP1 + i];
+        for (int i = tid; i < nl * GEO1; i += nth) sg[i] = A.geo[l0 * GEO1 + i];
+        __syncthreads();
+        if (UPDATE) {
+            // full p_ab = p*_ab + C_ba q0_A,a + C_ab q0_B,b
+            for (int i = tid; i < nl * S * NP1; i += nth) {
+                const int l = i / (S * NP1), r = i % (S * NP1), s = r / NP1, n = r % NP1;
+                const int a = s % P, b = s / P;
+                const float ca = A.cP[a], cb = A.cP[b], den = 1.0f / (1.0f + ca + cb);
+                sp[i] = sq[(l * S + s) * 2 * NP1 + n] + (1.0f + cb) * den * s0[(l * 2 + 0) * P * NP1 + a * NP1 + n] +
+                        (1.0f + ca) * den * s0[(l * 2 + 1) * P * NP1 + b * NP1 + n];
+            }
+            __syncthreads();
+            for (int i = tid; i < nl * S * 2; i += nth) {
+                const int l = i / (S * 2), r = i % (S * 2), s = r / 2, e = r % 2;
+                const int64_t lg = l0 + l;
+                const float *g = sg + l * GEO1;
+                const int nd = e ? N : 0;
+                const float tau = e ? 1.0f : -1.0f;
+                const float pm = sp[(l * S + s) * NP1 + nd];
+                const float wnm = tau * sq[(l * S + s) * 2 * NP1 + NP1 + nd];
+                const int c = A.conn[lg * 2 + e];
+                float pp, wnp;
+                if (c >= 0) {
+                    const float *tr = A.tr_in + ((int64_t)(c >> 1) * S + s) * 4 + (c & 1) * 2;
+                    pp = tr[0];
+                    wnp = -tr[1];
+                } else if (c == -2) {
+                    pp = -pm;
+                    wnp = wnm;
+                } else {
+                    pp = 2.0f * A.qb[(lg * 2 + e) * S + s];
+                    wnp = 0.0f;
+                }
+                const float wm = g[7 + 3 * e], zz = g[8 + 3 * e], iz = g[9 + 3 * e];
+                const float dP = wm * (pp - pm) + zz * (wnm - wnp);
+                const float dWn = (1.0f - wm) * (wnp - wnm) + iz * (pm - pp);
+                sx[(l * S + s) * 4 + e] = g[1] * dWn;
+                sx[(l * S + s) * 4 + 2 + e] = g[1] * tau * dP;
+            }
+            __syncthreads();
+            for (int i = tid; i < nl * S * NP1; i += nth) {
+                const int l = i / (S * NP1), r = i % (S * NP1), s = r / NP1, n = r % NP1;
+                const int a = s % P, b = s / P;
+                const float *g = sg + l * GEO1;
+                const float *qs = sq + (l * S + s) * 2 * NP1;
+                const float *ps = sp + (l * S + s) * NP1;
+                float dw = 0.f, dp = 0.f;
+                for (int m = 0; m < NP1; ++m) {
+                    const float d = sD[m * NP1 + n];
+                    dw += d * qs[NP1 + m];
+                    dp += d * ps[m];
+                }
+                const float *xs = sx + (l * S + s) * 4;
+                const float lw = sL[n] * xs[0] + sL[NP1 + n] * xs[1];
+                const float lpp = sL[n] * xs[2] + sL[NP1 + n] * xs[3];
+                const float wab = 1.0f / (1.0f + A.cP[a] + A.cP[b]);
+                float rhs[2];
+                rhs[0] = -g[2] * wab * (g[0] * dw + lw);
+                rhs[1] = -g[3] * (g[0] * dp + lpp);
+                const int64_t base = ((l0 + l) * S + s) * 2 * NP1;
+                for (int fl = 0; fl < 2; ++fl) {
+                    const float rr = sc.a * A.res[base + fl * NP1 + n] + sc.dt * rhs[fl];
+                    A.res[base + fl * NP1 + n] = rr;
+                    const float qv = qs[fl * NP1 + n] + sc.b * rr;
+                    A.q[base + fl * NP1 + n] = qv;
+                    sn[(l * S + s) * 2 * NP1 + fl * NP1 + n] = qv;
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < nl * S * 2 * NP1; i += nth) sq[i] = sn[i];
+            __syncthreads();
+        }
+        // edge BCs: one thread per (line, node)
+        for (int i = tid; i < nl * NP1; i += nth) {
+            const int l = i / NP1, n = i % NP1;
+            const int64_t lg = l0 + l;
+            const int *mp = A.lmap + lg * 6;
+            float rp[2 * MAXP];
+            for (int side = 0; side < 2; ++side) {
+                const int tri = mp[3 * side], e = mp[3 * side + 1], rev = mp[3 * side + 2];
+                const int m = rev ? (N - n) : n;
+                const float Z = sg[l * GEO1 + 5 + side];
+                for (int a = 0; a < P; ++a) {
+                    const float *tr = A.tr2 + (((int64_t)tri * P + a) * 3 + e) * 2 * NP1;
+                    rp[side * P + a] = 0.5f * (tr[m] + Z * tr[NP1 + m]);
+                }
+            }
+            const float *H1 = sH, *H2 = sH + 4 * P * P;
+            for (int row = 0; row < 2 * P; ++row) {
+                float x = 0.f;
+                for (int col = 0; col < 2 * P; ++col) x += H1[row * 2 * P + col] * rp[col];
+                for (int s = 0; s < S; ++s) x += H2[row * S + s] * sq[(l * S + s) * 2 * NP1 + n];
+                const int side = row / P, a = row % P;
+                const int tri = mp[3 * side], e = mp[3 * side + 1], rev = mp[3 * side + 2];
+                const int m = rev ? (N - n) : n;
+                A.qb2[(((int64_t)tri * 3 + e) * P + a) * NP1 + m] = x;
+                const float q0 = x + rp[row];
+                A.q0[(lg * 2 + side) * P * NP1 + a * NP1 + n] = q0;
+                s0[(l * 2 + side) * P * NP1 + a * NP1 + n] = q0;
+            }
+        }
+        __syncthreads();
+        // new 1D traces (full p_ab, tangential velocity along the outward end direction)
+        for (int i = tid; i < nl * S * 2; i += nth) {
+            const int l = i / (S * 2), r = i % (S * 2), s = r / 2, e = r % 2;
+            const int a = s % P, b = s / P;
+            const int nd = e ? N : 0;
+            const float ca = A.cP[a], cb = A.cP[b], den = 1.0f / (1.0f + ca + cb);
+            const float *qs = sq + (l * S + s) * 2 * NP1;
+            const float p = qs[nd] + (1.0f + cb) * den * s0[(l * 2 + 0) * P * NP1 + a * NP1 + nd] +
+                            (1.0f + ca) * den * s0[(l * 2 + 1) * P * NP1 + b * NP1 + nd];
+            float *dst = A.tr_out + ((l0 + l) * S + s) * 4 + e * 2;
+            dst[0] = p;
+            dst[1] = (e ? 1.0f : -1.0f) * qs[NP1 + nd];
+        }
+    }
+}
+
+inline size_t k1d_smem(int N, int P, int tile) {
+    const int NP1 = N + 1, S = P * P;
+    return sizeof(float) * (NP1 * NP1 + 2 * NP1 + tile * (2 * S * 2 * NP1 + S * NP1 + S * 4 + 2 * P * NP1 + GEO1) +
+                            4 * P * P + 2 * P * S);
+}
+
+// ==================================================================== 0D
+__global__ void k0d_stage(Args0 A) {
+    const int c = blockIdx.x;
+    const int P = A.P, S = P * P, R = 3 * S;
+    extern __shared__ float rp[];
+    const int *cd = A.corner + c * 6;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        const int slot = i / S, s = i % S;
+        const int l = cd[2 * slot], e = cd[2 * slot + 1];
+        const float *tr = A.tr1 + ((int64_t)l * S + s) * 4 + e * 2;
+        rp[i] = 0.5f * (tr[0] + A.cornerZ[c * 3 + slot] * tr[1]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        float x = 0.f;
+        for (int j = 0; j < R; ++j) x += A.Hc[i * R + j] * rp[j];
+        const int slot = i / S, s = i % S;
+        const int l = cd[2 * slot], e = cd[2 * slot + 1];
+        A.qb1[((int64_t)l * 2 + e) * S + s] = x;
+    }
+}
+
+__global__ void k_advance_time(double *time, int64_t *step, double dt) {
+    time[0] += dt;
+    step[0] += 1;
+}
+
+// ==================================================================== misc
+// Gaussian pressure at the nodes (FP64 node coordinates from the tet vertices).
+template <int N>
+__global__ void k_init_gaussian(float *q, const double *cellv, const double *rst, int64_t K, double x0, double y0,
+                                double z0, double w, double amp) {
+    constexpr int NP = Ord<N>::NP;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= K * NP) return;
+    const int64_t k = i / NP;
+    const int n = (int)(i % NP);
+    const double r = rst[3 * n], s = rst[3 * n + 1], t = rst[3 * n + 2];
+    const double l0 = -(1.0 + r + s + t) * 0.5, l1 = (1.0 + r) * 0.5, l2 = (1.0 + s) * 0.5, l3 = (1.0 + t) * 0.5;
+    const double *v = cellv + 12 * k;
+    const double x = l0 * v[0] + l1 * v[3] + l2 * v[6] + l3 * v[9];
+    const double y = l0 * v[1] + l1 * v[4] + l2 * v[7] + l3 * v[10];
+    const double z = l0 * v[2] + l1 * v[5] + l2 * v[8] + l3 * v[11];
+    const double d2 = (x - x0) * (x - x0) + (y - y0) * (y - y0) + (z - z0) * (z - z0);
+    float *qk = q + k * 4 * NP;
+    qk[n] = (float)(amp * exp(-d2 / (w * w)));
+    qk[NP + n] = 0.f;
+    qk[2 * NP + n] = 0.f;
+    qk[3 * NP + n] = 0.f;
+}
+
+// Energy: per cell |J| [p^T M p /(2 rho c^2) + rho/2 sum u^T M u], FP64 accumulation.
+template <int N>
+__global__ void __launch_bounds__(256) k_energy_partial(const float *q, const float *Mref, const double *ew, int64_t K,
+                                                        double *partial) {
+    constexpr int NP = Ord<N>::NP;
+    __shared__ float sM[NP * NP];
+    __shared__ double red[256];
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sM[i] = Mref[i];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < K * 4; it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = it / 4;
+        const int fl = (int)(it % 4);
+        const float *x = q + k * 4 * NP + fl * NP;
+        double s = 0.0;
+        for (int n = 0; n < NP; ++n) {
+            float y = 0.f;
+            for (int m = 0; m < NP; ++m) y += sM[n * NP + m] * x[m];
+            s += (double)x[n] * (double)y;
+        }
+        acc += s * ew[2 * k + (fl == 0 ? 0 : 1)];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(const double *partial, int n, double *out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// Full auxiliary pressures for read-back.
+__global__ void k_full2(const float *q2, const float *q0, float *out, int64_t T, int P, int NP2) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = T * P * 3 * NP2;
+    if (i >= total) return;
+    const int64_t t = i / (P * 3 * NP2);
+    const int r = (int)(i % (3 * NP2));
+    const int fl = r / NP2, n = r % NP2;
+    out[i] = q2[i] + (fl == 0 ? q0[t * NP2 + n] : 0.f);
+}
+
+__global__ void k_full1(const float *q1, const float *q0, const float *cP, float *out, int64_t L, int P, int NP1) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int S = P * P;
+    const int64_t total = L * S * 2 * NP1;
+    if (i >= total) return;
+    const int64_t l = i / (S * 2 * NP1);
+    const int r = (int)(i % (S * 2 * NP1));
+    const int s = r / (2 * NP1), fl = (r / NP1) % 2, n = r % NP1;
+    float v = q1[i];
+    if (fl == 0) {
+        const int a = s % P, b = s / P;
+        const float ca = cP[a], cb = cP[b], den = 1.0f / (1.0f + ca + cb);
+        v += (1.0f + cb) * den * q0[(l * 2 + 0) * P * NP1 + a * NP1 + n] + (1.0f + ca) * den * q0[(l * 2 + 1) * P * NP1 + b * NP1 + n];
+    }
+    out[i] = v;
+}
+
+}  // namespace dgh
