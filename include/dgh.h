@@ -61,6 +61,7 @@ extern "C" {
 #define DGH_ENOMEM       -2   /* device or host allocation failed */
 #define DGH_ECUDA        -3   /* CUDA runtime error (launch or asynchronous) */
 #define DGH_EUNSTABLE    -4   /* non-finite values detected by a check */
+#define DGH_ETIMEOUT     -5   /* a bounded device-side wait gave up (reported by dgh_sync) */
 #define DGH_ESTATE       -6   /* call not valid in the current state */
 #define DGH_EUNSUPPORTED -7   /* feature / order not compiled in */
 

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdgh.so")
 SOURCES = ["api.cu", "refelem.cpp", "meshsetup.cpp"]
-HEADERS = ["kernels.cuh", "setup.h", os.path.join("..", "..", "include", "dgh.h")]
+HEADERS = [os.path.join("..", "..", "include", "dgh.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -17,6 +17,7 @@ def _stale():
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.abspath(__file__)]
+    deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".cu", ".cpp"))]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

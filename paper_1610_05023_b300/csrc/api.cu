@@ -40,7 +40,7 @@ struct dgh_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int N = 0, P = 0, Np = 0, Nfp = 0, Np2 = 0, Np1 = 0;
-    int64_t K = 0, T = 0, L = 0, Fb = 0;
+    int64_t K = 0, K32 = 0, T = 0, L = 0, Fb = 0;
     int C = 0;
     int M = 1;
     double dt = 0.0, t0 = 0.0;
@@ -50,10 +50,11 @@ struct dgh_ctx {
     std::vector<DevBuf> bufs;
     int64_t device_bytes = 0;
     // 3D
-    float *q3 = nullptr, *res3 = nullptr, *tr3[2] = {nullptr, nullptr}, *geo3 = nullptr, *qb3 = nullptr;
+    float *q3 = nullptr, *res3 = nullptr, *tin3[2] = {nullptr, nullptr}, *trb = nullptr, *geo3 = nullptr;
+    int *d_err = nullptr;
     int *conn3 = nullptr;
     float *D3 = nullptr, *L3 = nullptr, *M3 = nullptr;
-    int *fmask3 = nullptr, *fperm3 = nullptr;
+    int *fmask3 = nullptr, *fperm3 = nullptr, *nslot3 = nullptr;
     double *cellv = nullptr, *rst = nullptr, *ew = nullptr;
     // 2D
     float *q2 = nullptr, *res2 = nullptr, *tr2[2] = {nullptr, nullptr}, *geo2 = nullptr, *qb2 = nullptr, *q0_3 = nullptr;
@@ -76,7 +77,7 @@ struct dgh_ctx {
     SrcParams src{};
     float *srcvec = nullptr;
     // launch shapes
-    int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1;
+    int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0;
     size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
     // graphs (one per trace parity)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -147,16 +148,19 @@ Args3 args3(dgh_ctx *c, int cur) {
     Args3 A;
     A.q = c->q3;
     A.res = c->res3;
-    A.tr_in = c->tr3[cur];
-    A.tr_out = c->tr3[cur ^ 1];
+    A.tin = c->tin3[cur];
+    A.tout = c->tin3[cur ^ 1];
+    A.trb = c->trb;
     A.geo = c->geo3;
     A.conn = c->conn3;
-    A.qb = c->qb3;
+    A.err = c->d_err;
+    A.K = c->K;
     A.D = c->D3;
     A.LIFT = c->L3;
     A.fmask = c->fmask3;
     A.fperm = c->fperm3;
-    A.K = c->K;
+    A.nslot = c->nslot3;
+    A.K32 = c->K32;
     A.src = c->src;
     A.src.vec = c->srcvec;
     return A;
@@ -172,8 +176,8 @@ Args2 args2(dgh_ctx *c, int cur, bool update) {
     A.conn = c->conn2;
     A.qb = c->qb2;
     A.q0 = c->q0_3;
-    A.qb3 = c->qb3;
-    A.tr3 = update ? c->tr3[cur ^ 1] : c->tr3[cur];
+    A.tin3 = update ? c->tin3[cur ^ 1] : c->tin3[cur];
+    A.trb = c->trb;
     A.tri_face = c->tri_face;
     A.tri_bface = c->tri_bface;
     A.D = c->D2;
@@ -213,6 +217,12 @@ Args1 args1(dgh_ctx *c, int cur, bool update) {
 template <int N>
 struct Launch3 {
     static int run(dgh_ctx *c, int cur, int stage, bool update) {
+        if (!update) {
+            const int64_t total = c->K * 4 * Cfg3<N>::NFP;
+            k3d_traces<N><<<int((total + 127) / 128), 128, 0, c->stream>>>(c->q3, c->geo3, c->conn3, c->fmask3, c->fperm3,
+                                                                           c->tin3[cur], c->trb, c->K);
+            return DGH_OK;
+        }
         StageCoef sc;
         sc.a = float(kRkA[stage]);
         sc.b = float(kRkB[stage]);
@@ -220,11 +230,7 @@ struct Launch3 {
         sc.c_dt = kRkC[stage] * c->dt;
         sc.time = c->d_time;
         Args3 A = args3(c, cur);
-        if (!update) A.tr_out = c->tr3[cur];
-        if (update)
-            k3d_stage<N, true><<<c->grid3, 256, c->smem3, c->stream>>>(A, sc);
-        else
-            k3d_stage<N, false><<<c->grid3, 256, c->smem3, c->stream>>>(A, sc);
+        k3d_stage<N><<<c->grid3, Cfg3<N>::NW * 32, Cfg3<N>::SMEM, c->stream>>>(A, sc);
         return DGH_OK;
     }
 };
@@ -283,17 +289,18 @@ void launch0(dgh_ctx *c, int cur_traces) {
 template <int N>
 struct SetAttrs {
     static int run(dgh_ctx *c) {
-        cudaFuncSetAttribute(k3d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3);
-        cudaFuncSetAttribute(k3d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3);
+        c->smem3 = Cfg3<N>::SMEM;
+        cudaFuncSetAttribute(k3d_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3);
         cudaFuncSetAttribute(k2d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem2);
         cudaFuncSetAttribute(k2d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem2);
         cudaFuncSetAttribute(k1d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem1);
         cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem1);
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N, true>, 256, c->smem3);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N>, Cfg3<N>::NW * 32, c->smem3);
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-        const int64_t tiles3 = (c->K + Ord<N>::TILE3 - 1) / Ord<N>::TILE3;
+        const int64_t tiles3 = c->K32;
+        c->occ3 = nb;
         c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)std::max(nb, 1) * sms));
         int nb2 = 0, nb1 = 0;
         if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, 256, c->smem2);
@@ -386,6 +393,25 @@ float *level_ptr(dgh_ctx *c, int level, bool res) {
     if (level == 3) return res ? c->res3 : c->q3;
     if (level == 2) return res ? c->res2 : c->q2;
     return res ? c->res1 : c->q1;
+}
+
+// canonical [K][4][Np] index -> interleaved [K32][4][Np][32] index
+inline size_t il3(const dgh_ctx *c, size_t i) {
+    const size_t per = size_t(4) * c->Np;
+    const size_t k = i / per, r = i % per;
+    return ((k / 32) * per + r) * 32 + (k % 32);
+}
+
+int copy_out3(dgh_ctx *c, const float *dptr, double *out, size_t n) {
+    std::vector<float> h(size_t(c->K32) * 32 * 4 * c->Np);
+    cudaError_t e = cudaMemcpyAsync(h.data(), dptr, h.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("device to host copy: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    for (size_t i = 0; i < n; ++i) out[i] = h[il3(c, i)];
+    return DGH_OK;
 }
 
 int copy_out(dgh_ctx *c, const float *dptr, double *out, size_t n) {
@@ -540,66 +566,102 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     const int Np = T3.Np, Nfp = T3.Nfp, Np2 = T2.Np, Np1 = T1.Np;
     int rc;
     // ---------------------------------------------------------------- 3D
+    // Cell-interleaved tiles of 32 cells: q, res [K32][4][Np][32], geometry
+    // [K32][GEO3][32], connectivity [K32][4][32]; traces [K32*32][4][2][Nfp].
+    ctx->K32 = (K + 31) / 32;
     {
-        std::vector<float> geo(size_t(K) * GEO3, 0.f);
-        std::vector<int> conn(size_t(K) * 4);
+        const int64_t K32 = ctx->K32, Kp = K32 * 32;
+        int NW = 1, C = 1, CP = 4;
+        switch (N) {
+            case 1: NW = Cfg3<1>::NW; C = Cfg3<1>::C; CP = Cfg3<1>::CP; break;
+            case 2: NW = Cfg3<2>::NW; C = Cfg3<2>::C; CP = Cfg3<2>::CP; break;
+            case 3: NW = Cfg3<3>::NW; C = Cfg3<3>::C; CP = Cfg3<3>::CP; break;
+            case 4: NW = Cfg3<4>::NW; C = Cfg3<4>::C; CP = Cfg3<4>::CP; break;
+            case 5: NW = Cfg3<5>::NW; C = Cfg3<5>::C; CP = Cfg3<5>::CP; break;
+            case 6: NW = Cfg3<6>::NW; C = Cfg3<6>::C; CP = Cfg3<6>::CP; break;
+        }
+        std::vector<float> geo(size_t(Kp) * GEO3, 0.f);
+        std::vector<int> conn(size_t(Kp) * 4);
         std::vector<double> cellv(size_t(K) * 12), ew(size_t(K) * 2);
-        for (int64_t k = 0; k < K; ++k) {
-            float *g = &geo[size_t(k) * GEO3];
-            for (int q = 0; q < 9; ++q) g[q] = float(m.drdx[9 * k + q]);
+        auto G = [&](int64_t k, int q) -> float & { return geo[(size_t(k / 32) * GEO3 + q) * 32 + (k % 32)]; };
+        auto CN = [&](int64_t k, int f) -> int & { return conn[(size_t(k / 32) * 4 + f) * 32 + (k % 32)]; };
+        for (int64_t k = 0; k < Kp; ++k) {
+            if (k >= K) {   // padding cells: identity metric, unit impedance, an ABC face 0
+                G(k, 0) = G(k, 4) = G(k, 8) = 1.f;
+                for (int f = 0; f < 4; ++f) {
+                    G(k, 9 + f) = 1.f;
+                    CN(k, f) = -1;
+                }
+                G(k, 13) = G(k, 14) = G(k, 15) = 1.f;
+                continue;
+            }
+            for (int q = 0; q < 9; ++q) G(k, q) = float(m.drdx[9 * k + q]);
             const double Z = m.rho[k] * m.c[k];
             for (int f = 0; f < 4; ++f) {
-                float *gf = g + 9 + 7 * f;
-                for (int i = 0; i < 3; ++i) gf[i] = float(m.nrm[12 * k + 3 * f + i]);
-                gf[3] = float(m.fscale[4 * k + f]);
                 const int64_t nb = m.nbr[4 * k + f];
                 double Zp = Z;
                 if (nb >= 0) Zp = m.rho[nb / 4] * m.c[nb / 4];
-                gf[4] = float(Z / (Z + Zp));
-                gf[5] = float(Z * Zp / (Z + Zp));
-                gf[6] = float(1.0 / (Z + Zp));
+                G(k, 9 + f) = float(Zp);
                 if (nb >= 0) {
-                    conn[4 * k + f] = int((nb << 3) | m.nbrSigma[4 * k + f]);
+                    CN(k, f) = int((nb << 3) | m.nbrSigma[4 * k + f]);
                 } else {
                     const int64_t b = m.bfaceOf[4 * k + f];
                     const int dir = m.bc[m.bfaceDom[b]] == BC_DIRICHLET ? 1 : 0;
-                    conn[4 * k + f] = int(-1 - ((b << 1) | dir));
+                    CN(k, f) = int(-1 - ((b << 1) | dir));
                 }
             }
-            g[37] = float(m.rho[k] * m.c[k] * m.c[k]);
-            g[38] = float(1.0 / m.rho[k]);
-            g[39] = float(Z);
+            G(k, 13) = float(m.rho[k] * m.c[k] * m.c[k]);
+            G(k, 14) = float(1.0 / m.rho[k]);
+            G(k, 15) = float(Z);
             for (int v = 0; v < 4; ++v)
                 for (int dd = 0; dd < 3; ++dd) cellv[12 * k + 3 * v + dd] = m.VX[3 * m.EToV[4 * k + v] + dd];
             ew[2 * k] = std::fabs(m.J[k]) / (2.0 * m.rho[k] * m.c[k] * m.c[k]);
             ew[2 * k + 1] = std::fabs(m.J[k]) * 0.5 * m.rho[k];
         }
-        std::vector<float> D(size_t(3) * Np * Np), Lf(size_t(4) * Nfp * Np), Mf(size_t(Np) * Np);
+        // D rows of output chunk w (nodes w*C .. w*C+C-1), padded to CP: [m][j][w][CP]
+        std::vector<float> D(size_t(Np) * 3 * NW * CP, 0.f), Lf(size_t(4) * Nfp * NW * CP, 0.f), Mf(size_t(Np) * Np);
         const Mat *Dj[3] = {&T3.Dr, &T3.Ds, &T3.Dt};
-        for (int j = 0; j < 3; ++j)
-            for (int n = 0; n < Np; ++n)
-                for (int mm = 0; mm < Np; ++mm) D[(size_t(j) * Np + mm) * Np + n] = float((*Dj[j])(n, mm));
-        for (int n = 0; n < Np; ++n)
-            for (int fm = 0; fm < 4 * Nfp; ++fm) Lf[size_t(fm) * Np + n] = float(T3.LIFT(n, fm));
+        for (int mm = 0; mm < Np; ++mm)
+            for (int j = 0; j < 3; ++j)
+                for (int w = 0; w < NW; ++w)
+                    for (int c = 0; c < C; ++c) {
+                        const int n = w * C + c;
+                        if (n < Np) D[((size_t(mm) * 3 + j) * NW + w) * CP + c] = float((*Dj[j])(n, mm));
+                    }
+        for (int fm = 0; fm < 4 * Nfp; ++fm)
+            for (int w = 0; w < NW; ++w)
+                for (int c = 0; c < C; ++c) {
+                    const int n = w * C + c;
+                    if (n < Np) Lf[(size_t(fm) * NW + w) * CP + c] = float(T3.LIFT(n, fm));
+                }
         for (size_t i = 0; i < Mf.size(); ++i) Mf[i] = float(T3.M.a[i]);
-        std::vector<int> fmask(4 * Nfp), fperm(6 * Nfp);
+        std::vector<int> fmask(4 * Nfp), fperm(6 * Nfp), nslot(size_t(Np) * 3, -1);
         for (int f = 0; f < 4; ++f)
-            for (int q = 0; q < Nfp; ++q) fmask[f * Nfp + q] = T3.Fmask[f][q];
-        for (int s = 0; s < 6; ++s)
-            for (int q = 0; q < Nfp; ++q) fperm[s * Nfp + q] = T3.facePerm[s][q];
+            for (int q = 0; q < Nfp; ++q) {
+                const int n = T3.Fmask[f][q];
+                fmask[f * Nfp + q] = n;
+                for (int sl = 0; sl < 3; ++sl)
+                    if (nslot[3 * n + sl] < 0) {
+                        nslot[3 * n + sl] = f * Nfp + q;
+                        break;
+                    }
+            }
+        for (int sg = 0; sg < 6; ++sg)
+            for (int q = 0; q < Nfp; ++q) fperm[sg * Nfp + q] = T3.facePerm[sg][q];
         std::vector<double> rst(size_t(3) * Np);
         for (int n = 0; n < Np; ++n) {
             rst[3 * n] = T3.r[n];
             rst[3 * n + 1] = T3.s[n];
             rst[3 * n + 2] = T3.t[n];
         }
-        if ((rc = dalloc(ctx, ctx->q3, size_t(K) * 4 * Np)) || (rc = dalloc(ctx, ctx->res3, size_t(K) * 4 * Np)) ||
-            (rc = dalloc(ctx, ctx->tr3[0], size_t(K) * 8 * Nfp)) || (rc = dalloc(ctx, ctx->tr3[1], size_t(K) * 8 * Nfp)) ||
-            (rc = dalloc(ctx, ctx->qb3, size_t(ctx->Fb) * Nfp)) || (rc = upload(ctx, ctx->geo3, geo)) ||
+        if ((rc = dalloc(ctx, ctx->q3, size_t(Kp) * 4 * Np)) || (rc = dalloc(ctx, ctx->res3, size_t(Kp) * 4 * Np)) ||
+            (rc = dalloc(ctx, ctx->tin3[0], size_t(Kp) * 8 * Nfp)) || (rc = dalloc(ctx, ctx->tin3[1], size_t(Kp) * 8 * Nfp)) ||
+            (rc = dalloc(ctx, ctx->trb, size_t(std::max<int64_t>(ctx->Fb, 1)) * 2 * Nfp)) ||
+            (rc = dalloc(ctx, ctx->d_err, 1)) || (rc = upload(ctx, ctx->geo3, geo)) ||
             (rc = upload(ctx, ctx->conn3, conn)) || (rc = upload(ctx, ctx->D3, D)) || (rc = upload(ctx, ctx->L3, Lf)) ||
             (rc = upload(ctx, ctx->M3, Mf)) || (rc = upload(ctx, ctx->fmask3, fmask)) ||
-            (rc = upload(ctx, ctx->fperm3, fperm)) || (rc = upload(ctx, ctx->cellv, cellv)) ||
-            (rc = upload(ctx, ctx->rst, rst)) || (rc = upload(ctx, ctx->ew, ew)))
+            (rc = upload(ctx, ctx->fperm3, fperm)) || (rc = upload(ctx, ctx->nslot3, nslot)) ||
+            (rc = upload(ctx, ctx->cellv, cellv)) || (rc = upload(ctx, ctx->rst, rst)) || (rc = upload(ctx, ctx->ew, ew)))
             return fail(rc, "");
     }
     // ---------------------------------------------------------------- 2D
@@ -740,15 +802,6 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     ctx->energy_blocks = 2 * 148;
     if ((rc = dalloc(ctx, ctx->partial, ctx->energy_blocks))) return fail(rc, "");
     // launch shapes
-    ctx->smem3 = 0;
-    switch (N) {
-        case 1: ctx->smem3 = k3d_smem<1>(); break;
-        case 2: ctx->smem3 = k3d_smem<2>(); break;
-        case 3: ctx->smem3 = k3d_smem<3>(); break;
-        case 4: ctx->smem3 = k3d_smem<4>(); break;
-        case 5: ctx->smem3 = k3d_smem<5>(); break;
-        case 6: ctx->smem3 = k3d_smem<6>(); break;
-    }
     ctx->tile2 = std::max(1, 256 / std::max(1, P * Np2));
     ctx->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
     ctx->smem2 = P ? k2d_smem(N, P, ctx->tile2) : 0;
@@ -843,6 +896,7 @@ int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp
     for (int lv = 1; lv <= 3; ++lv) {
         size_t n;
         level_count(ctx, lv, n);
+        if (lv == 3) n = size_t(ctx->K32) * 32 * 4 * ctx->Np;
         CK(cudaMemsetAsync(level_ptr(ctx, lv, false), 0, n * sizeof(float), ctx->stream));
         CK(cudaMemsetAsync(level_ptr(ctx, lv, true), 0, n * sizeof(float), ctx->stream));
     }
@@ -874,9 +928,16 @@ int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count) {
         return DGH_EINVAL;
     }
     if (n == 0) return DGH_OK;
-    std::vector<float> h(n);
-    for (size_t i = 0; i < n; ++i) h[i] = float(in[i]);
-    CK(cudaMemcpyAsync(level_ptr(ctx, level, false), h.data(), n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<float> h;
+    if (level == 3) {
+        h.assign(size_t(ctx->K32) * 32 * 4 * ctx->Np, 0.f);
+        for (size_t i = 0; i < n; ++i) h[il3(ctx, i)] = float(in[i]);
+    } else {
+        h.resize(n);
+        for (size_t i = 0; i < n; ++i) h[i] = float(in[i]);
+    }
+    CK(cudaMemcpyAsync(level_ptr(ctx, level, false), h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->dirty = true;
     return DGH_OK;
@@ -889,6 +950,7 @@ int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count) {
         ctx->err = "state size mismatch";
         return DGH_EINVAL;
     }
+    if (level == 3) return copy_out3(ctx, ctx->q3, out, n);
     return copy_out(ctx, level_ptr(ctx, level, false), out, n);
 }
 
@@ -899,7 +961,8 @@ int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count) {
         ctx->err = "field size mismatch";
         return DGH_EINVAL;
     }
-    if (level == 3 || n == 0) return copy_out(ctx, ctx->q3, out, n);
+    if (level == 3) return copy_out3(ctx, ctx->q3, out, n);
+    if (n == 0) return DGH_OK;
     if (ctx->dirty) {
         int rc = run_closure(ctx);
         if (rc) return rc;
@@ -1041,6 +1104,12 @@ int dgh_time_kernels(dgh_ctx *ctx, int64_t nsteps, double out_ms[5]) {
 int dgh_sync(dgh_ctx *ctx) {
     if (!ctx) return DGH_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
+    int err = 0;
+    CK(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        ctx->err = "a device-side wait timed out (stage kernel aborted)";
+        return DGH_ETIMEOUT;
+    }
     return DGH_OK;
 }
 
@@ -1066,7 +1135,7 @@ int dgh_get_energy(dgh_ctx *ctx, double *E) {
 int dgh_save_state(dgh_ctx *ctx, void *buf, size_t *size) {
     if (!ctx || !size) return DGH_EINVAL;
     size_t n3, n2, n1;
-    level_count(ctx, 3, n3);
+    n3 = size_t(ctx->K32) * 32 * 4 * ctx->Np;   // raw interleaved arrays
     level_count(ctx, 2, n2);
     level_count(ctx, 1, n1);
     const size_t header = 8 * sizeof(int64_t);
@@ -1101,7 +1170,7 @@ int dgh_save_state(dgh_ctx *ctx, void *buf, size_t *size) {
 int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size) {
     if (!ctx || !buf) return DGH_EINVAL;
     size_t n3, n2, n1;
-    level_count(ctx, 3, n3);
+    n3 = size_t(ctx->K32) * 32 * 4 * ctx->Np;
     level_count(ctx, 2, n2);
     level_count(ctx, 1, n1);
     const size_t header = 8 * sizeof(int64_t);

@@ -28,10 +28,8 @@ struct Ord {
     static constexpr int NP2 = (N + 1) * (N + 2) / 2;
     static constexpr int NFP2 = N + 1;
     static constexpr int NP1 = N + 1;
-    static constexpr int TILE3 = (256 / NP) > 0 ? (256 / NP) : 1;
 };
 
-constexpr int GEO3 = 40;   // per tet: drdx[9], 4 x (nx,ny,nz,fscale,wm,zz,iz), rho c^2, 1/rho, Z
 constexpr int GEO2 = 28;   // per tri: drdx[4], 3 x (nx,ny,fscale,wm,zz,iz), rho c^2, 1/rho, Z, pad[3]
 constexpr int GEO1 = 16;   // per line: rx, fscale, rho c^2, 1/rho, Z, ZA, ZB, 2 x (wm,zz,iz), pad[3]
 constexpr int MAXP = 8;
@@ -50,21 +48,6 @@ struct StageCoef {
     const double *time;     // device: time at the start of the step
 };
 
-struct Args3 {
-    float *q, *res;
-    const float *tr_in;
-    float *tr_out;
-    const float *geo;
-    const int *conn;        // >=0: (k'*4+f')<<3 | sigma ; <0: -1 - (bidx<<1 | dirichlet)
-    const float *qb;        // [Fb][Nfp]
-    const float *D;         // [3][Np(m)][Np(n)]  D_j[n][m] stored at (j*Np + m)*Np + n
-    const float *LIFT;      // [4Nfp(fm)][Np(n)]
-    const int *fmask;       // [4][Nfp]
-    const int *fperm;       // [6][Nfp]
-    int64_t K;
-    SrcParams src;
-};
-
 struct Args2 {
     float *q, *res;         // [T][P][3][Np2]
     const float *tr_in;     // [T][P][3][2][Nfp2]
@@ -73,8 +56,8 @@ struct Args2 {
     const int *conn;        // >=0: (t'*3+e')<<1 | flip ; -1: HABC edge (qb2) ; -2: Dirichlet edge
     const float *qb;        // [T][3][P][Nfp2]  incoming 2D characteristic at domain-edge nodes
     float *q0;              // [T][Np2]         r^- + r^+ of the 3D field at the triangle nodes
-    float *qb3;             // [Fb][Nfp]        out: incoming 3D characteristic
-    const float *tr3;       // new 3D traces [K][4][2][Nfp]
+    float *tin3;            // out: 3D incoming traces [K32][4][2][Nfp][32], exterior state (2 r^-, 0)
+    const float *trb;       // own 3D traces of the boundary faces [Fb][2][Nfp]
     const int *tri_face;    // [T] global face id k*4+f of the owning tet face
     const int *tri_bface;   // [T] boundary face index
     const float *D;         // [2][Np2(m)][Np2(n)]
@@ -123,181 +106,9 @@ __device__ __forceinline__ double ricker_integral_d(double t, double f, double t
     return (t - ts) * exp(-a * a);
 }
 
-// ==================================================================== 3D
-// Contravariant fluxes fr, fs, ft; face flux terms; volume + lift; update.
-template <int N, bool UPDATE>
-__global__ void __launch_bounds__(256) k3d_stage(Args3 A, StageCoef sc) {
-    using O = Ord<N>;
-    constexpr int NP = O::NP, NFP = O::NFP, TILE = O::TILE3, NF = 4 * NFP;
-    extern __shared__ float sm[];
-    float *sD = sm;                        // 3*NP*NP
-    float *sL = sD + 3 * NP * NP;          // NF*NP
-    float *sq = sL + NF * NP;              // TILE*4*NP
-    float *sf = sq + TILE * 4 * NP;        // TILE*3*NP
-    float *sx = sf + TILE * 3 * NP;        // TILE*2*NF
-    float *sg = sx + TILE * 2 * NF;        // TILE*GEO3
-    int *sfm = reinterpret_cast<int *>(sg + TILE * GEO3);  // 4*NFP
-    int *sfp = sfm + 4 * NFP;              // 6*NFP
-    const int tid = threadIdx.x, nth = blockDim.x;
-
-    if (UPDATE) {
-        for (int i = tid; i < 3 * NP * NP; i += nth) sD[i] = A.D[i];
-        for (int i = tid; i < NF * NP; i += nth) sL[i] = A.LIFT[i];
-    }
-    for (int i = tid; i < 4 * NFP; i += nth) sfm[i] = A.fmask[i];
-    for (int i = tid; i < 6 * NFP; i += nth) sfp[i] = A.fperm[i];
-    const int64_t ntiles = (A.K + TILE - 1) / TILE;
-    double tstage = 0.0;
-    if (UPDATE && A.src.n > 0) tstage = sc.time[0] + sc.c_dt;
-
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t k0 = tile * TILE;
-        const int ne = (int)((A.K - k0) < TILE ? (A.K - k0) : TILE);
-        __syncthreads();
-        {
-            const float *src = A.q + k0 * 4 * NP;
-            for (int i = tid; i < ne * 4 * NP; i += nth) sq[i] = src[i];
-            const float *gsrc = A.geo + k0 * GEO3;
-            for (int i = tid; i < ne * GEO3; i += nth) sg[i] = gsrc[i];
-        }
-        __syncthreads();
-        if (!UPDATE) {
-            // traces of the current fields only
-            for (int i = tid; i < ne * NF; i += nth) {
-                const int e = i / NF, fm = i % NF, f = fm / NFP, m = fm % NFP;
-                const int n = sfm[f * NFP + m];
-                const float *g = sg + e * GEO3 + 9 + 7 * f;
-                const float *qe = sq + e * 4 * NP;
-                const float un = g[0] * qe[NP + n] + g[1] * qe[2 * NP + n] + g[2] * qe[3 * NP + n];
-                float *dst = A.tr_out + ((k0 + e) * 4 + f) * 2 * NFP;
-                dst[m] = qe[n];
-                dst[NFP + m] = un;
-            }
-            continue;
-        }
-        // contravariant fluxes f_j = sum_i dr_j/dx_i u_i
-        for (int i = tid; i < ne * NP; i += nth) {
-            const int e = i / NP, n = i % NP;
-            const float *qe = sq + e * 4 * NP;
-            const float *g = sg + e * GEO3;
-            const float u = qe[NP + n], v = qe[2 * NP + n], w = qe[3 * NP + n];
-            float *fe = sf + e * 3 * NP;
-            fe[n] = g[0] * u + g[1] * v + g[2] * w;
-            fe[NP + n] = g[3] * u + g[4] * v + g[5] * w;
-            fe[2 * NP + n] = g[6] * u + g[7] * v + g[8] * w;
-        }
-        // upwind flux differences at the face nodes
-        for (int i = tid; i < ne * NF; i += nth) {
-            const int e = i / NF, fm = i % NF, f = fm / NFP, m = fm % NFP;
-            const int64_t k = k0 + e;
-            const int n = sfm[f * NFP + m];
-            const float *qe = sq + e * 4 * NP;
-            const float *g = sg + e * GEO3 + 9 + 7 * f;
-            const float pm = qe[n];
-            const float unm = g[0] * qe[NP + n] + g[1] * qe[2 * NP + n] + g[2] * qe[3 * NP + n];
-            const int c = A.conn[k * 4 + f];
-            float pp, unp;
-            if (c >= 0) {
-                const int nb = c >> 3, sg_ = c & 7;
-                const int mm = sfp[sg_ * NFP + m];
-                const float *tr = A.tr_in + (int64_t)nb * 2 * NFP;
-                pp = tr[mm];
-                unp = -tr[NFP + mm];
-            } else {
-                const int code = -1 - c;
-                if (code & 1) {          // p = 0: mirror state
-                    pp = -pm;
-                    unp = unm;
-                } else {                 // incoming characteristic r^- (0 for the basic ABC)
-                    pp = 2.0f * A.qb[(int64_t)(code >> 1) * NFP + m];
-                    unp = 0.0f;
-                }
-            }
-            const float fs = g[3], wm = g[4], zz = g[5], iz = g[6];
-            const float dP = wm * (pp - pm) + zz * (unm - unp);
-            const float dUn = (1.0f - wm) * (unp - unm) + iz * (pm - pp);
-            sx[e * 2 * NF + fm] = fs * dUn;
-            sx[e * 2 * NF + NF + fm] = fs * dP;
-        }
-        __syncthreads();
-        float qn[4];
-        int my_e = -1, my_n = 0;
-        for (int i = tid; i < ne * NP; i += nth) {   // one item per thread (nth >= TILE*NP)
-            const int e = i / NP, n = i % NP;
-            my_e = e;
-            my_n = n;
-            const float *qe = sq + e * 4 * NP;
-            const float *fe = sf + e * 3 * NP;
-            float div = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
-#pragma unroll 5
-            for (int m = 0; m < NP; ++m) {
-                const float dr = sD[m * NP + n], ds = sD[(NP + m) * NP + n], dt = sD[(2 * NP + m) * NP + n];
-                const float p = qe[m];
-                div += dr * fe[m] + ds * fe[NP + m] + dt * fe[2 * NP + m];
-                dpr += dr * p;
-                dps += ds * p;
-                dpt += dt * p;
-            }
-            const float *xe = sx + e * 2 * NF;
-            float lun = 0.f, lp[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int f = 0; f < 4; ++f) {
-#pragma unroll 5
-                for (int m = 0; m < NFP; ++m) {
-                    const float l = sL[(f * NFP + m) * NP + n];
-                    lun += l * xe[f * NFP + m];
-                    lp[f] += l * xe[NF + f * NFP + m];
-                }
-            }
-            const float *g = sg + e * GEO3;
-            const float rc2 = g[37], irho = g[38];
-            float rhs[4];
-            rhs[0] = -rc2 * (div + lun);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float grad = g[d] * dpr + g[3 + d] * dps + g[6 + d] * dpt;
-                const float lift = g[9 + d] * lp[0] + g[16 + d] * lp[1] + g[23 + d] * lp[2] + g[30 + d] * lp[3];
-                rhs[1 + d] = -irho * (grad + lift);
-            }
-            const int64_t k = k0 + e;
-            for (int s = 0; s < A.src.n; ++s)
-                if (A.src.cell[s] == k)
-                    rhs[0] += (float)(A.src.amp[s] * ricker_integral_d(tstage, A.src.f_peak[s], A.src.t_s[s])) *
-                              A.src.vec[s * NP + n];
-            float *qg = A.q + k * 4 * NP;
-            float *rg = A.res + k * 4 * NP;
-#pragma unroll
-            for (int fl = 0; fl < 4; ++fl) {
-                const float r = sc.a * rg[fl * NP + n] + sc.dt * rhs[fl];
-                rg[fl * NP + n] = r;
-                qn[fl] = qe[fl * NP + n] + sc.b * r;
-                qg[fl * NP + n] = qn[fl];
-            }
-        }
-        __syncthreads();
-        if (my_e >= 0)
-#pragma unroll
-            for (int fl = 0; fl < 4; ++fl) sq[my_e * 4 * NP + fl * NP + my_n] = qn[fl];
-        __syncthreads();
-        for (int i = tid; i < ne * NF; i += nth) {
-            const int e = i / NF, fm = i % NF, f = fm / NFP, m = fm % NFP;
-            const int n = sfm[f * NFP + m];
-            const float *g = sg + e * GEO3 + 9 + 7 * f;
-            const float *qe = sq + e * 4 * NP;
-            const float un = g[0] * qe[NP + n] + g[1] * qe[2 * NP + n] + g[2] * qe[3 * NP + n];
-            float *dst = A.tr_out + ((k0 + e) * 4 + f) * 2 * NFP;
-            dst[m] = qe[n];
-            dst[NFP + m] = un;
-        }
-    }
-}
-
-template <int N>
-constexpr size_t k3d_smem() {
-    using O = Ord<N>;
-    return sizeof(float) * (3 * O::NP * O::NP + 4 * O::NFP * O::NP + O::TILE3 * (4 * O::NP + 3 * O::NP + 2 * 4 * O::NFP + GEO3)) +
-           sizeof(int) * (4 * O::NFP + 6 * O::NFP);
-}
+}  // namespace dgh
+#include "k3d.cuh"
+namespace dgh {
 
 // ==================================================================== 2D
 // One block handles a tile of triangles; items are (tri, set, node).
@@ -415,13 +226,17 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
         for (int i = tid; i < nt * NP2; i += nth) {
             const int t = i / NP2, n = i % NP2;
             const int64_t tg = t0 + t;
-            const float *tr = A.tr3 + (int64_t)A.tri_face[tg] * 2 * NP2;   // tet face traces (Nfp == Np2)
+            const float *tr = A.trb + (int64_t)A.tri_bface[tg] * 2 * NP2;   // tet face traces (Nfp == Np2)
             const float Z = sg[t * GEO2 + 24];
             const float rp = 0.5f * (tr[n] + Z * tr[NP2 + n]);
             float rm = 0.f;
             for (int a = 0; a < P; ++a) rm += A.cP[a] * sq[(t * P + a) * 3 * NP2 + n];
             rm *= A.invM;
-            A.qb3[(int64_t)A.tri_bface[tg] * NP2 + n] = rm;
+            {
+                const int64_t gf = A.tri_face[tg], kc = gf >> 2;
+                const int fc = (int)(gf & 3);
+                A.tin3[(((kc >> 5) * 4 + fc) * 2 * NP2 + n) * 32 + (kc & 31)] = 2.0f * rm;   // exterior p; n.u = 0
+            }
             const float q0 = rm + rp;
             A.q0[tg * NP2 + n] = q0;
             s0[t * NP2 + n] = q0;
@@ -641,11 +456,11 @@ __global__ void k_init_gaussian(float *q, const double *cellv, const double *rst
     const double y = l0 * v[1] + l1 * v[4] + l2 * v[7] + l3 * v[10];
     const double z = l0 * v[2] + l1 * v[5] + l2 * v[8] + l3 * v[11];
     const double d2 = (x - x0) * (x - x0) + (y - y0) * (y - y0) + (z - z0) * (z - z0);
-    float *qk = q + k * 4 * NP;
-    qk[n] = (float)(amp * exp(-d2 / (w * w)));
-    qk[NP + n] = 0.f;
-    qk[2 * NP + n] = 0.f;
-    qk[3 * NP + n] = 0.f;
+    float *qk = q + (k / 32) * (4 * NP * 32) + (k % 32);   // cell-interleaved [K/32][4][Np][32]
+    qk[n * 32] = (float)(amp * exp(-d2 / (w * w)));
+    qk[(NP + n) * 32] = 0.f;
+    qk[(2 * NP + n) * 32] = 0.f;
+    qk[(3 * NP + n) * 32] = 0.f;
 }
 
 // Energy: per cell |J| [p^T M p /(2 rho c^2) + rho/2 sum u^T M u], FP64 accumulation.
@@ -661,12 +476,12 @@ __global__ void __launch_bounds__(256) k_energy_partial(const float *q, const fl
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < K * 4; it += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = it / 4;
         const int fl = (int)(it % 4);
-        const float *x = q + k * 4 * NP + fl * NP;
+        const float *x = q + (k / 32) * (4 * NP * 32) + fl * NP * 32 + (k % 32);   // stride 32 between nodes
         double s = 0.0;
         for (int n = 0; n < NP; ++n) {
             float y = 0.f;
-            for (int m = 0; m < NP; ++m) y += sM[n * NP + m] * x[m];
-            s += (double)x[n] * (double)y;
+            for (int m = 0; m < NP; ++m) y += sM[n * NP + m] * x[m * 32];
+            s += (double)x[n * 32] * (double)y;
         }
         acc += s * ew[2 * k + (fl == 0 ? 0 : 1)];
     }
