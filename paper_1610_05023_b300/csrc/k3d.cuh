@@ -193,31 +193,37 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
         float nrm[4][4];    // outward normal and Fscale of the 4 faces
 #pragma unroll
         for (int f = 0; f < 4; ++f) face_normal(g, f, nrm[f][0], nrm[f][1], nrm[f][2], nrm[f][3]);
-        // ---------------- face fluxes (slots f*NFP+m split over the warps)
-        for (int s = w * G::SPW; s < (w + 1) * G::SPW && s < NF; ++s) {
-            const int f = s / NFP, m = s % NFP;
-            const float nx = f == 0 ? nrm[0][0] : f == 1 ? nrm[1][0] : f == 2 ? nrm[2][0] : nrm[3][0];
-            const float ny = f == 0 ? nrm[0][1] : f == 1 ? nrm[1][1] : f == 2 ? nrm[2][1] : nrm[3][1];
-            const float nz = f == 0 ? nrm[0][2] : f == 1 ? nrm[1][2] : f == 2 ? nrm[2][2] : nrm[3][2];
-            const float fsc = f == 0 ? nrm[0][3] : f == 1 ? nrm[1][3] : f == 2 ? nrm[2][3] : nrm[3][3];
-            const float Zp = sG[(9 + f) * 32 + e];
-            const float wm = Zm / (Zm + Zp), zz = Zm * Zp / (Zm + Zp), iz = 1.0f / (Zm + Zp);
-            const int n = sFm[s];
-            const float pm = sQ[n * 32 + e];
-            const float unm = nx * sQ[(NP + n) * 32 + e] + ny * sQ[(2 * NP + n) * 32 + e] + nz * sQ[(3 * NP + n) * 32 + e];
-            float *xp_slot = sTi + ((2 * f) * NFP + m) * 32 + e;       // p slot -> Fscale dP
-            float *xu_slot = sTi + ((2 * f + 1) * NFP + m) * 32 + e;   // n.u slot -> Fscale dUn
-            float pp = *xp_slot;
-            float unp = *xu_slot;
-            const int c = sC[f * 32 + e];
-            if (c < 0 && ((-1 - c) & 1)) {   // p = 0 face: mirror state
-                pp = -pm;
-                unp = unm;
+        // ---------------- face fluxes (slots f*NFP+m split over the warps; per-face terms hoisted)
+        {
+            const int s0 = w * G::SPW, s1 = (s0 + G::SPW < NF) ? s0 + G::SPW : NF;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (f * NFP >= s1 || (f + 1) * NFP <= s0) continue;
+                const float nx = nrm[f][0], ny = nrm[f][1], nz = nrm[f][2], fsc = nrm[f][3];
+                const float Zp = sG[(9 + f) * 32 + e];
+                const float izs = 1.0f / (Zm + Zp);
+                const float wm = Zm * izs, zz = Zm * Zp * izs;
+                const int c = sC[f * 32 + e];
+                const bool dir = c < 0 && ((-1 - c) & 1);
+                const int m0 = (s0 > f * NFP) ? s0 - f * NFP : 0;
+                const int m1 = (s1 < (f + 1) * NFP) ? s1 - f * NFP : NFP;
+                for (int m = m0; m < m1; ++m) {
+                    const int n = sFm[f * NFP + m];
+                    const float pm = sQ[n * 32 + e];
+                    const float unm = nx * sQ[(NP + n) * 32 + e] + ny * sQ[(2 * NP + n) * 32 + e] + nz * sQ[(3 * NP + n) * 32 + e];
+                    float *xp_slot = sTi + ((2 * f) * NFP + m) * 32 + e;       // p slot -> Fscale dP
+                    float *xu_slot = sTi + ((2 * f + 1) * NFP + m) * 32 + e;   // n.u slot -> Fscale dUn
+                    float pp = *xp_slot, unp = *xu_slot;
+                    if (dir) {   // p = 0 face: mirror state
+                        pp = -pm;
+                        unp = unm;
+                    }
+                    const float dP = wm * (pp - pm) + zz * (unm - unp);
+                    const float dUn = (1.0f - wm) * (unp - unm) + izs * (pm - pp);
+                    *xu_slot = fsc * dUn;
+                    *xp_slot = fsc * dP;
+                }
             }
-            const float dP = wm * (pp - pm) + zz * (unm - unp);
-            const float dUn = (1.0f - wm) * (unp - unm) + iz * (pm - pp);
-            *xu_slot = fsc * dUn;
-            *xp_slot = fsc * dP;
         }
         __syncthreads();
         // ---------------- contravariant fluxes f_j = sum_i dr_j/dx_i u_i
