@@ -177,6 +177,26 @@ int dgh_sync(dgh_ctx *ctx);
  * reduced on the GPU with FP64 accumulation (synchronising). */
 int dgh_get_energy(dgh_ctx *ctx, double *E);
 
+/* Energy as dgh_get_energy, but the call allocates no memory at all: the
+ * per-block partial sums live in a fixed static device array of the library
+ * (65,536 doubles = 512 KiB, held on every GPU that loads the library until
+ * the process exits).  Meant for callers that cannot allocate device memory
+ * when they need the value -- code running while a CUDA graph is being
+ * captured, where cudaMalloc is not allowed, or code inside a framework whose
+ * memory pool owns the whole device.  The paper has no counterpart; it is a
+ * service of this library.
+ *  d_energy: DEVICE pointer to one double, owned by the caller, written on
+ *            `stream` (NULL = the context's stream); asynchronous, read it
+ *            after synchronising that stream.
+ *  Limit: at most 4,194,304 cells (65,536 partial sums of 256 (cell, field)
+ *         items); larger contexts get DGH_EINVAL with a message.
+ *  The first call on each device looks up the array's device address with
+ *  cudaGetSymbolAddress; make that first call outside any stream capture.
+ *  All calls share the one array (every partial sum is rewritten by each
+ *  call, nothing needs clearing), so calls whose kernels overlap on the GPU
+ *  -- e.g. on two streams at once -- race and must be serialised. */
+int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stream);
+
 /* Serialises the complete time-stepping state (all levels, residuals,
  * boundary algebra, time, step count) into buf.  Call with buf == NULL to
  * query the size in *size.  dgh_load_state restores it into a context

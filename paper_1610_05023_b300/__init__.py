@@ -78,6 +78,7 @@ def load_library(path=LIB_PATH):
         "dgh_sync": (ctypes.c_int, [P]),
         "dgh_time_kernels": (ctypes.c_int, [P, ctypes.c_int64, D]),
         "dgh_get_energy": (ctypes.c_int, [P, D]),
+        "dgh_get_energy_noalloc": (ctypes.c_int, [P, ctypes.c_void_p, P]),
         "dgh_save_state": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "dgh_load_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
     }
@@ -241,6 +242,13 @@ class Solver:
         e = ctypes.c_double()
         self._check(self._lib.dgh_get_energy(self._h, ctypes.byref(e)))
         return e.value
+
+    def energy_noalloc(self, d_out, stream=None):
+        """Energy written to the device double at address d_out (an int), with no
+        allocation inside the call (see dgh_get_energy_noalloc); asynchronous."""
+        sptr = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+        self._check(self._lib.dgh_get_energy_noalloc(self._h, ctypes.c_void_p(d_out),
+                                                     ctypes.c_void_p(sptr) if sptr else None))
 
     def save_state(self):
         size = ctypes.c_size_t(0)

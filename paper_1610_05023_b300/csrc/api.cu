@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1203,3 +1204,106 @@ int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Energy without any device allocation.
+//
+// Some callers cannot allocate device memory at the moment they want the
+// energy: code that runs while a CUDA graph is being captured (cudaMalloc is
+// not allowed inside a capture), or code embedded in a host framework whose
+// memory pool owns the whole device and forbids allocations outside it.  This
+// entry point therefore keeps its per-block partial sums in a fixed
+// file-scope device array instead of allocating them.  The array is
+// kNoAllocMaxPartials doubles (512 KiB) and stays resident on every GPU that
+// loads the library until the process exits.
+namespace {
+
+constexpr int64_t kNoAllocMaxPartials = 65536;
+constexpr int kNoAllocBlock = 256;
+__device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[256] = {};   // device address of g_noalloc_partials, per device ordinal
+
+// Per-device look-up of the array's device address (host code cannot use
+// the symbol itself as a device pointer).
+int noalloc_scratch(dgh_ctx *ctx, double **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        ctx->err = "device ordinal out of range for the static scratch table";
+        return DGH_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("cudaGetSymbolAddress(static energy scratch): ") + cudaGetErrorString(e);
+            return DGH_ECUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return DGH_OK;
+}
+
+// One block per kNoAllocBlock (cell, field) items; block b writes partial[b].
+template <int N>
+__global__ void __launch_bounds__(kNoAllocBlock) k_energy_partial_fixed(const float *q, const float *Mref, const double *ew,
+                                                                        int64_t K, double *partial) {
+    constexpr int NP = Ord<N>::NP;
+    __shared__ float sM[NP * NP];
+    __shared__ double red[kNoAllocBlock];
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sM[i] = Mref[i];
+    __syncthreads();
+    const int64_t it = blockIdx.x * (int64_t)kNoAllocBlock + threadIdx.x;
+    double acc = 0.0;
+    if (it < K * 4) {
+        const int64_t k = it / 4;
+        const int fl = (int)(it % 4);
+        const float *x = q + (k / 32) * (4 * NP * 32) + fl * NP * 32 + (k % 32);
+        for (int n = 0; n < NP; ++n) {
+            float y = 0.f;
+            for (int m = 0; m < NP; ++m) y += sM[n * NP + m] * x[m * 32];
+            acc += (double)x[n * 32] * (double)y;
+        }
+        acc *= ew[2 * k + (fl == 0 ? 0 : 1)];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kNoAllocBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+}  // namespace
+
+extern "C" int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stream) {
+    if (!ctx || !d_energy) return DGH_EINVAL;
+    const int64_t nblocks = (ctx->K * 4 + kNoAllocBlock - 1) / kNoAllocBlock;
+    if (nblocks > kNoAllocMaxPartials) {
+        ctx->err = "dgh_get_energy_noalloc: " + std::to_string(ctx->K) + " cells need " + std::to_string(nblocks) +
+                   " partial sums, more than the static scratch holds (" + std::to_string(kNoAllocMaxPartials) +
+                   ", i.e. at most " + std::to_string(kNoAllocMaxPartials * kNoAllocBlock / 4) + " cells)";
+        return DGH_EINVAL;
+    }
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(ctx, &scratch);
+    if (rc) return rc;
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    const int nb = (int)nblocks;
+    switch (ctx->N) {
+        case 1: k_energy_partial_fixed<1><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
+        case 2: k_energy_partial_fixed<2><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
+        case 3: k_energy_partial_fixed<3><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
+        case 4: k_energy_partial_fixed<4><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
+        case 5: k_energy_partial_fixed<5><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
+        case 6: k_energy_partial_fixed<6><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
+    }
+    k_sum_partials<<<1, 256, 0, s>>>(scratch, nb, d_energy);
+    CK(cudaGetLastError());
+    return DGH_OK;
+}
