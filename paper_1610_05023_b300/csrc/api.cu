@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -42,6 +43,10 @@ struct dgh_ctx {
     int device = 0;
     int N = 0, P = 0, Np = 0, Nfp = 0, Np2 = 0, Np1 = 0;
     int64_t K = 0, K32 = 0, T = 0, L = 0, Fb = 0;
+    int64_t Ki32 = 0, Kb32 = 0;       // 32-cell blocks of interior cells, then of cells with HABC faces
+    std::vector<int64_t> can2dev;     // canonical cell -> device cell slot
+    cudaStream_t side = nullptr;      // HABC chain stream (overlaps the interior 3D work)
+    cudaEvent_t ev3d[5] = {}, ev2d[5] = {}, evjoin = nullptr;
     int C = 0;
     int M = 1;
     double dt = 0.0, t0 = 0.0;
@@ -78,7 +83,8 @@ struct dgh_ctx {
     SrcParams src{};
     float *srcvec = nullptr;
     // launch shapes
-    int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0;
+    int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0, sms = 1;
+    unsigned long long *tile_ctr = nullptr;   // [11] block counters of the 3D launches of a step
     size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
     // graphs (one per trace parity)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -155,13 +161,13 @@ Args3 args3(dgh_ctx *c, int cur) {
     A.geo = c->geo3;
     A.conn = c->conn3;
     A.err = c->d_err;
-    A.K = c->K;
+    A.blk_begin = 0;
+    A.blk_end = c->K32;
     A.D = c->D3;
     A.LIFT = c->L3;
     A.fmask = c->fmask3;
     A.fperm = c->fperm3;
     A.nslot = c->nslot3;
-    A.K32 = c->K32;
     A.src = c->src;
     A.src.vec = c->srcvec;
     return A;
@@ -215,13 +221,15 @@ Args1 args1(dgh_ctx *c, int cur, bool update) {
     return A;
 }
 
+// part: 0 = all cells, 1 = interior blocks, 2 = blocks with HABC faces
 template <int N>
 struct Launch3 {
-    static int run(dgh_ctx *c, int cur, int stage, bool update) {
+    static int run(dgh_ctx *c, int cur, int stage, bool update, int part = 0, cudaStream_t st = nullptr) {
+        if (!st) st = c->stream;
         if (!update) {
-            const int64_t total = c->K * 4 * Cfg3<N>::NFP;
-            k3d_traces<N><<<int((total + 127) / 128), 128, 0, c->stream>>>(c->q3, c->geo3, c->conn3, c->fmask3, c->fperm3,
-                                                                           c->tin3[cur], c->trb, c->K);
+            const int64_t total = c->K32 * 32 * 4 * Cfg3<N>::NFP;
+            k3d_traces<N><<<int((total + 127) / 128), 128, 0, st>>>(c->q3, c->geo3, c->conn3, c->fmask3, c->fperm3,
+                                                                    c->tin3[cur], c->trb, c->K32 * 32);
             return DGH_OK;
         }
         StageCoef sc;
@@ -231,14 +239,23 @@ struct Launch3 {
         sc.c_dt = kRkC[stage] * c->dt;
         sc.time = c->d_time;
         Args3 A = args3(c, cur);
-        k3d_stage<N><<<c->grid3, Cfg3<N>::NW * 32, Cfg3<N>::SMEM, c->stream>>>(A, sc);
+        A.tile_ctr = c->tile_ctr + (part == 0 ? 10 : stage * 2 + (part - 1));
+        if (part == 0) cudaMemsetAsync(A.tile_ctr, 0, sizeof(unsigned long long), st);
+        if (part == 1) A.blk_end = c->Ki32;
+        if (part == 2) A.blk_begin = c->Ki32;
+        const int64_t nblk = A.blk_end - A.blk_begin;
+        if (nblk <= 0) return DGH_OK;
+        const int grid = (int)std::min<int64_t>(nblk, c->grid3);   // persistent CTAs, blocks claimed dynamically
+        A.max_tiles = int(std::min<int64_t>(nblk, int64_t(1) << 30));
+        k3d_stage<N><<<grid, Cfg3<N>::NW * 32, Cfg3<N>::SMEM, st>>>(A, sc);
         return DGH_OK;
     }
 };
 
 template <int N>
 struct Launch2 {
-    static int run(dgh_ctx *c, int cur, int stage, bool update) {
+    static int run(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st = nullptr) {
+        if (!st) st = c->stream;
         if (c->T == 0) return DGH_OK;
         StageCoef sc;
         sc.a = float(kRkA[stage]);
@@ -248,16 +265,17 @@ struct Launch2 {
         sc.time = c->d_time;
         Args2 A = args2(c, cur, update);
         if (update)
-            k2d_stage<N, true><<<c->grid2, 256, c->smem2, c->stream>>>(A, sc, c->tile2);
+            k2d_stage<N, true><<<c->grid2, 256, c->smem2, st>>>(A, sc, c->tile2);
         else
-            k2d_stage<N, false><<<c->grid2, 256, c->smem2, c->stream>>>(A, sc, c->tile2);
+            k2d_stage<N, false><<<c->grid2, 256, c->smem2, st>>>(A, sc, c->tile2);
         return DGH_OK;
     }
 };
 
 template <int N>
 struct Launch1 {
-    static int run(dgh_ctx *c, int cur, int stage, bool update) {
+    static int run(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st = nullptr) {
+        if (!st) st = c->stream;
         if (c->L == 0) return DGH_OK;
         StageCoef sc;
         sc.a = float(kRkA[stage]);
@@ -267,14 +285,15 @@ struct Launch1 {
         sc.time = c->d_time;
         Args1 A = args1(c, cur, update);
         if (update)
-            k1d_stage<N, true><<<c->grid1, 256, c->smem1, c->stream>>>(A, sc, c->tile1);
+            k1d_stage<N, true><<<c->grid1, 256, c->smem1, st>>>(A, sc, c->tile1);
         else
-            k1d_stage<N, false><<<c->grid1, 256, c->smem1, c->stream>>>(A, sc, c->tile1);
+            k1d_stage<N, false><<<c->grid1, 256, c->smem1, st>>>(A, sc, c->tile1);
         return DGH_OK;
     }
 };
 
-void launch0(dgh_ctx *c, int cur_traces) {
+void launch0(dgh_ctx *c, int cur_traces, cudaStream_t st = nullptr) {
+    if (!st) st = c->stream;
     if (c->C == 0) return;
     Args0 A;
     A.tr1 = c->tr1[cur_traces];
@@ -284,7 +303,7 @@ void launch0(dgh_ctx *c, int cur_traces) {
     A.Hc = c->Hc;
     A.P = c->P;
     A.C = c->C;
-    k0d_stage<<<c->C, 128, c->smem0, c->stream>>>(A);
+    k0d_stage<<<c->C, 128, c->smem0, st>>>(A);
 }
 
 template <int N>
@@ -302,6 +321,7 @@ struct SetAttrs {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         const int64_t tiles3 = c->K32;
         c->occ3 = nb;
+        c->sms = sms;
         c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)std::max(nb, 1) * sms));
         int nb2 = 0, nb1 = 0;
         if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, 256, c->smem2);
@@ -333,20 +353,38 @@ int run_closure(dgh_ctx *c) {
     return DGH_OK;
 }
 
-// The 20 stage launches of one step plus the time advance; cur flips once
-// per stage, so a step starting from cur ends with cur ^ 1.
-int enqueue_step(dgh_ctx *c, int cur) {
+// The stage launches of one step plus the time advance; cur flips once per
+// stage, so a step starting from cur ends with cur ^ 1.  With overlap, the
+// HABC chain of stage s (2D, 1D, 0D kernels) runs on the side stream while
+// the interior cells of stage s+1 are computed on the main stream; the cells
+// with HABC faces of stage s+1 wait for the 2D kernel of stage s (it writes
+// their exterior states), and the 2D kernel of stage s+1 waits for them.
+int enqueue_step(dgh_ctx *c, int cur, bool overlap) {
+    cudaStream_t ms = c->stream, ss = overlap ? c->side : c->stream;
+    cudaMemsetAsync(c->tile_ctr, 0, 10 * sizeof(unsigned long long), ms);
     for (int s = 0; s < 5; ++s) {
-        int rc = dispatchN<Launch3>(c->N, c, cur, s, true);
+        int rc = dispatchN<Launch3>(c->N, c, cur, s, true, 1, ms);
         if (rc) return rc;
-        rc = dispatchN<Launch2>(c->N, c, cur, s, true);
+        if (overlap && s > 0) cudaStreamWaitEvent(ms, c->ev2d[s - 1], 0);
+        rc = dispatchN<Launch3>(c->N, c, cur, s, true, 2, ms);
         if (rc) return rc;
-        rc = dispatchN<Launch1>(c->N, c, cur, s, true);
+        if (overlap) {
+            cudaEventRecord(c->ev3d[s], ms);
+            cudaStreamWaitEvent(ss, c->ev3d[s], 0);
+        }
+        rc = dispatchN<Launch2>(c->N, c, cur, s, true, ss);
         if (rc) return rc;
-        launch0(c, cur ^ 1);
+        if (overlap) cudaEventRecord(c->ev2d[s], ss);
+        rc = dispatchN<Launch1>(c->N, c, cur, s, true, ss);
+        if (rc) return rc;
+        launch0(c, cur ^ 1, ss);
         cur ^= 1;
     }
-    k_advance_time<<<1, 1, 0, c->stream>>>(c->d_time, c->d_step, c->dt);
+    k_advance_time<<<1, 1, 0, ms>>>(c->d_time, c->d_step, c->dt);
+    if (overlap) {
+        cudaEventRecord(c->evjoin, ss);
+        cudaStreamWaitEvent(ms, c->evjoin, 0);
+    }
     return DGH_OK;
 }
 
@@ -366,7 +404,7 @@ int build_graph(dgh_ctx *c, int cur) {
         c->err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
         return DGH_ECUDA;
     }
-    int rc = enqueue_step(c, cur);
+    int rc = enqueue_step(c, cur, true);
     e = cudaStreamEndCapture(cs, &g);
     if (rc) return rc;
     if (e != cudaSuccess) {
@@ -399,7 +437,7 @@ float *level_ptr(dgh_ctx *c, int level, bool res) {
 // canonical [K][4][Np] index -> interleaved [K32][4][Np][32] index
 inline size_t il3(const dgh_ctx *c, size_t i) {
     const size_t per = size_t(4) * c->Np;
-    const size_t k = i / per, r = i % per;
+    const size_t k = size_t(c->can2dev[i / per]), r = i % per;
     return ((k / 32) * per + r) * 32 + (k % 32);
 }
 
@@ -438,6 +476,12 @@ const char *dgh_last_error(const dgh_ctx *ctx) { return ctx ? ctx->err.c_str() :
 void dgh_destroy(dgh_ctx *ctx) {
     if (!ctx) return;
     drop_graphs(ctx);
+    for (int i = 0; i < 5; ++i) {
+        if (ctx->ev3d[i]) cudaEventDestroy(ctx->ev3d[i]);
+        if (ctx->ev2d[i]) cudaEventDestroy(ctx->ev2d[i]);
+    }
+    if (ctx->evjoin) cudaEventDestroy(ctx->evjoin);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     for (auto &b : ctx->bufs) cudaFree(b.p);
     delete ctx;
 }
@@ -569,7 +613,22 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     // ---------------------------------------------------------------- 3D
     // Cell-interleaved tiles of 32 cells: q, res [K32][4][Np][32], geometry
     // [K32][GEO3][32], connectivity [K32][4][32]; traces [K32*32][4][2][Nfp].
-    ctx->K32 = (K + 31) / 32;
+    // Device cell order: cells without HABC faces first, then cells with HABC
+    // faces (whose exterior state the 2D kernel writes), each group padded to
+    // whole 32-cell blocks, so the two groups can be launched separately.
+    {
+        std::vector<char> habc_cell(size_t(K), 0);
+        for (int64_t t = 0; t < m.Ktri; ++t) habc_cell[m.bface[m.triBface[t]] / 4] = 1;
+        int64_t ni = 0, nb = 0;
+        for (int64_t k = 0; k < K; ++k) (habc_cell[k] ? nb : ni)++;
+        ctx->Ki32 = (ni + 31) / 32;
+        ctx->Kb32 = (nb + 31) / 32;
+        ctx->K32 = ctx->Ki32 + ctx->Kb32;
+        ctx->can2dev.assign(size_t(K), -1);
+        int64_t pi = 0, pb = ctx->Ki32 * 32;
+        for (int64_t k = 0; k < K; ++k) ctx->can2dev[k] = habc_cell[k] ? pb++ : pi++;
+    }
+    if (ctx->K32 * 32 * 4 >= (int64_t(1) << 28)) return fail(DGH_EUNSUPPORTED, "too many cells for the 32-bit connectivity encoding");
     {
         const int64_t K32 = ctx->K32, Kp = K32 * 32;
         int NW = 1, C = 1, CP = 4;
@@ -582,42 +641,40 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
             case 6: NW = Cfg3<6>::NW; C = Cfg3<6>::C; CP = Cfg3<6>::CP; break;
         }
         std::vector<float> geo(size_t(Kp) * GEO3, 0.f);
-        std::vector<int> conn(size_t(Kp) * 4);
-        std::vector<double> cellv(size_t(K) * 12), ew(size_t(K) * 2);
-        auto G = [&](int64_t k, int q) -> float & { return geo[(size_t(k / 32) * GEO3 + q) * 32 + (k % 32)]; };
-        auto CN = [&](int64_t k, int f) -> int & { return conn[(size_t(k / 32) * 4 + f) * 32 + (k % 32)]; };
-        for (int64_t k = 0; k < Kp; ++k) {
-            if (k >= K) {   // padding cells: identity metric, unit impedance, an ABC face 0
-                G(k, 0) = G(k, 4) = G(k, 8) = 1.f;
-                for (int f = 0; f < 4; ++f) {
-                    G(k, 9 + f) = 1.f;
-                    CN(k, f) = -1;
-                }
-                G(k, 13) = G(k, 14) = G(k, 15) = 1.f;
-                continue;
-            }
-            for (int q = 0; q < 9; ++q) G(k, q) = float(m.drdx[9 * k + q]);
+        std::vector<int> conn(size_t(Kp) * 4, kPadConn);
+        std::vector<double> cellv(size_t(Kp) * 12, 0.0), ew(size_t(Kp) * 2, 0.0);
+        auto G = [&](int64_t kd, int q) -> float & { return geo[(size_t(kd / 32) * GEO3 + q) * 32 + (kd % 32)]; };
+        auto CN = [&](int64_t kd, int f) -> int & { return conn[(size_t(kd / 32) * 4 + f) * 32 + (kd % 32)]; };
+        // padding cells: identity metric, unit impedance (their results are never read)
+        for (int64_t kd = 0; kd < Kp; ++kd) {
+            G(kd, 0) = G(kd, 4) = G(kd, 8) = 1.f;
+            for (int f = 0; f < 4; ++f) G(kd, 9 + f) = 1.f;
+            G(kd, 13) = G(kd, 14) = G(kd, 15) = 1.f;
+        }
+        for (int64_t k = 0; k < K; ++k) {
+            const int64_t kd = ctx->can2dev[k];
+            for (int q = 0; q < 9; ++q) G(kd, q) = float(m.drdx[9 * k + q]);
             const double Z = m.rho[k] * m.c[k];
             for (int f = 0; f < 4; ++f) {
                 const int64_t nb = m.nbr[4 * k + f];
                 double Zp = Z;
                 if (nb >= 0) Zp = m.rho[nb / 4] * m.c[nb / 4];
-                G(k, 9 + f) = float(Zp);
+                G(kd, 9 + f) = float(Zp);
                 if (nb >= 0) {
-                    CN(k, f) = int((nb << 3) | m.nbrSigma[4 * k + f]);
+                    CN(kd, f) = int(((ctx->can2dev[nb / 4] * 4 + nb % 4) << 3) | m.nbrSigma[4 * k + f]);
                 } else {
                     const int64_t b = m.bfaceOf[4 * k + f];
                     const int dir = m.bc[m.bfaceDom[b]] == BC_DIRICHLET ? 1 : 0;
-                    CN(k, f) = int(-1 - ((b << 1) | dir));
+                    CN(kd, f) = int(-1 - ((b << 1) | dir));
                 }
             }
-            G(k, 13) = float(m.rho[k] * m.c[k] * m.c[k]);
-            G(k, 14) = float(1.0 / m.rho[k]);
-            G(k, 15) = float(Z);
+            G(kd, 13) = float(m.rho[k] * m.c[k] * m.c[k]);
+            G(kd, 14) = float(1.0 / m.rho[k]);
+            G(kd, 15) = float(Z);
             for (int v = 0; v < 4; ++v)
-                for (int dd = 0; dd < 3; ++dd) cellv[12 * k + 3 * v + dd] = m.VX[3 * m.EToV[4 * k + v] + dd];
-            ew[2 * k] = std::fabs(m.J[k]) / (2.0 * m.rho[k] * m.c[k] * m.c[k]);
-            ew[2 * k + 1] = std::fabs(m.J[k]) * 0.5 * m.rho[k];
+                for (int dd = 0; dd < 3; ++dd) cellv[12 * kd + 3 * v + dd] = m.VX[3 * m.EToV[4 * k + v] + dd];
+            ew[2 * kd] = std::fabs(m.J[k]) / (2.0 * m.rho[k] * m.c[k] * m.c[k]);
+            ew[2 * kd + 1] = std::fabs(m.J[k]) * 0.5 * m.rho[k];
         }
         // D rows of output chunk w (nodes w*C .. w*C+C-1), padded to CP: [m][j][w][CP]
         std::vector<float> D(size_t(Np) * 3 * NW * CP, 0.f), Lf(size_t(4) * Nfp * NW * CP, 0.f), Mf(size_t(Np) * Np);
@@ -698,7 +755,7 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
             g[22] = float(m.rho[k] * m.c[k] * m.c[k]);
             g[23] = float(1.0 / m.rho[k]);
             g[24] = float(Z);
-            tface[t] = int(gf);
+            tface[t] = int(ctx->can2dev[gf / 4] * 4 + gf % 4);
             tb[t] = int(m.triBface[t]);
         }
         std::vector<float> D(size_t(2) * Np2 * Np2), Lf(size_t(3) * (N + 1) * Np2);
@@ -797,7 +854,7 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
         if ((rc = upload(ctx, ctx->corner, cor)) || (rc = upload(ctx, ctx->cornerZ, cz))) return fail(rc, "");
     }
     // ---------------------------------------------------------------- misc
-    if ((rc = dalloc(ctx, ctx->d_time, 1)) || (rc = dalloc(ctx, ctx->d_step, 1)) ||
+    if ((rc = dalloc(ctx, ctx->tile_ctr, 11)) || (rc = dalloc(ctx, ctx->d_time, 1)) || (rc = dalloc(ctx, ctx->d_step, 1)) ||
         (rc = dalloc(ctx, ctx->srcvec, size_t(MAXSRC) * Np)) || (rc = dalloc(ctx, ctx->d_energy, 1)))
         return fail(rc, "");
     ctx->energy_blocks = 2 * 148;
@@ -809,6 +866,17 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     ctx->smem1 = P ? k1d_smem(N, P, ctx->tile1) : 0;
     ctx->smem0 = sizeof(float) * 3 * P * P;
     dispatchN<SetAttrs>(N, ctx);
+    {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi) != cudaSuccess) return fail(DGH_ECUDA, "side stream");
+
+    }
+    for (int i = 0; i < 5; ++i)
+        if (cudaEventCreateWithFlags(&ctx->ev3d[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev2d[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(DGH_ECUDA, "events");
+    if (cudaEventCreateWithFlags(&ctx->evjoin, cudaEventDisableTiming) != cudaSuccess) return fail(DGH_ECUDA, "events");
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(DGH_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
@@ -901,15 +969,15 @@ int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp
         CK(cudaMemsetAsync(level_ptr(ctx, lv, false), 0, n * sizeof(float), ctx->stream));
         CK(cudaMemsetAsync(level_ptr(ctx, lv, true), 0, n * sizeof(float), ctx->stream));
     }
-    const int64_t total = ctx->K * ctx->Np;
+    const int64_t total = ctx->K32 * 32 * ctx->Np;
     const int blocks = int((total + 255) / 256);
     switch (ctx->N) {
-        case 1: k_init_gaussian<1><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
-        case 2: k_init_gaussian<2><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
-        case 3: k_init_gaussian<3><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
-        case 4: k_init_gaussian<4><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
-        case 5: k_init_gaussian<5><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
-        case 6: k_init_gaussian<6><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K, x0[0], x0[1], x0[2], width, amp); break;
+        case 1: k_init_gaussian<1><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+        case 2: k_init_gaussian<2><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+        case 3: k_init_gaussian<3><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+        case 4: k_init_gaussian<4><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+        case 5: k_init_gaussian<5><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+        case 6: k_init_gaussian<6><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
     }
     CK(cudaGetLastError());
     ctx->step_count = 0;
@@ -1011,7 +1079,7 @@ int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double
             }
             const int s = ctx->src.n;
             CK(cudaMemcpy(ctx->srcvec + size_t(s) * Np, vec.data(), Np * sizeof(float), cudaMemcpyHostToDevice));
-            ctx->src.cell[s] = k;
+            ctx->src.cell[s] = ctx->can2dev[k];
             ctx->src.f_peak[s] = f_peak;
             ctx->src.t_s[s] = t_s;
             ctx->src.amp[s] = amp;
@@ -1039,7 +1107,7 @@ int dgh_step(dgh_ctx *ctx, int64_t nsteps) {
             }
             CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
         } else {
-            int rc = enqueue_step(ctx, ctx->cur);
+            int rc = enqueue_step(ctx, ctx->cur, false);
             if (rc) return rc;
         }
         ctx->cur ^= 1;   // 5 stages: odd number of trace swaps
@@ -1118,12 +1186,12 @@ int dgh_get_energy(dgh_ctx *ctx, double *E) {
     if (!ctx || !E) return DGH_EINVAL;
     const int nb = ctx->energy_blocks;
     switch (ctx->N) {
-        case 1: k_energy_partial<1><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
-        case 2: k_energy_partial<2><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
-        case 3: k_energy_partial<3><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
-        case 4: k_energy_partial<4><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
-        case 5: k_energy_partial<5><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
-        case 6: k_energy_partial<6><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, ctx->partial); break;
+        case 1: k_energy_partial<1><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+        case 2: k_energy_partial<2><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+        case 3: k_energy_partial<3><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+        case 4: k_energy_partial<4><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+        case 5: k_energy_partial<5><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+        case 6: k_energy_partial<6><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
     }
     k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, nb, ctx->d_energy);
     CK(cudaGetLastError());
@@ -1283,7 +1351,7 @@ __global__ void __launch_bounds__(kNoAllocBlock) k_energy_partial_fixed(const fl
 
 extern "C" int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stream) {
     if (!ctx || !d_energy) return DGH_EINVAL;
-    const int64_t nblocks = (ctx->K * 4 + kNoAllocBlock - 1) / kNoAllocBlock;
+    const int64_t nblocks = (ctx->K32 * 32 * 4 + kNoAllocBlock - 1) / kNoAllocBlock;
     if (nblocks > kNoAllocMaxPartials) {
         ctx->err = "dgh_get_energy_noalloc: " + std::to_string(ctx->K) + " cells need " + std::to_string(nblocks) +
                    " partial sums, more than the static scratch holds (" + std::to_string(kNoAllocMaxPartials) +
@@ -1296,12 +1364,12 @@ extern "C" int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stre
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
     const int nb = (int)nblocks;
     switch (ctx->N) {
-        case 1: k_energy_partial_fixed<1><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
-        case 2: k_energy_partial_fixed<2><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
-        case 3: k_energy_partial_fixed<3><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
-        case 4: k_energy_partial_fixed<4><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
-        case 5: k_energy_partial_fixed<5><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
-        case 6: k_energy_partial_fixed<6><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K, scratch); break;
+        case 1: k_energy_partial_fixed<1><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+        case 2: k_energy_partial_fixed<2><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+        case 3: k_energy_partial_fixed<3><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+        case 4: k_energy_partial_fixed<4><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+        case 5: k_energy_partial_fixed<5><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+        case 6: k_energy_partial_fixed<6><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
     }
     k_sum_partials<<<1, 256, 0, s>>>(scratch, nb, d_energy);
     CK(cudaGetLastError());

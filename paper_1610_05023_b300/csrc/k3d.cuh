@@ -28,6 +28,7 @@ namespace dgh {
 
 constexpr int GEO3 = 16;  // per cell (interleaved [16][32]): drdx[9], Z of the 4 neighbours, rho c^2, 1/rho, Z
 constexpr unsigned long long kWaitLimit = 1ull << 24;   // mbarrier polls before reporting a timeout
+constexpr int kPadConn = (int)0x80000000;               // connectivity of padding cells (no pushes)
 
 template <int N>
 struct Cfg3 {
@@ -63,8 +64,11 @@ struct Args3 {
     const int *fperm;        // [6][Nfp]
     const int *nslot;        // [Np][3] face slots (f*Nfp+m) of every node, -1 padded
     int *err;                // device error word (bounded waits)
-    int64_t K32;             // number of 32-cell blocks
-    int64_t K;               // number of real cells (the rest of the last block is padding)
+    int64_t blk_begin;       // 32-cell blocks [blk_begin, blk_end) handled by this launch
+    int64_t blk_end;
+    unsigned long long *tile_ctr;  // zeroed before the launch; CTAs claim blocks from it
+    int max_tiles;                 // blocks per CTA at most (CTAs retire regularly so that
+                                   // concurrent kernels of the HABC chain get SMs)
     SrcParams src;
 };
 
@@ -148,18 +152,21 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
     int *sNs = sFp + 6 * NFP;
     const int tid = threadIdx.x, nth = NW * 32;
     const int w = tid >> 5, e = tid & 31;
-    const int64_t G0 = gridDim.x;
-    const int64_t ntiles = A.K32;
+    const int64_t ntiles = A.blk_end;
 
+    // blocks are claimed dynamically (one atomic per block), so CTAs that start
+    // late -- e.g. behind a concurrent kernel of the HABC chain -- simply take
+    // fewer blocks
+    __shared__ int64_t s_blk[2];
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if ((int64_t)blockIdx.x < ntiles) issue_tile<N>(A, sS, &bar[0], blockIdx.x);
-        if (G::NSTAGE == 2 && (int64_t)blockIdx.x + G0 < ntiles) issue_tile<N>(A, sS + G::STAGE, &bar[1], blockIdx.x + G0);
+        for (int q = 0; q < G::NSTAGE; ++q) {
+            const int64_t b = q < A.max_tiles ? A.blk_begin + (int64_t)atomicAdd(A.tile_ctr, 1ull) : ntiles;
+            s_blk[q] = b;
+            if (b < ntiles) issue_tile<N>(A, sS + q * G::STAGE, &bar[q], b);
+        }
     }
     for (int i = tid; i < NP * 3 * NW * CP; i += nth) sD[i] = A.D[i];
     for (int i = tid; i < NF * NW * CP; i += nth) sL[i] = A.LIFT[i];
@@ -170,9 +177,10 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
     if (A.src.n > 0) tstage = sc.time[0] + sc.c_dt;
     __syncthreads();
 
-    int it = 0;
-    for (int64_t blk = blockIdx.x; blk < ntiles; blk += G0, ++it) {
+    for (int it = 0;; ++it) {
         const int st = G::NSTAGE == 2 ? (it & 1) : 0;
+        const int64_t blk = s_blk[st];
+        if (blk >= ntiles) break;
         float *sQ = sS + st * G::STAGE;
         float *sTi = sQ + QS;       // incoming traces, overwritten in place by the flux terms
         const float *sG = sTi + TI;
@@ -327,13 +335,14 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
 #pragma unroll
             for (int s = 0; s < G::MAXSLOT; ++s) {
                 const int slot = sNs[n * G::MAXSLOT + s];
-                if (slot < 0 || k >= A.K) break;
+                if (slot < 0) break;
                 const int f = slot / NFP, m = slot % NFP;
                 const float nx = f == 0 ? nrm[0][0] : f == 1 ? nrm[1][0] : f == 2 ? nrm[2][0] : nrm[3][0];
                 const float ny = f == 0 ? nrm[0][1] : f == 1 ? nrm[1][1] : f == 2 ? nrm[2][1] : nrm[3][1];
                 const float nz = f == 0 ? nrm[0][2] : f == 1 ? nrm[1][2] : f == 2 ? nrm[2][2] : nrm[3][2];
                 const float un = nx * qn[1] + ny * qn[2] + nz * qn[3];
                 const int cc = f == 0 ? cf0 : f == 1 ? cf1 : f == 2 ? cf2 : cf3;
+                if (cc == kPadConn) break;   // padding cell: nothing to push
                 if (cc >= 0) {   // neighbour face (k', f'): its node order, its normal
                     const int nb = cc >> 3;
                     const int64_t kn = nb >> 2;
@@ -350,7 +359,12 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
             }
         }
         __syncthreads();   // stage st (with the flux terms) is free again
-        if (tid == 0 && blk + G::NSTAGE * G0 < ntiles) issue_tile<N>(A, sS + st * G::STAGE, &bar[st], blk + G::NSTAGE * G0);
+        if (tid == 0) {
+            const int64_t b = it + G::NSTAGE < A.max_tiles ? A.blk_begin + (int64_t)atomicAdd(A.tile_ctr, 1ull) : ntiles;
+            s_blk[st] = b;
+            if (b < ntiles) issue_tile<N>(A, sS + st * G::STAGE, &bar[st], b);
+        }
+        __syncthreads();
     }
 }
 
@@ -375,6 +389,7 @@ __global__ void __launch_bounds__(128) k3d_traces(const float *q, const float *g
     const float p = qt[n * 32 + e];
     const float un = nx * qt[(NP + n) * 32 + e] + ny * qt[(2 * NP + n) * 32 + e] + nz * qt[(3 * NP + n) * 32 + e];
     const int cc = conn[(blk * 4 + f) * 32 + e];
+    if (cc == kPadConn) return;
     if (cc >= 0) {
         const int nb = cc >> 3;
         const int64_t kn = nb >> 2;
