@@ -143,6 +143,101 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+BATCH_SEED = 4000
+
+
+def run_batch_form(args):
+    """Batching form: 48 independent seeded problems (n ~ U{8..24} hexes per
+    axis, N ~ U{3,4,5}, P ~ U{2,4,6}, c = rho = 1, Ricker source f0 ~ U[2,6],
+    xs ~ U[-0.5,0.5]^3, t_s = 1.25/f0, each at its own CFL time step), all
+    advanced by the same number of steps.  Times (CUDA events on the launching
+    stream) the batch before and after the launch-shape autotuner, and the
+    same problems stepped one after another (each alone on the GPU, its own
+    graph).  Metric: sum of the problems' DOF x 5 stages x steps / time."""
+    import torch
+    import paper_1610_05023_b300 as dgh
+    from paper_1610_05023_b300 import workloads as W
+    torch.cuda.set_device(0)
+    probs = W.batch_problems(BATCH_SEED)
+    seq = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    solvers = []
+    for p in probs:
+        VX, EToV = W.kuhn_mesh(p["n"], 1.0, 0.02, seed=p["mesh_seed"])
+        s = dgh.Solver(VX, EToV, p["N"], p["P"], stream=seq)
+        s.add_point_source(p["xs"], p["f0"], p["t_s"])
+        solvers.append(s)
+    infos = [s.info for s in solvers]
+    ndof = sum(i["ndof"] for i in infos)
+    t1 = time.perf_counter()
+    b = dgh.Batch(solvers)
+    t2 = time.perf_counter()
+    bs = torch.cuda.ExternalStream(b.stream_handle)
+
+    def timed(stream, fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    b.step(args.warmup)
+    b.sync()
+    ms_untuned = timed(bs, lambda: b.step(args.steps))
+    t3 = time.perf_counter()
+    tune_before, tune_after = b.tune(steps=3)
+    t4 = time.perf_counter()
+    b.step(args.warmup)
+    b.sync()
+    try:
+        gid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        gid = "0"
+    clocks = ClockSampler(gid)
+    clocks.start()
+    ms_batch = timed(bs, lambda: b.step(args.steps))
+    clk = clocks.stop()
+    b.sync()
+    for s in solvers:
+        s.step(args.warmup)
+    ms_seq = timed(seq, lambda: [s.step(args.steps) for s in solvers])
+    n_prob, n_groups = b.counts
+    rate = lambda ms: ndof * 5 * args.steps / (ms * 1e-3)
+    groups = {}
+    for i, p in enumerate(probs):
+        groups.setdefault((p["N"], p["P"]), []).append(i)
+    per_group = 0
+    for (N, P), members in groups.items():
+        T = sum(infos[i]["n_tris"] for i in members)
+        L = sum(infos[i]["n_lines"] for i in members)
+        C = sum(infos[i]["n_corners"] for i in members)
+        per_group += 5 * (1 + (T > 0) + (L > 0) + (C > 0)) + 1
+    line = {
+        "form": "batch", "metric": METRIC, "value": rate(ms_batch), "unit": METRIC, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch48_seed%d" % BATCH_SEED, "problems": n_prob, "groups": n_groups,
+                   "ndof": ndof, "cells": sum(i["n_cells"] for i in infos),
+                   "recipe": "n~U{8..24}, N~U{3,4,5}, P~U{2,4,6}, Ricker f0~U[2,6], xs~U[-0.5,0.5]^3",
+                   "l2_policy": "inputs larger than L2"},
+        "untuned": {"value": rate(ms_untuned), "ms_per_step": ms_untuned / args.steps},
+        "sequential": {"value": rate(ms_seq), "ms_per_step": ms_seq / args.steps,
+                       "note": "the same problems one after another, each alone with its own graph"},
+        "speedup_vs_sequential": ms_seq / ms_batch,
+        "tuner": {"ms_before": tune_before, "ms_after": tune_after, "seconds": t4 - t3,
+                  "shapes": [b.launch(g) for g in range(n_groups)]},
+        "setup_seconds": {"problems": t1 - t0, "batch": t2 - t1},
+        "gpu_launches": per_group * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    for s in solvers:
+        s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -151,9 +246,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=48, help="hexes per axis (48 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="plain", choices=["plain", "batch"],
+                    help="batch: the batching form (48 independent problems) instead of the plain workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batch":
+        return run_batch_form(args)
 
     import torch
     import paper_1610_05023_b300 as dgh
@@ -222,12 +321,15 @@ def main():
     e2e_value = world * ndof * 5 * e2e_steps / (t1 - t0)
     state_bytes = q3.size * 4
 
-    launches_per_step = 5 * (1 + (info["n_tris"] > 0) + (info["n_lines"] > 0) + (info["n_corners"] > 0)) + 1
+    parts3 = 2 if info["n_tris"] > 0 else 1      # interior cells, then cells with HABC faces
+    launches_per_step = 5 * (parts3 + (info["n_tris"] > 0) + (info["n_lines"] > 0) + (info["n_corners"] > 0)) + 1
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, ndof=ndof, n_cells=K, n_tris=info["n_tris"], n_lines=info["n_lines"],
+        "config": dict(WORKLOAD, **({} if args.n == 48 else {"workload": "cube%d_N4_P6_gaussian" % args.n,
+                                                              "mesh": "%d^3 hex x 6 Kuhn tets" % args.n}),
+                       ndof=ndof, n_cells=K, n_tris=info["n_tris"], n_lines=info["n_lines"],
                        n_corners=info["n_corners"], dt=info["dt"],
                        l2_policy="inputs larger than L2 (state %.0f MB per array)" % (q3.size * 4 / 1e6),
                        parallelism="replicas" if world > 1 else "single"),

@@ -155,7 +155,7 @@ int dgh_set_time(dgh_ctx *ctx, double t);
  * integral of the Ricker wavelet of peak frequency f_peak and delay t_s
  * (Sec. 4.1, eq. validBench:ricker), scaled by amp; discretised as
  * S(t) M_k^{-1} l(xs) in the cell k containing xs (lowest id on ties) and
- * evaluated at every RK stage time.  At most 16 sources per context.
+ * evaluated at every RK stage time.  At most 64 sources per context.
  * Errors: DGH_EINVAL if xs lies outside the mesh. */
 int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double t_s, double amp);
 
@@ -203,6 +203,99 @@ int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stream);
  * created from the same description.  DGH_EINVAL on size mismatch. */
 int dgh_save_state(dgh_ctx *ctx, void *buf, size_t *size);
 int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size);
+
+/* ---------------------------------------------------------------- launch shapes
+ * Launch shape of the stage kernels: the number of elements a CTA handles,
+ * which the paper tunes per kernel as K_blk (Sec. 3.3, Tables 4-5), and the
+ * number of persistent 3D CTAs.  tile2 = triangles per CTA of the 2D kernel,
+ * tile1 = line cells per CTA of the 1D kernel, cta3_per_sm = persistent 3D
+ * CTAs per SM (0 = as many as fit).  grid3/grid2/grid1 (CTAs per launch),
+ * occ3 (3D CTAs that fit on one SM) and sms are derived, read only.  A 3D
+ * CTA always handles 32-cell blocks (one cell per lane). */
+typedef struct dgh_launch {
+    int32_t tile2, tile1, cta3_per_sm;
+    int32_t grid3, grid2, grid1, occ3, sms;
+} dgh_launch;
+
+int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *out);
+
+/* Sets tile2, tile1 and cta3_per_sm (the other fields are ignored).  No
+ * result changes: every element's arithmetic is the same whatever the shape.
+ * DGH_EINVAL if a value is out of range or the tile does not fit in shared
+ * memory (the previous shape is kept). */
+int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in);
+
+/* Autotuner: coordinate search over tile2, tile1 and cta3_per_sm, each
+ * candidate timed with CUDA events over `steps` whole steps (best of two),
+ * kept when at least 1% faster.  The fields, time and step count are saved
+ * before and restored after (host copy of the state), so the search changes
+ * no result.  ms_before / ms_after (may be NULL) receive the time of one
+ * step before and after.  Synchronising; takes roughly
+ * (3 + number of candidates) * 2 * steps steps of GPU time. */
+int dgh_tune(dgh_ctx *ctx, int steps, double *ms_before, double *ms_after);
+
+/* ---------------------------------------------------------------- batching
+ * A batch steps many independent problems (each with its own mesh, material,
+ * N, P, time step and sources) together: the problems are grouped by (N, P);
+ * each group becomes one union context over all its problems' cells,
+ * triangles, lines and corners, with each problem's time step folded into
+ * its cells' coefficients, and one CUDA graph per step runs all groups
+ * concurrently (one branch per group).  This is the paper's method applied
+ * per problem (Algorithm 1 with eqs. timeStepProc1-2); the paper itself runs
+ * one problem at a time. */
+typedef struct dgh_batch dgh_batch;
+
+/* Snapshots `count` problem contexts (mesh, material, N, P, time step,
+ * sources, current fields, time, step count) into a new batch on the current
+ * device.  The problem contexts are only read and stay valid and
+ * independent: stepping the batch does not advance them.  Device memory of
+ * the batch is separate from theirs.  At most 64 point sources per (N, P)
+ * group.  Errors: DGH_EINVAL (null arguments, problems on another device, too
+ * many sources), DGH_ENOMEM, DGH_ECUDA. */
+int dgh_batch_create(dgh_ctx *const *problems, int count, dgh_batch **out);
+
+/* Host-only dry run of the grouping: for the descriptions descs[0..count),
+ * group_of[i] receives the group of problem i (groups numbered in order of
+ * first appearance of their (N, P)), group_info[g] (room for `count`
+ * entries) the sizes of the union mesh of group g (dt, time, step_count and
+ * device_bytes are 0), *n_groups the number of groups.  No GPU is used. */
+int dgh_batch_plan(const dgh_desc *descs, int count, int *group_of, dgh_info *group_info, int *n_groups);
+
+void dgh_batch_destroy(dgh_batch *b);
+const char *dgh_batch_last_error(const dgh_batch *b);   /* NULL: last failing dgh_batch_create */
+int dgh_batch_count(const dgh_batch *b, int *n_problems, int *n_groups);
+
+/* *stream receives the batch's own non-blocking cudaStream_t, on which all its
+ * device work runs (owned by the batch, valid until dgh_batch_destroy): record
+ * events on it, or make other streams wait on it. */
+int dgh_batch_stream(const dgh_batch *b, void **stream);
+
+/* Advances every problem by nsteps steps of its own time step (asynchronous,
+ * on the batch's own stream; one graph launch per step). */
+int dgh_batch_step(dgh_batch *b, int64_t nsteps);
+
+/* Waits for the batch; reports asynchronous errors and timed-out waits
+ * (DGH_ETIMEOUT) of any group. */
+int dgh_batch_sync(dgh_batch *b);
+
+/* Problem i (0-based, the order given to dgh_batch_create): sizes, its own
+ * dt, time t0 + steps * dt and step count, in the layout and units of
+ * dgh_get_info (device_bytes = those of its group). */
+int dgh_batch_get_info(const dgh_batch *b, int i, dgh_info *out);
+
+/* Problem i's time-stepped variables of a level in the canonical layout of
+ * dgh_get_state (count as there, for that problem alone).  Synchronising. */
+int dgh_batch_get_state(dgh_batch *b, int i, int level, double *out, size_t count);
+
+/* Problem i's 3D energy as dgh_get_energy.  Synchronising. */
+int dgh_batch_get_energy(dgh_batch *b, int i, double *E);
+
+/* Launch shape of group g (0 <= g < n_groups). */
+int dgh_batch_get_launch(const dgh_batch *b, int group, dgh_launch *out);
+
+/* Autotuner of dgh_tune over the launch shapes of all groups, timed on whole
+ * batch steps; fields, times and step counts are restored afterwards. */
+int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,11 @@ class _Info(ctypes.Structure):
     ]
 
 
+class _Launch(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in
+                ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1", "occ3", "sms")]
+
+
 _lib = None
 
 
@@ -81,6 +86,23 @@ def load_library(path=LIB_PATH):
         "dgh_get_energy_noalloc": (ctypes.c_int, [P, ctypes.c_void_p, P]),
         "dgh_save_state": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "dgh_load_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
+        "dgh_get_launch": (ctypes.c_int, [P, ctypes.POINTER(_Launch)]),
+        "dgh_set_launch": (ctypes.c_int, [P, ctypes.POINTER(_Launch)]),
+        "dgh_tune": (ctypes.c_int, [P, ctypes.c_int, D, D]),
+        "dgh_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]),
+        "dgh_batch_plan": (ctypes.c_int, [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(_Info), ctypes.POINTER(ctypes.c_int)]),
+        "dgh_batch_destroy": (None, [P]),
+        "dgh_batch_last_error": (ctypes.c_char_p, [P]),
+        "dgh_batch_count": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "dgh_batch_stream": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+        "dgh_batch_step": (ctypes.c_int, [P, ctypes.c_int64]),
+        "dgh_batch_sync": (ctypes.c_int, [P]),
+        "dgh_batch_get_info": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_Info)]),
+        "dgh_batch_get_state": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, D, ctypes.c_size_t]),
+        "dgh_batch_get_energy": (ctypes.c_int, [P, ctypes.c_int, D]),
+        "dgh_batch_get_launch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_Launch)]),
+        "dgh_batch_tune": (ctypes.c_int, [P, ctypes.c_int, D, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -122,6 +144,29 @@ def plan(VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0):
     if rc != DGH_OK:
         raise DghError(rc, lib.dgh_last_error(None).decode())
     return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+
+def batch_plan(problems):
+    """Host-only grouping of a batch (no GPU).  problems: a list of dicts with
+    the keyword arguments of plan().  Returns (group_of, group_infos)."""
+    lib = load_library()
+    descs = (_Desc * len(problems))()
+    keep = []
+    for i, kw in enumerate(problems):
+        kw = dict(kw)
+        d, k = _make_desc(kw.pop("VX"), kw.pop("EToV"), kw.pop("N"), kw.pop("P"), kw.pop("bc", (BC_HABC,) * 6),
+                          kw.pop("c", 1.0), kw.pop("rho", 1.0), kw.pop("dt", 0.0), kw.pop("cfl", 1.0))
+        if kw:
+            raise TypeError("unknown keys %s" % sorted(kw))
+        descs[i] = d
+        keep.append(k)
+    gof = (ctypes.c_int * len(problems))()
+    infos = (_Info * len(problems))()
+    ng = ctypes.c_int()
+    rc = lib.dgh_batch_plan(descs, len(problems), gof, infos, ctypes.byref(ng))
+    if rc != DGH_OK:
+        raise DghError(rc, lib.dgh_last_error(None).decode())
+    return list(gof), [{f: getattr(infos[g], f) for f, _ in _Info._fields_} for g in range(ng.value)]
 
 
 class Solver:
@@ -260,3 +305,104 @@ class Solver:
     def load_state(self, blob):
         buf = ctypes.create_string_buffer(bytes(blob), len(blob))
         self._check(self._lib.dgh_load_state(self._h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+
+    @property
+    def launch(self):
+        """Launch shape (tile2, tile1, cta3_per_sm and the derived grids)."""
+        o = _Launch()
+        self._check(self._lib.dgh_get_launch(self._h, ctypes.byref(o)))
+        return {f: getattr(o, f) for f, _ in _Launch._fields_}
+
+    def set_launch(self, tile2=None, tile1=None, cta3_per_sm=None):
+        cur = self.launch
+        o = _Launch()
+        o.tile2 = cur["tile2"] if tile2 is None else int(tile2)
+        o.tile1 = cur["tile1"] if tile1 is None else int(tile1)
+        o.cta3_per_sm = cur["cta3_per_sm"] if cta3_per_sm is None else int(cta3_per_sm)
+        self._check(self._lib.dgh_set_launch(self._h, ctypes.byref(o)))
+
+    def tune(self, steps=5):
+        """Autotune the launch shape (results unchanged); returns (ms/step before, after)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.dgh_tune(self._h, int(steps), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+
+class Batch:
+    """Independent problems stepped together (see dgh_batch_create): a snapshot
+    of the given Solver objects, grouped by (N, P), one graph per step."""
+
+    def __init__(self, solvers):
+        lib = load_library()
+        arr = (ctypes.c_void_p * len(solvers))(*[s._h.value for s in solvers])
+        h = ctypes.c_void_p()
+        rc = lib.dgh_batch_create(arr, len(solvers), ctypes.byref(h))
+        if rc != DGH_OK:
+            raise DghError(rc, lib.dgh_batch_last_error(None).decode())
+        self._h, self._lib = h, lib
+        self._P = [s.P for s in solvers]
+
+    def _check(self, rc):
+        if rc != DGH_OK:
+            raise DghError(rc, self._lib.dgh_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dgh_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def counts(self):
+        n, g = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.dgh_batch_count(self._h, ctypes.byref(n), ctypes.byref(g)))
+        return n.value, g.value
+
+    @property
+    def stream_handle(self):
+        """The batch's cudaStream_t as an int (all its device work runs there)."""
+        p = ctypes.c_void_p()
+        self._check(self._lib.dgh_batch_stream(self._h, ctypes.byref(p)))
+        return p.value
+
+    def info(self, i):
+        o = _Info()
+        self._check(self._lib.dgh_batch_get_info(self._h, int(i), ctypes.byref(o)))
+        return {f: getattr(o, f) for f, _ in _Info._fields_}
+
+    def shape(self, i, level):
+        d = self.info(i)
+        P = self._P[i]
+        return {3: (d["n_cells"], 4, d["Np"]), 2: (d["n_tris"], P, 3, d["Np2"]),
+                1: (d["n_lines"], P * P, 2, d["Np1"])}[level]
+
+    def step(self, n=1):
+        self._check(self._lib.dgh_batch_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.dgh_batch_sync(self._h))
+
+    def get_state(self, i, level):
+        out = np.empty(self.shape(i, level))
+        self._check(self._lib.dgh_batch_get_state(self._h, int(i), level, _dptr(out), out.size))
+        return out
+
+    def energy(self, i):
+        e = ctypes.c_double()
+        self._check(self._lib.dgh_batch_get_energy(self._h, int(i), ctypes.byref(e)))
+        return e.value
+
+    def launch(self, group):
+        o = _Launch()
+        self._check(self._lib.dgh_batch_get_launch(self._h, int(group), ctypes.byref(o)))
+        return {f: getattr(o, f) for f, _ in _Launch._fields_}
+
+    def tune(self, steps=5):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.dgh_batch_tune(self._h, int(steps), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value

@@ -44,6 +44,8 @@ struct dgh_ctx {
     int N = 0, P = 0, Np = 0, Nfp = 0, Np2 = 0, Np1 = 0;
     int64_t K = 0, K32 = 0, T = 0, L = 0, Fb = 0;
     int64_t Ki32 = 0, Kb32 = 0;       // 32-cell blocks of interior cells, then of cells with HABC faces
+    bool no_overlap = false;          // union of a batch: one launch over all cells, no side stream
+    std::vector<int64_t> part_blk0;   // first 32-cell block of every part (batch problem), + end
     std::vector<int64_t> can2dev;     // canonical cell -> device cell slot
     cudaStream_t side = nullptr;      // HABC chain stream (overlaps the interior 3D work)
     cudaEvent_t ev3d[5] = {}, ev2d[5] = {}, evjoin = nullptr;
@@ -82,10 +84,14 @@ struct dgh_ctx {
     // sources
     SrcParams src{};
     float *srcvec = nullptr;
+    std::vector<int64_t> src_k;       // canonical cell of every source
+    std::vector<float> src_vec_h;     // host copy of the source vectors [n][Np]
     // launch shapes
     int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0, sms = 1;
+    int cta3_per_sm = 0;              // tunable: persistent 3D CTAs per SM (0 = occupancy limit)
     unsigned long long *tile_ctr = nullptr;   // [11] block counters of the 3D launches of a step
     size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
+    int smem_optin = 0;
     // graphs (one per trace parity)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     // host copies needed by read-back
@@ -310,19 +316,42 @@ template <int N>
 struct SetAttrs {
     static int run(dgh_ctx *c) {
         c->smem3 = Cfg3<N>::SMEM;
+        // The limit is a property of the kernel, shared by every context of
+        // this N (whatever P and tile): the 2D/1D kernels get the device's
+        // opt-in maximum once, so that no context lowers it below another's need.
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
         cudaFuncSetAttribute(k3d_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3);
-        cudaFuncSetAttribute(k2d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem2);
-        cudaFuncSetAttribute(k2d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem2);
-        cudaFuncSetAttribute(k1d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem1);
-        cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem1);
+        cudaFuncSetAttribute(k2d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k1d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        c->smem_optin = optin;
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N>, Cfg3<N>::NW * 32, c->smem3);
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-        const int64_t tiles3 = c->K32;
         c->occ3 = nb;
         c->sms = sms;
-        c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)std::max(nb, 1) * sms));
+        return DGH_OK;
+    }
+};
+
+// Launch shapes from the tunables: triangles / lines per CTA of the 2D / 1D
+// kernels (tile2, tile1) and the number of persistent 3D CTAs per SM
+// (cta3_per_sm, 0 = as many as fit).  Returns DGH_EINVAL for a tile whose
+// shared memory does not fit.
+template <int N>
+struct Shapes {
+    static int run(dgh_ctx *c) {
+        const int P = c->P;
+        c->smem2 = P ? k2d_smem(N, P, c->tile2) : 0;
+        c->smem1 = P ? k1d_smem(N, P, c->tile1) : 0;
+        c->smem0 = sizeof(float) * 3 * P * P;
+        if ((int64_t)c->smem2 > c->smem_optin || (int64_t)c->smem1 > c->smem_optin) return DGH_EINVAL;
+        const int sms = c->sms;
+        const int per_sm = c->cta3_per_sm > 0 ? std::min(c->cta3_per_sm, std::max(c->occ3, 1)) : std::max(c->occ3, 1);
+        c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(c->K32, (int64_t)per_sm * sms));
         int nb2 = 0, nb1 = 0;
         if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, 256, c->smem2);
         if (c->L) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k1d_stage<N, true>, 256, c->smem1);
@@ -359,8 +388,11 @@ int run_closure(dgh_ctx *c) {
 // the interior cells of stage s+1 are computed on the main stream; the cells
 // with HABC faces of stage s+1 wait for the 2D kernel of stage s (it writes
 // their exterior states), and the 2D kernel of stage s+1 waits for them.
-int enqueue_step(dgh_ctx *c, int cur, bool overlap) {
-    cudaStream_t ms = c->stream, ss = overlap ? c->side : c->stream;
+// ms overrides the context's stream (a batch enqueues each group on its own).
+int enqueue_step(dgh_ctx *c, int cur, bool overlap, cudaStream_t ms = nullptr) {
+    if (!ms) ms = c->stream;
+    overlap = overlap && !c->no_overlap;
+    cudaStream_t ss = overlap ? c->side : ms;
     cudaMemsetAsync(c->tile_ctr, 0, 10 * sizeof(unsigned long long), ms);
     for (int s = 0; s < 5; ++s) {
         int rc = dispatchN<Launch3>(c->N, c, cur, s, true, 1, ms);
@@ -571,28 +603,26 @@ int dgh_plan(const dgh_desc *d, dgh_info *o) {
     return DGH_OK;
 }
 
-int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
-    if (!out) {
-        g_create_error = "out is NULL";
-        return DGH_EINVAL;
-    }
-    *out = nullptr;
-    int vrc = validate_desc(d);
-    if (vrc) return vrc;
-    dgh_ctx *ctx = new dgh_ctx();
-    ctx->stream = static_cast<cudaStream_t>(stream);
-    cudaGetDevice(&ctx->device);
+}  // extern "C"
+
+// Device arrays of a context whose host set-up (mesh, reference elements,
+// HABC operators, dt) is complete.  parts lists the cell offsets of the
+// independent problems the mesh is made of ({0, K} for one problem); each
+// problem gets its own range of 32-cell blocks.  With one problem the cells
+// without HABC faces come first and the cells with HABC faces (whose exterior
+// state the 2D kernel writes) last, each group padded to whole blocks, so
+// that the two groups can be launched separately; a batch union launches all
+// blocks at once (no_overlap).  m.dtCell, when present, holds each cell's own
+// time step, which is folded into the rho c^2 and 1/rho coefficients of all
+// levels (every right-hand side is proportional to one of them), so that the
+// stage kernels advance with dt = 1.
+static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
     auto fail = [&](int rc, const std::string &msg) {
-        g_create_error = msg.empty() ? ctx->err : msg;
-        dgh_destroy(ctx);
+        if (!msg.empty()) ctx->err = msg;
         return rc;
     };
-    const int N = ctx->N = d->order, P = ctx->P = d->habc_order;
+    const int N = ctx->N, P = ctx->P;
     HostMesh &m = ctx->mesh;
-    {
-        int rc0 = host_setup(d, m, ctx->ref3, ctx->ref2, ctx->ref1, ctx->habc);
-        if (rc0) return fail(rc0, g_create_error);
-    }
     const RefTet &T3 = ctx->ref3;
     const RefTri &T2 = ctx->ref2;
     const RefLine &T1 = ctx->ref1;
@@ -606,27 +636,40 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     ctx->Fb = int64_t(m.bface.size());
     ctx->C = int(m.corners.size());
     ctx->M = ctx->habc.M;
-    ctx->dt = d->dt > 0.0 ? d->dt : dt_rule(m, d->cfl > 0.0 ? d->cfl : 1.0);
     const int64_t K = m.K;
     const int Np = T3.Np, Nfp = T3.Nfp, Np2 = T2.Np, Np1 = T1.Np;
+    auto fold = [&](int64_t k) { return m.dtCell.empty() ? 1.0 : m.dtCell[size_t(k)]; };
     int rc;
     // ---------------------------------------------------------------- 3D
     // Cell-interleaved tiles of 32 cells: q, res [K32][4][Np][32], geometry
     // [K32][GEO3][32], connectivity [K32][4][32]; traces [K32*32][4][2][Nfp].
-    // Device cell order: cells without HABC faces first, then cells with HABC
-    // faces (whose exterior state the 2D kernel writes), each group padded to
-    // whole 32-cell blocks, so the two groups can be launched separately.
     {
+        const int nparts = int(parts.size()) - 1;
         std::vector<char> habc_cell(size_t(K), 0);
         for (int64_t t = 0; t < m.Ktri; ++t) habc_cell[m.bface[m.triBface[t]] / 4] = 1;
-        int64_t ni = 0, nb = 0;
-        for (int64_t k = 0; k < K; ++k) (habc_cell[k] ? nb : ni)++;
-        ctx->Ki32 = (ni + 31) / 32;
-        ctx->Kb32 = (nb + 31) / 32;
-        ctx->K32 = ctx->Ki32 + ctx->Kb32;
         ctx->can2dev.assign(size_t(K), -1);
-        int64_t pi = 0, pb = ctx->Ki32 * 32;
-        for (int64_t k = 0; k < K; ++k) ctx->can2dev[k] = habc_cell[k] ? pb++ : pi++;
+        ctx->part_blk0.assign(size_t(nparts) + 1, 0);
+        int64_t blk = 0;
+        for (int pp = 0; pp < nparts; ++pp) {
+            int64_t ni = 0, nb = 0;
+            for (int64_t k = parts[pp]; k < parts[pp + 1]; ++k) (habc_cell[k] ? nb : ni)++;
+            const int64_t bi = (ni + 31) / 32, bb = (nb + 31) / 32;
+            int64_t pi = blk * 32, pb = (blk + bi) * 32;
+            for (int64_t k = parts[pp]; k < parts[pp + 1]; ++k) ctx->can2dev[k] = habc_cell[k] ? pb++ : pi++;
+            ctx->part_blk0[pp] = blk;
+            if (nparts == 1) {
+                ctx->Ki32 = bi;
+                ctx->Kb32 = bb;
+            }
+            blk += bi + bb;
+        }
+        ctx->part_blk0[nparts] = blk;
+        ctx->K32 = blk;
+        if (nparts != 1) {
+            ctx->Ki32 = blk;
+            ctx->Kb32 = 0;
+            ctx->no_overlap = true;
+        }
     }
     if (ctx->K32 * 32 * 4 >= (int64_t(1) << 28)) return fail(DGH_EUNSUPPORTED, "too many cells for the 32-bit connectivity encoding");
     {
@@ -664,12 +707,12 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
                     CN(kd, f) = int(((ctx->can2dev[nb / 4] * 4 + nb % 4) << 3) | m.nbrSigma[4 * k + f]);
                 } else {
                     const int64_t b = m.bfaceOf[4 * k + f];
-                    const int dir = m.bc[m.bfaceDom[b]] == BC_DIRICHLET ? 1 : 0;
+                    const int dir = m.bfaceDir[b] ? 1 : 0;
                     CN(kd, f) = int(-1 - ((b << 1) | dir));
                 }
             }
-            G(kd, 13) = float(m.rho[k] * m.c[k] * m.c[k]);
-            G(kd, 14) = float(1.0 / m.rho[k]);
+            G(kd, 13) = float(m.rho[k] * m.c[k] * m.c[k] * fold(k));
+            G(kd, 14) = float(fold(k) / m.rho[k]);
             G(kd, 15) = float(Z);
             for (int v = 0; v < 4; ++v)
                 for (int dd = 0; dd < 3; ++dd) cellv[12 * kd + 3 * v + dd] = m.VX[3 * m.EToV[4 * k + v] + dd];
@@ -745,15 +788,14 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
                     Zp = m.rho[kn] * m.c[kn];
                     conn[3 * t + e] = int((nb << 1) | m.flip2[3 * t + e]);
                 } else {
-                    const int B = m.edgeDom[3 * t + e];
-                    conn[3 * t + e] = (m.bc[B] == BC_DIRICHLET) ? -2 : -1;
+                    conn[3 * t + e] = m.edgeDir[3 * t + e] ? -2 : -1;
                 }
                 ge[3] = float(Z / (Z + Zp));
                 ge[4] = float(Z * Zp / (Z + Zp));
                 ge[5] = float(1.0 / (Z + Zp));
             }
-            g[22] = float(m.rho[k] * m.c[k] * m.c[k]);
-            g[23] = float(1.0 / m.rho[k]);
+            g[22] = float(m.rho[k] * m.c[k] * m.c[k] * fold(k));
+            g[23] = float(fold(k) / m.rho[k]);
             g[24] = float(Z);
             tface[t] = int(ctx->can2dev[gf / 4] * 4 + gf % 4);
             tb[t] = int(m.triBface[t]);
@@ -792,8 +834,8 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
             const double Z = ZA;   // a line cell takes the material of its face-A triangle
             g[0] = float(1.0 / m.J1[l]);
             g[1] = float(1.0 / std::fabs(m.J1[l]));
-            g[2] = float(m.rho[kA] * m.c[kA] * m.c[kA]);
-            g[3] = float(1.0 / m.rho[kA]);
+            g[2] = float(m.rho[kA] * m.c[kA] * m.c[kA] * fold(kA));
+            g[3] = float(fold(kA) / m.rho[kA]);
             g[4] = float(Z);
             g[5] = float(ZA);
             g[6] = float(ZB);
@@ -805,7 +847,7 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
                     Zp = m.rho[kn] * m.c[kn];
                     conn[2 * l + e] = int(nb);
                 } else {
-                    conn[2 * l + e] = (m.bc[m.endDom[2 * l + e]] == BC_DIRICHLET) ? -2 : -1;
+                    conn[2 * l + e] = m.endDir[2 * l + e] ? -2 : -1;
                 }
                 g[7 + 3 * e] = float(Z / (Z + Zp));
                 g[8 + 3 * e] = float(Z * Zp / (Z + Zp));
@@ -862,10 +904,8 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     // launch shapes
     ctx->tile2 = std::max(1, 256 / std::max(1, P * Np2));
     ctx->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
-    ctx->smem2 = P ? k2d_smem(N, P, ctx->tile2) : 0;
-    ctx->smem1 = P ? k1d_smem(N, P, ctx->tile1) : 0;
-    ctx->smem0 = sizeof(float) * 3 * P * P;
     dispatchN<SetAttrs>(N, ctx);
+    if ((rc = dispatchN<Shapes>(N, ctx))) return fail(DGH_EUNSUPPORTED, "2D/1D tile does not fit in shared memory");
     {
         int lo = 0, hi = 0;
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -880,6 +920,36 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(DGH_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+    return DGH_OK;
+}
+
+extern "C" {
+
+int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return DGH_EINVAL;
+    }
+    *out = nullptr;
+    int vrc = validate_desc(d);
+    if (vrc) return vrc;
+    dgh_ctx *ctx = new dgh_ctx();
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&ctx->device);
+    ctx->N = d->order;
+    ctx->P = d->habc_order;
+    int rc = host_setup(d, ctx->mesh, ctx->ref3, ctx->ref2, ctx->ref1, ctx->habc);
+    if (rc) {
+        dgh_destroy(ctx);
+        return rc;
+    }
+    ctx->dt = d->dt > 0.0 ? d->dt : dt_rule(ctx->mesh, d->cfl > 0.0 ? d->cfl : 1.0);
+    rc = build_context(ctx, {0, ctx->mesh.K});
+    if (rc) {
+        g_create_error = ctx->err;
+        dgh_destroy(ctx);
+        return rc;
+    }
     *out = ctx;
     return DGH_OK;
 }
@@ -1084,6 +1154,8 @@ int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double
             ctx->src.t_s[s] = t_s;
             ctx->src.amp[s] = amp;
             ctx->src.n = s + 1;
+            ctx->src_k.push_back(k);
+            ctx->src_vec_h.insert(ctx->src_vec_h.end(), vec.begin(), vec.end());
             drop_graphs(ctx);
             return DGH_OK;
         }
@@ -1269,6 +1341,598 @@ int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size) {
     ctx->step_count = h[4];
     ctx->dirty = true;
     return DGH_OK;
+}
+
+
+// ---------------------------------------------------------------- launch shapes and tuning
+int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *o) {
+    if (!ctx || !o) return DGH_EINVAL;
+    o->tile2 = ctx->tile2;
+    o->tile1 = ctx->tile1;
+    o->cta3_per_sm = ctx->cta3_per_sm;
+    o->grid3 = ctx->grid3;
+    o->grid2 = ctx->grid2;
+    o->grid1 = ctx->grid1;
+    o->occ3 = ctx->occ3;
+    o->sms = ctx->sms;
+    return DGH_OK;
+}
+
+int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in) {
+    if (!ctx || !in || in->tile2 < 1 || in->tile1 < 1 || in->cta3_per_sm < 0) {
+        if (ctx) ctx->err = "tile2, tile1 must be >= 1 and cta3_per_sm >= 0";
+        return DGH_EINVAL;
+    }
+    const int t2 = ctx->tile2, t1 = ctx->tile1, c3 = ctx->cta3_per_sm;
+    ctx->tile2 = in->tile2;
+    ctx->tile1 = in->tile1;
+    ctx->cta3_per_sm = in->cta3_per_sm;
+    if (dispatchN<Shapes>(ctx->N, ctx) != DGH_OK) {
+        ctx->tile2 = t2;
+        ctx->tile1 = t1;
+        ctx->cta3_per_sm = c3;
+        dispatchN<Shapes>(ctx->N, ctx);
+        ctx->err = "launch shape does not fit in shared memory";
+        return DGH_EINVAL;
+    }
+    drop_graphs(ctx);
+    return DGH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Milliseconds per step of run(steps) on stream st (after two untimed steps),
+// best of two repetitions.
+template <class Run>
+int time_per_step(cudaStream_t st, int steps, Run run, double &ms, std::string &err) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        err = "cudaEventCreate failed";
+        return DGH_ECUDA;
+    }
+    int rc = run(2);   // both trace parities: any graph is built before the timed region
+    ms = 1e300;
+    for (int rep = 0; rep < 2 && rc == DGH_OK; ++rep) {
+        cudaEventRecord(a, st);
+        rc = run(steps);
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            err = "tuning run failed";
+            rc = DGH_ECUDA;
+            break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        ms = std::min(ms, double(t) / steps);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+
+// Coordinate search over the launch shape of every context (2D triangles per
+// CTA, 1D lines per CTA, persistent 3D CTAs per SM), the paper's tuning of
+// elements per block (K_blk) carried over to these kernels: each candidate
+// is timed on whole steps and kept if it is at least 1% faster.  The fields
+// are saved before and restored after, so the search changes no result.
+template <class Run, class Invalidate>
+int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, Run run, Invalidate invalidate,
+                  double *ms_before, double *ms_after, std::string &err) {
+    std::vector<std::vector<char>> saved(cs.size());
+    for (size_t i = 0; i < cs.size(); ++i) {
+        size_t sz = 0;
+        int rc = dgh_save_state(cs[i], nullptr, &sz);
+        if (rc) return rc;
+        saved[i].resize(sz);
+        if ((rc = dgh_save_state(cs[i], saved[i].data(), &sz))) {
+            err = cs[i]->err;
+            return rc;
+        }
+    }
+    double best = 0.0;
+    int rc = time_per_step(st, steps, run, best, err);
+    if (rc) return rc;
+    if (ms_before) *ms_before = best;
+    for (dgh_ctx *c : cs) {
+        for (int param = 0; param < 3 && rc == DGH_OK; ++param) {
+            int *slot = param == 0 ? &c->tile2 : param == 1 ? &c->tile1 : &c->cta3_per_sm;
+            std::vector<int> cand;
+            if (param == 0 && c->T > 0)
+                for (int v = 1; v <= 32 && v <= c->T; v *= 2) cand.push_back(v);
+            if (param == 1 && c->L > 0)
+                for (int v = 1; v <= 32 && v <= c->L; v *= 2) cand.push_back(v);
+            if (param == 2)
+                for (int v = 0; v <= c->occ3; ++v) cand.push_back(v);
+            int keep = *slot;
+            for (int v : cand) {
+                if (v == keep) continue;
+                *slot = v;
+                if (dispatchN<Shapes>(c->N, c) != DGH_OK) continue;
+                invalidate();
+                double ms = 0.0;
+                if ((rc = time_per_step(st, steps, run, ms, err))) break;
+                if (ms < 0.99 * best) {
+                    best = ms;
+                    keep = v;
+                }
+            }
+            *slot = keep;
+            dispatchN<Shapes>(c->N, c);
+            invalidate();
+        }
+        if (rc) break;
+    }
+    for (size_t i = 0; i < cs.size(); ++i) {
+        int rc2 = dgh_load_state(cs[i], saved[i].data(), saved[i].size());
+        if (rc2 && !rc) {
+            err = cs[i]->err;
+            rc = rc2;
+        }
+    }
+    if (ms_after) *ms_after = best;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int dgh_tune(dgh_ctx *ctx, int steps, double *ms_before, double *ms_after) {
+    if (!ctx || steps < 1) return DGH_EINVAL;
+    const int64_t sc0 = ctx->step_count;
+    int rc = tune_contexts(
+        {ctx}, ctx->stream, steps, [&](int n) { return dgh_step(ctx, n); }, [&]() { drop_graphs(ctx); }, ms_before,
+        ms_after, ctx->err);
+    ctx->step_count = sc0;
+    return rc;
+}
+
+// ============================================================================
+// Batching form: independent problems stepped together.
+//
+// The problems are grouped by (N, P).  Each group is one union context whose
+// mesh is the disjoint union of its problems' meshes (every problem keeps its
+// own range of 32-cell blocks, triangles, lines and corners), with every
+// problem's time step folded into its cells' coefficients.  One CUDA graph
+// per step forks one branch per group; inside a branch the stage kernels of
+// Algorithm 1 run over all problems of the group at once, the 3D kernel
+// claiming 32-cell blocks from a device counter (the work queue), so small
+// problems share the GPU instead of each under-filling it.
+struct dgh_batch {
+    std::string err = "no error";
+    int device = 0;
+    cudaStream_t stream = nullptr;   // capture / replay stream (non-blocking)
+    std::vector<dgh_ctx *> groups;
+    std::vector<cudaStream_t> gstream;
+    std::vector<cudaEvent_t> gjoin;
+    cudaEvent_t fork = nullptr;
+    struct Prob {
+        int group = 0, part = 0, N = 0, P = 0;
+        int64_t cell0 = 0, K = 0, tri0 = 0, T = 0, lin0 = 0, L = 0, C = 0, Fb = 0;
+        double dt = 0.0, t0 = 0.0;
+        int64_t step0 = 0;
+    };
+    std::vector<Prob> probs;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t step_count = 0;
+};
+
+namespace {
+
+void batch_drop_graphs(dgh_batch *b) {
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) {
+            cudaGraphExecDestroy(b->graph[i]);
+            b->graph[i] = nullptr;
+        }
+}
+
+int batch_build_graph(dgh_batch *b) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        b->err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    int rc = DGH_OK;
+    cudaEventRecord(b->fork, b->stream);
+    for (size_t i = 0; i < b->groups.size() && rc == DGH_OK; ++i) {
+        cudaStreamWaitEvent(b->gstream[i], b->fork, 0);
+        rc = enqueue_step(b->groups[i], b->groups[i]->cur, false, b->gstream[i]);
+        if (rc) b->err = b->groups[i]->err;
+        cudaEventRecord(b->gjoin[i], b->gstream[i]);
+        cudaStreamWaitEvent(b->stream, b->gjoin[i], 0);
+    }
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        b->err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->graph[b->cur], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    return DGH_OK;
+}
+
+// Host-only grouping of problems by (N, P), in order of first appearance.
+std::vector<int> group_by_order(const std::vector<std::pair<int, int>> &np, int &ngroups) {
+    std::vector<std::pair<int, int>> keys;
+    std::vector<int> g(np.size());
+    for (size_t i = 0; i < np.size(); ++i) {
+        size_t j = 0;
+        while (j < keys.size() && keys[j] != np[i]) ++j;
+        if (j == keys.size()) keys.push_back(np[i]);
+        g[i] = int(j);
+    }
+    ngroups = int(keys.size());
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dgh_batch_last_error(const dgh_batch *b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void dgh_batch_destroy(dgh_batch *b) {
+    if (!b) return;
+    batch_drop_graphs(b);
+    for (dgh_ctx *c : b->groups) dgh_destroy(c);
+    for (cudaStream_t s : b->gstream)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->gjoin)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int dgh_batch_plan(const dgh_desc *descs, int count, int *group_of, dgh_info *group_info, int *n_groups) {
+    if (!descs || count < 1 || !group_of || !group_info || !n_groups) {
+        g_create_error = "invalid batch plan arguments";
+        return DGH_EINVAL;
+    }
+    std::vector<std::pair<int, int>> np(static_cast<size_t>(count));
+    for (int i = 0; i < count; ++i) {
+        int rc = validate_desc(&descs[i]);
+        if (rc) return rc;
+        np[i] = {descs[i].order, descs[i].habc_order};
+    }
+    int ng = 0;
+    std::vector<int> g = group_by_order(np, ng);
+    for (int gi = 0; gi < ng; ++gi) {
+        std::vector<HostMesh> parts;
+        RefTet T3;
+        RefTri T2;
+        RefLine T1;
+        HabcOps habc;
+        for (int i = 0; i < count; ++i) {
+            if (g[i] != gi) continue;
+            parts.emplace_back();
+            int rc = host_setup(&descs[i], parts.back(), T3, T2, T1, habc);
+            if (rc) return rc;
+        }
+        HostMesh u;
+        merge_meshes(parts, u);
+        dgh_info &o = group_info[gi];
+        std::memset(&o, 0, sizeof(o));
+        o.order = u.N;
+        o.habc_order = u.P;
+        o.Np = T3.Np;
+        o.Np2 = T2.Np;
+        o.Np1 = T1.Np;
+        o.n_corners = int(u.corners.size());
+        o.n_cells = u.K;
+        o.n_tris = u.Ktri;
+        o.n_lines = u.Klin;
+        o.n_bfaces = int64_t(u.bface.size());
+        const int64_t P = u.P;
+        o.ndof = 4 * int64_t(T3.Np) * u.K + 3 * P * T2.Np * u.Ktri + 2 * P * P * T1.Np * u.Klin;
+    }
+    for (int i = 0; i < count; ++i) group_of[i] = g[i];
+    *n_groups = ng;
+    return DGH_OK;
+}
+
+int dgh_batch_create(dgh_ctx *const *problems, int count, dgh_batch **out) {
+    if (!out || !problems || count < 1) {
+        g_create_error = "invalid batch arguments";
+        return DGH_EINVAL;
+    }
+    *out = nullptr;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<std::pair<int, int>> np(static_cast<size_t>(count));
+    for (int i = 0; i < count; ++i) {
+        if (!problems[i]) {
+            g_create_error = "null problem context";
+            return DGH_EINVAL;
+        }
+        if (problems[i]->device != dev) {
+            g_create_error = "all problems must live on the current device";
+            return DGH_EINVAL;
+        }
+        np[i] = {problems[i]->N, problems[i]->P};
+    }
+    int ng = 0;
+    std::vector<int> gof = group_by_order(np, ng);
+    dgh_batch *b = new dgh_batch();
+    b->device = dev;
+    auto fail = [&](int rc, const std::string &msg) {
+        g_create_error = msg;
+        dgh_batch_destroy(b);
+        return rc;
+    };
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(DGH_ECUDA, "batch stream / event");
+    b->probs.resize(size_t(count));
+    for (int gi = 0; gi < ng; ++gi) {
+        std::vector<int> members;
+        for (int i = 0; i < count; ++i)
+            if (gof[i] == gi) members.push_back(i);
+        dgh_ctx *u = new dgh_ctx();
+        b->groups.push_back(u);
+        const dgh_ctx *first = problems[members[0]];
+        u->stream = b->stream;
+        u->device = dev;
+        u->N = first->N;
+        u->P = first->P;
+        u->ref3 = first->ref3;
+        u->ref2 = first->ref2;
+        u->ref1 = first->ref1;
+        u->habc = first->habc;
+        u->dt = 1.0;   // time steps folded into the coefficients: the clock counts steps
+        std::vector<HostMesh> parts;
+        std::vector<int64_t> offs{0};
+        int64_t t0 = 0, l0 = 0;
+        for (size_t j = 0; j < members.size(); ++j) {
+            dgh_ctx *pc = problems[members[j]];
+            double tnow = 0.0;
+            if (cudaStreamSynchronize(pc->stream) != cudaSuccess ||
+                cudaMemcpy(&tnow, pc->d_time, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(DGH_ECUDA, "reading a problem's time");
+            parts.push_back(pc->mesh);
+            parts.back().dtCell.assign(size_t(pc->mesh.K), pc->dt);
+            dgh_batch::Prob &pr = b->probs[size_t(members[j])];
+            pr.group = gi;
+            pr.part = int(j);
+            pr.N = pc->N;
+            pr.P = pc->P;
+            pr.cell0 = offs.back();
+            pr.K = pc->K;
+            pr.tri0 = t0;
+            pr.T = pc->T;
+            pr.lin0 = l0;
+            pr.L = pc->L;
+            pr.C = pc->C;
+            pr.Fb = pc->Fb;
+            pr.dt = pc->dt;
+            pr.t0 = tnow;
+            pr.step0 = pc->step_count;
+            offs.push_back(offs.back() + pc->K);
+            t0 += pc->T;
+            l0 += pc->L;
+        }
+        merge_meshes(parts, u->mesh);
+        parts.clear();
+        int rc = build_context(u, offs);
+        if (rc) return fail(rc, u->err);
+        // sources: time measured in steps of the problem's own dt
+        for (size_t j = 0; j < members.size(); ++j) {
+            const dgh_ctx *pc = problems[members[j]];
+            const dgh_batch::Prob &pr = b->probs[size_t(members[j])];
+            for (int s = 0; s < pc->src.n; ++s) {
+                const int d = u->src.n;
+                if (d >= MAXSRC) return fail(DGH_EINVAL, "more than MAXSRC point sources in one (N, P) group");
+                const std::vector<float> vec(pc->src_vec_h.begin() + size_t(s) * pc->Np,
+                                             pc->src_vec_h.begin() + size_t(s + 1) * pc->Np);
+                if (cudaMemcpy(u->srcvec + size_t(d) * u->Np, vec.data(), vec.size() * sizeof(float),
+                               cudaMemcpyHostToDevice) != cudaSuccess)
+                    return fail(DGH_ECUDA, "source upload");
+                u->src.cell[d] = u->can2dev[size_t(pr.cell0 + pc->src_k[size_t(s)])];
+                u->src.f_peak[d] = pc->src.f_peak[s] * pr.dt;
+                u->src.t_s[d] = (pc->src.t_s[s] - pr.t0) / pr.dt;
+                u->src.amp[d] = pc->src.amp[s] * pr.dt * pr.dt;
+                u->src.n = d + 1;
+                u->src_k.push_back(pr.cell0 + pc->src_k[size_t(s)]);
+                u->src_vec_h.insert(u->src_vec_h.end(), vec.begin(), vec.end());
+            }
+        }
+        // current fields of every problem, concatenated in canonical order
+        for (int lv = 3; lv >= 1; --lv) {
+            size_t ntot = 0;
+            level_count(u, lv, ntot);
+            std::vector<double> all(ntot);
+            size_t at = 0;
+            for (int i : members) {
+                size_t n = 0;
+                level_count(problems[i], lv, n);
+                if (n && dgh_get_state(problems[i], lv, all.data() + at, n) != DGH_OK)
+                    return fail(DGH_ECUDA, std::string("reading a problem's state: ") + problems[i]->err);
+                at += n;
+            }
+            if (ntot && (rc = dgh_set_state(u, lv, all.data(), ntot))) return fail(rc, u->err);
+        }
+        cudaStream_t gs = nullptr;
+        cudaEvent_t ge = nullptr;
+        if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) return fail(DGH_ECUDA, "group stream");
+        b->gstream.push_back(gs);
+        if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) return fail(DGH_ECUDA, "group event");
+        b->gjoin.push_back(ge);
+    }
+    *out = b;
+    return DGH_OK;
+}
+
+int dgh_batch_stream(const dgh_batch *b, void **stream) {
+    if (!b || !stream) return DGH_EINVAL;
+    *stream = static_cast<void *>(b->stream);
+    return DGH_OK;
+}
+
+int dgh_batch_count(const dgh_batch *b, int *n_problems, int *n_groups) {
+    if (!b) return DGH_EINVAL;
+    if (n_problems) *n_problems = int(b->probs.size());
+    if (n_groups) *n_groups = int(b->groups.size());
+    return DGH_OK;
+}
+
+int dgh_batch_step(dgh_batch *b, int64_t nsteps) {
+    if (!b || nsteps < 0) return DGH_EINVAL;
+    for (dgh_ctx *u : b->groups)
+        if (u->dirty) {
+            int rc = run_closure(u);
+            if (rc) {
+                b->err = u->err;
+                return rc;
+            }
+        }
+    for (int64_t i = 0; i < nsteps; ++i) {
+        if (!b->graph[b->cur]) {
+            int rc = batch_build_graph(b);
+            if (rc) return rc;
+        }
+        cudaError_t e = cudaGraphLaunch(b->graph[b->cur], b->stream);
+        if (e != cudaSuccess) {
+            b->err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+            return DGH_ECUDA;
+        }
+        b->cur ^= 1;
+        for (dgh_ctx *u : b->groups) {
+            u->cur ^= 1;
+            u->step_count++;
+        }
+        b->step_count++;
+    }
+    return DGH_OK;
+}
+
+int dgh_batch_sync(dgh_batch *b) {
+    if (!b) return DGH_EINVAL;
+    for (dgh_ctx *u : b->groups) {
+        int rc = dgh_sync(u);
+        if (rc) {
+            b->err = u->err;
+            return rc;
+        }
+    }
+    return DGH_OK;
+}
+
+int dgh_batch_get_info(const dgh_batch *b, int i, dgh_info *o) {
+    if (!b || !o || i < 0 || i >= int(b->probs.size())) return DGH_EINVAL;
+    const dgh_batch::Prob &p = b->probs[size_t(i)];
+    const dgh_ctx *u = b->groups[size_t(p.group)];
+    std::memset(o, 0, sizeof(*o));
+    o->order = p.N;
+    o->habc_order = p.P;
+    o->Np = u->Np;
+    o->Np2 = u->Np2;
+    o->Np1 = u->Np1;
+    o->n_corners = int(p.C);
+    o->n_cells = p.K;
+    o->n_tris = p.T;
+    o->n_lines = p.L;
+    o->n_bfaces = p.Fb;
+    o->ndof = 4 * int64_t(u->Np) * p.K + 3 * int64_t(p.P) * u->Np2 * p.T + 2 * int64_t(p.P) * p.P * u->Np1 * p.L;
+    o->step_count = p.step0 + b->step_count;
+    o->dt = p.dt;
+    o->time = p.t0 + double(b->step_count) * p.dt;
+    o->device_bytes = u->device_bytes;
+    return DGH_OK;
+}
+
+int dgh_batch_get_state(dgh_batch *b, int i, int level, double *out, size_t count) {
+    if (!b || i < 0 || i >= int(b->probs.size()) || (!out && count)) return DGH_EINVAL;
+    const dgh_batch::Prob &p = b->probs[size_t(i)];
+    dgh_ctx *u = b->groups[size_t(p.group)];
+    size_t per = 0, off = 0, n = 0;
+    if (level == 3) {
+        per = size_t(4) * u->Np;
+        off = size_t(p.cell0) * per;
+        n = size_t(p.K) * per;
+    } else if (level == 2) {
+        per = size_t(p.P) * 3 * u->Np2;
+        off = size_t(p.tri0) * per;
+        n = size_t(p.T) * per;
+    } else if (level == 1) {
+        per = size_t(p.P) * p.P * 2 * u->Np1;
+        off = size_t(p.lin0) * per;
+        n = size_t(p.L) * per;
+    } else {
+        b->err = "level must be 3, 2 or 1";
+        return DGH_EINVAL;
+    }
+    if (n != count) {
+        b->err = "state size mismatch";
+        return DGH_EINVAL;
+    }
+    if (n == 0) return DGH_OK;
+    size_t ntot = 0;
+    level_count(u, level, ntot);
+    std::vector<double> all(ntot);
+    int rc = dgh_get_state(u, level, all.data(), ntot);
+    if (rc) {
+        b->err = u->err;
+        return rc;
+    }
+    std::memcpy(out, all.data() + off, n * sizeof(double));
+    return DGH_OK;
+}
+
+int dgh_batch_get_energy(dgh_batch *b, int i, double *E) {
+    if (!b || !E || i < 0 || i >= int(b->probs.size())) return DGH_EINVAL;
+    const dgh_batch::Prob &p = b->probs[size_t(i)];
+    dgh_ctx *u = b->groups[size_t(p.group)];
+    const int64_t blk0 = u->part_blk0[size_t(p.part)], nblk = u->part_blk0[size_t(p.part) + 1] - blk0;
+    const float *q = u->q3 + blk0 * 4 * u->Np * 32;
+    const double *ew = u->ew + blk0 * 32 * 2;
+    const int nb = u->energy_blocks;
+    cudaStream_t st = u->stream;
+    switch (u->N) {
+        case 1: k_energy_partial<1><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+        case 2: k_energy_partial<2><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+        case 3: k_energy_partial<3><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+        case 4: k_energy_partial<4><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+        case 5: k_energy_partial<5><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+        case 6: k_energy_partial<6><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+    }
+    k_sum_partials<<<1, 256, 0, st>>>(u->partial, nb, u->d_energy);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E, u->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        b->err = std::string("energy: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    return DGH_OK;
+}
+
+int dgh_batch_get_launch(const dgh_batch *b, int group, dgh_launch *o) {
+    if (!b || group < 0 || group >= int(b->groups.size())) return DGH_EINVAL;
+    return dgh_get_launch(b->groups[size_t(group)], o);
+}
+
+int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after) {
+    if (!b || steps < 1) return DGH_EINVAL;
+    const int64_t sc0 = b->step_count;
+    std::vector<int64_t> gsc;
+    for (dgh_ctx *u : b->groups) gsc.push_back(u->step_count);
+    int rc = tune_contexts(
+        b->groups, b->stream, steps, [&](int n) { return dgh_batch_step(b, n); }, [&]() { batch_drop_graphs(b); },
+        ms_before, ms_after, b->err);
+    b->step_count = sc0;
+    for (size_t i = 0; i < b->groups.size(); ++i) b->groups[i]->step_count = gsc[i];
+    return rc;
 }
 
 }  // extern "C"

@@ -310,6 +310,8 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
         float *qg = A.q + blk * QS;
         float *rg = A.res + blk * QS;
         const int cf0 = sC[e], cf1 = sC[32 + e], cf2 = sC[64 + e], cf3 = sC[96 + e];
+        bool has_src = false;   // one scan of the source list per tile, not per node
+        for (int s = 0; s < A.src.n; ++s) has_src |= A.src.cell[s] == k;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int n = w * C + c;
@@ -319,10 +321,11 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
             rhs[1] = -irho * dr[c];
             rhs[2] = -irho * ds[c];
             rhs[3] = -irho * dt[c];
-            for (int s = 0; s < A.src.n; ++s)
-                if (A.src.cell[s] == k)
-                    rhs[0] += (float)(A.src.amp[s] * ricker_integral_d(tstage, A.src.f_peak[s], A.src.t_s[s])) *
-                              A.src.vec[s * NP + n];
+            if (has_src)
+                for (int s = 0; s < A.src.n; ++s)
+                    if (A.src.cell[s] == k)
+                        rhs[0] += (float)(A.src.amp[s] * ricker_integral_d(tstage, A.src.f_peak[s], A.src.t_s[s])) *
+                                  A.src.vec[s * NP + n];
             float qn[4];
 #pragma unroll
             for (int fl = 0; fl < 4; ++fl) {

@@ -345,8 +345,92 @@ bool build_mesh(HostMesh &m, const RefTet &T, const RefTri &F, const RefLine &L,
         }
         m.corners.push_back(c);
     }
+    // p = 0 flags per entity
+    m.bfaceDir.assign(m.bface.size(), 0);
+    for (size_t b = 0; b < m.bface.size(); ++b) m.bfaceDir[b] = m.bc[m.bfaceDom[b]] == BC_DIRICHLET;
+    m.edgeDir.assign(size_t(Tn) * 3, 0);
+    for (int64_t ge = 0; ge < Tn * 3; ++ge)
+        if (m.edgeDom[ge] >= 0) m.edgeDir[ge] = m.bc[m.edgeDom[ge]] == BC_DIRICHLET;
+    m.endDir.assign(size_t(Ln) * 2, 0);
+    for (int64_t le = 0; le < Ln * 2; ++le)
+        if (m.endDom[le] >= 0) m.endDir[le] = m.bc[m.endDom[le]] == BC_DIRICHLET;
     (void)Nfp;
     return true;
+}
+
+void merge_meshes(const std::vector<HostMesh> &parts, HostMesh &o) {
+    o = HostMesh();
+    o.N = parts.empty() ? 0 : parts[0].N;
+    o.P = parts.empty() ? 0 : parts[0].P;
+    for (int d = 0; d < 6; ++d) o.bc[d] = BC_HABC;
+    for (int d = 0; d < 3; ++d) {
+        o.lo[d] = 1e300;
+        o.hi[d] = -1e300;
+    }
+    int64_t vOff = 0, kOff = 0, bOff = 0, tOff = 0, lOff = 0;
+    auto app = [](auto &dst, const auto &src) { dst.insert(dst.end(), src.begin(), src.end()); };
+    for (const HostMesh &m : parts) {
+        for (int d = 0; d < 3; ++d) {
+            o.lo[d] = std::min(o.lo[d], m.lo[d]);
+            o.hi[d] = std::max(o.hi[d], m.hi[d]);
+        }
+        app(o.VX, m.VX);
+        for (int32_t v : m.EToV) o.EToV.push_back(int32_t(v + vOff));
+        app(o.c, m.c);
+        app(o.rho, m.rho);
+        app(o.J, m.J);
+        app(o.drdx, m.drdx);
+        app(o.nrm, m.nrm);
+        app(o.fscale, m.fscale);
+        for (int64_t x : m.nbr) o.nbr.push_back(x >= 0 ? x + 4 * kOff : -1);
+        app(o.nbrSigma, m.nbrSigma);
+        for (int64_t x : m.bface) o.bface.push_back(x + 4 * kOff);
+        app(o.bfaceDom, m.bfaceDom);
+        for (int64_t x : m.bfaceOf) o.bfaceOf.push_back(x >= 0 ? x + bOff : -1);
+        app(o.bfaceDir, m.bfaceDir);
+        for (int64_t x : m.triBface) o.triBface.push_back(x + bOff);
+        app(o.triDom, m.triDom);
+        for (int32_t v : m.triV) o.triV.push_back(int32_t(v + vOff));
+        app(o.triAxes, m.triAxes);
+        app(o.drdx2, m.drdx2);
+        app(o.nrm2, m.nrm2);
+        app(o.fscale2, m.fscale2);
+        for (int64_t x : m.nbr2) o.nbr2.push_back(x >= 0 ? x + 3 * tOff : -1);
+        app(o.flip2, m.flip2);
+        app(o.edgeDom, m.edgeDom);
+        app(o.edgeDir, m.edgeDir);
+        for (int s = 0; s < 2; ++s) {
+            for (int64_t x : m.linTri[s]) o.linTri[s].push_back(x + tOff);
+            app(o.linEdge[s], m.linEdge[s]);
+            app(o.linRev[s], m.linRev[s]);
+        }
+        app(o.linA, m.linA);
+        app(o.linB, m.linB);
+        app(o.linAxis, m.linAxis);
+        for (int32_t v : m.linV) o.linV.push_back(int32_t(v + vOff));
+        app(o.J1, m.J1);
+        for (int64_t x : m.nbr1) o.nbr1.push_back(x >= 0 ? x + 2 * lOff : -1);
+        app(o.endDom, m.endDom);
+        app(o.endDir, m.endDir);
+        for (HostMesh::Corner c : m.corners) {
+            for (int q = 0; q < 3; ++q) c.line[q] += lOff;
+            o.corners.push_back(c);
+        }
+        if (m.dtCell.empty()) {
+            o.dtCell.insert(o.dtCell.end(), size_t(m.K), 0.0);
+        } else {
+            app(o.dtCell, m.dtCell);
+        }
+        vOff += m.Nv;
+        kOff += m.K;
+        bOff += int64_t(m.bface.size());
+        tOff += m.Ktri;
+        lOff += m.Klin;
+    }
+    o.Nv = vOff;
+    o.K = kOff;
+    o.Ktri = tOff;
+    o.Klin = lOff;
 }
 
 double dt_rule(const HostMesh &m, double cfl) {

@@ -101,8 +101,17 @@ struct HostMesh {
     // 0D
     struct Corner { int faces[3]; int64_t line[3]; int end[3]; };  // line[0]: YZ edge, [1]: XZ, [2]: XY
     std::vector<Corner> corners;
+    // p = 0 flags resolved per entity (a batch of problems has one bc[] per problem)
+    std::vector<int8_t> bfaceDir;  // per boundary face
+    std::vector<int8_t> edgeDir;   // per triangle edge (open edges only)
+    std::vector<int8_t> endDir;    // per line end (corner ends only)
+    std::vector<double> dtCell;    // per-cell time step (batches); empty: one time step for all
     bool face_habc(int d) const { return bc[d] == BC_HABC && P >= 1; }
 };
+
+// Disjoint union of meshes of the same N and P (a batch of independent
+// problems): indices are offset, per-entity flags and time steps kept.
+void merge_meshes(const std::vector<HostMesh> &parts, HostMesh &out);
 
 // Builds all meshes; returns false with a message on invalid input.
 bool build_mesh(HostMesh &m, const RefTet &T, const RefTri &F, const RefLine &L, std::string &err);

@@ -101,3 +101,22 @@ def random_state(seed, shape, scale=1.0):
     """Reproducible uniform(-scale, scale) array of the given shape."""
     rng = np.random.Generator(np.random.Philox(seed))
     return (2.0 * rng.random(shape) - 1.0) * scale
+
+
+def batch_problems(seed, count=48, n_range=(8, 24), orders=(3, 4, 5), habc_orders=(2, 4, 6), f_range=(2.0, 6.0),
+                   src_box=0.5):
+    """A seeded list of independent problems for the batching form: problem i
+    has n ~ U{n_range} hexes per axis on [-1,1]^3 (jitter 2% h, mesh seed
+    seed + i), degree N and HABC order P drawn uniformly from the given sets,
+    c = rho = 1, and a Ricker point source of peak frequency f0 ~ U[f_range]
+    at xs ~ U[-src_box, src_box]^3 with delay t_s = 1.25 / f0."""
+    out = []
+    for i in range(count):
+        u = [float(hashed_uniform(seed, i, j)[0]) for j in range(7)]
+        n = n_range[0] + int(u[0] * (n_range[1] - n_range[0] + 1))
+        N = orders[int(u[1] * len(orders))]
+        P = habc_orders[int(u[2] * len(habc_orders))]
+        f0 = f_range[0] + u[3] * (f_range[1] - f_range[0])
+        xs = [(2.0 * u[4 + a] - 1.0) * src_box for a in range(3)]
+        out.append({"n": n, "N": N, "P": P, "f0": f0, "xs": xs, "t_s": 1.25 / f0, "mesh_seed": seed + i})
+    return out

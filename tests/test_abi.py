@@ -76,3 +76,25 @@ def test_plan_mixed_boundaries_and_dt():
     assert info["n_corners"] == 4              # K^pnt = 4 with one Dirichlet face
     h = 2.0 / n
     assert abs(info["dt"] - 1.0 / (9 * 2 * np.sqrt(2) / h)) < 1e-12
+
+
+def test_batch_plan_groups_and_sums():
+    """Host-only batch grouping: problems are grouped by (N, P) in order of
+    first appearance and every union mesh has the summed sizes of its problems
+    (cells, triangles, lines, corners, boundary faces, DOFs)."""
+    from oracle.mesh import BC_DIRICHLET
+    specs = [(2, 3, 2, (0,) * 6), (3, 4, 1, (0,) * 6), (2, 3, 2, (BC_DIRICHLET,) + (0,) * 5),
+             (2, 2, 0, (0,) * 6), (3, 3, 2, (0,) * 6)]
+    probs = []
+    for i, (n, N, P, bc) in enumerate(specs):
+        VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=40 + i)
+        probs.append(dict(VX=VX, EToV=EToV, N=N, P=P, bc=bc))
+    gof, infos = dgh.batch_plan(probs)
+    assert gof == [0, 1, 0, 2, 0]
+    assert len(infos) == 3
+    singles = [dgh.plan(**p) for p in probs]
+    for g, info in enumerate(infos):
+        members = [s for s, gg in zip(singles, gof) if gg == g]
+        for k in ("n_cells", "n_tris", "n_lines", "n_corners", "n_bfaces", "ndof"):
+            assert info[k] == sum(m[k] for m in members), (g, k)
+        assert (info["order"], info["habc_order"]) == (members[0]["order"], members[0]["habc_order"])
