@@ -238,6 +238,65 @@ def run_batch_form(args):
         s.close()
 
 
+PREC_SEED = 3000
+PREC_NAMES = {0: "fp32", 1: "bf16_tc", 2: "fp16_tc", 3: "split_bf16_tc"}
+
+
+def run_precision_form(args):
+    """Precision form: the N = 6 layered workload (32^3 hexahedra x 6 =
+    196,608 tets, three horizontal layers (c, rho) = (1,1), (1.5,1.2), (2,1.5)
+    bottom to top, HABC P = 4, Gaussian pulse of width 0.1 centred at
+    (0.75, 0.70, 0.80) + U(+-0.05) seeded), stepped with the FP32 CUDA-core
+    3D kernel and with the tensor-core kernels (BF16, FP16, split BF16).
+    Each arm: CUDA-event time of K steps on its stream, the mean 3D launch,
+    and the relative L2 difference of its 3D fields from the FP32 arm's after
+    the same steps."""
+    import torch
+    import paper_1610_05023_b300 as dgh
+    from paper_1610_05023_b300 import workloads as W
+    torch.cuda.set_device(0)
+    n = args.n if args.n != 48 else 32
+    VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=PREC_SEED)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.0, 1.5, 2.0], [1.0, 1.2, 1.5])
+    x0 = W.seeded_point(PREC_SEED, [0.75, 0.70, 0.80], 0.05)
+    peak, peak_kind = peaks()
+    arms, ref = [], None
+    for prec in (0, 3, 2, 1):
+        st = torch.cuda.Stream()
+        g = dgh.Solver(VX, EToV, 6, 4, c=c, rho=rho, stream=st, precision=prec)
+        info = g.info
+        g.init_gaussian(x0, 0.1)
+        g.step(args.warmup)
+        g.sync()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.step(args.steps)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        q3 = g.get_state(3)
+        if ref is None:
+            ref = q3
+        diff = [float(np.linalg.norm(q3[:, f] - ref[:, f]) / max(np.linalg.norm(ref[:, f]), 1e-30)) for f in range(4)]
+        kt = g.time_kernels(10)
+        K, Np, Nfp = info["n_cells"], info["Np"], 28
+        bpt = 4 * (16 * Np + 16 * Nfp) + 100
+        ach = K * bpt / (kt["k3d"] * 1e-3) / 1e9
+        arms.append({"precision": PREC_NAMES[prec], "ms_per_step": ms / args.steps,
+                     "value": info["ndof"] * 5 * args.steps / (ms * 1e-3), "k3d_launch_ms": kt["k3d"],
+                     "k3d_hbm_frac": ach / peak, "k3d_achieved_gbs": ach, "rel_l2_vs_fp32": diff,
+                     "launch": g.launch})
+        g.close()
+    line = {"form": "precision", "metric": METRIC, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32 state; bf16/fp16 tensor-core products",
+            "data": "synthetic",
+            "config": {"workload": "layered%d_N6_P4_gaussian" % n, "n_cells": 6 * n ** 3, "seed": PREC_SEED,
+                       "bytes_per_tet": 4 * (16 * 84 + 16 * 28) + 100, "peak_gbs": peak, "peak_kind": peak_kind},
+            "arms": arms, "value": max(a["value"] for a in arms)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -246,13 +305,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=48, help="hexes per axis (48 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "batch"],
-                    help="batch: the batching form (48 independent problems) instead of the plain workload")
+    ap.add_argument("--form", default="plain", choices=["plain", "batch", "precision"],
+                    help="batch: the batching form (48 independent problems); precision: the N = 6 layered "
+                         "workload with the FP32 and tensor-core 3D kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.form == "batch":
         return run_batch_form(args)
+    if args.form == "precision":
+        return run_precision_form(args)
 
     import torch
     import paper_1610_05023_b300 as dgh

@@ -69,8 +69,14 @@ extern "C" {
 #define DGH_BC_HABC       0   /* Pade HABC of order P (P = 0: basic ABC, Sec. 3.2) */
 #define DGH_BC_DIRICHLET  1   /* p = 0 (free surface, Sec. 2.4, Sec. 3.2)         */
 
-/* Arithmetic of the 3D volume / lift contractions. */
-#define DGH_PREC_FP32     0   /* FP32 CUDA cores (the plain path)                 */
+/* Arithmetic of the 3D volume / lift contractions (the products
+ * D_j x and LIFT x of eq. dgLocalRhs); everything else (fluxes, update,
+ * 2D/1D/0D levels) is FP32 in every mode.  The tensor-core modes run the
+ * products on tcgen05 tensor cores with FP32 accumulation in tensor memory. */
+#define DGH_PREC_FP32        0   /* FP32 CUDA cores (the plain path)              */
+#define DGH_PREC_BF16_TC     1   /* BF16 operands, one product                    */
+#define DGH_PREC_FP16_TC     2   /* FP16 operands, one product                    */
+#define DGH_PREC_SPLIT_BF16  3   /* x = hi + lo in BF16, hi*hi + lo*hi + hi*lo    */
 
 typedef struct dgh_ctx dgh_ctx;
 
@@ -79,7 +85,7 @@ typedef struct dgh_desc {
     int32_t        order;        /* N, 1..6                                     */
     int32_t        habc_order;   /* P, 0..8 (common to all HABC faces)           */
     int32_t        bc[6];        /* DGH_BC_* per domain face                     */
-    int32_t        precision;    /* DGH_PREC_*                                   */
+    int32_t        precision;    /* DGH_PREC_* (batches group problems by N, P and precision) */
     int32_t        reserved0;
     int64_t        n_vertices;
     int64_t        n_cells;

@@ -18,6 +18,9 @@ DGH_OK = 0
 BC_HABC = 0
 BC_DIRICHLET = 1
 PREC_FP32 = 0
+PREC_BF16_TC = 1
+PREC_FP16_TC = 2
+PREC_SPLIT_BF16 = 3
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -6: "ESTATE", -7: "EUNSUPPORTED"}
 
@@ -116,7 +119,7 @@ def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl):
+def _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl, precision=PREC_FP32):
     VX = np.ascontiguousarray(VX, dtype=np.float64)
     EToV = np.ascontiguousarray(EToV, dtype=np.int32)
     K = EToV.shape[0]
@@ -126,7 +129,7 @@ def _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl):
     d.order, d.habc_order = int(N), int(P)
     for i in range(6):
         d.bc[i] = int(bc[i])
-    d.precision = PREC_FP32
+    d.precision = int(precision)
     d.n_vertices, d.n_cells = VX.shape[0], K
     d.vertices = _dptr(VX)
     d.cells = EToV.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
@@ -135,10 +138,10 @@ def _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl):
     return d, (VX, EToV, c, rho)   # keep the arrays alive with the descriptor
 
 
-def plan(VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0):
+def plan(VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0, precision=PREC_FP32):
     """Host-only set-up (no GPU): sizes, ndof and time step of a problem."""
     lib = load_library()
-    d, _keep = _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl)
+    d, _keep = _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl, precision)
     i = _Info()
     rc = lib.dgh_plan(ctypes.byref(d), ctypes.byref(i))
     if rc != DGH_OK:
@@ -155,7 +158,8 @@ def batch_plan(problems):
     for i, kw in enumerate(problems):
         kw = dict(kw)
         d, k = _make_desc(kw.pop("VX"), kw.pop("EToV"), kw.pop("N"), kw.pop("P"), kw.pop("bc", (BC_HABC,) * 6),
-                          kw.pop("c", 1.0), kw.pop("rho", 1.0), kw.pop("dt", 0.0), kw.pop("cfl", 1.0))
+                          kw.pop("c", 1.0), kw.pop("rho", 1.0), kw.pop("dt", 0.0), kw.pop("cfl", 1.0),
+                          kw.pop("precision", PREC_FP32))
         if kw:
             raise TypeError("unknown keys %s" % sorted(kw))
         descs[i] = d
@@ -176,12 +180,15 @@ class Solver:
     degree, P HABC order (0 = basic ABC), bc six codes (BC_HABC /
     BC_DIRICHLET for -x,+x,-y,+y,-z,+z), c and rho per cell (or scalars),
     dt > 0 fixed step (else cfl * the min-over-cells rule), stream a
-    torch.cuda.Stream, an integer cudaStream_t or None.
+    torch.cuda.Stream, an integer cudaStream_t or None, precision one of
+    PREC_FP32 (CUDA cores), PREC_BF16_TC, PREC_FP16_TC, PREC_SPLIT_BF16
+    (tensor-core products of the 3D volume and lift terms).
     """
 
-    def __init__(self, VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0, stream=None):
+    def __init__(self, VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0, stream=None,
+                 precision=PREC_FP32):
         lib = load_library()
-        d, _keep = _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl)
+        d, _keep = _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl, precision)
         if stream is None:
             sptr = None
         elif isinstance(stream, int):

@@ -89,6 +89,8 @@ struct dgh_ctx {
     // launch shapes
     int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0, sms = 1;
     int cta3_per_sm = 0;              // tunable: persistent 3D CTAs per SM (0 = occupancy limit)
+    int precision = DGH_PREC_FP32;    // arithmetic of the 3D contractions (DGH_PREC_*)
+    uint8_t *tcops = nullptr;         // tensor-core operand images of D_r, D_s, D_t, LIFT (hi, then lo)
     unsigned long long *tile_ctr = nullptr;   // [11] block counters of the 3D launches of a step
     size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
     int smem_optin = 0;
@@ -227,6 +229,49 @@ Args1 args1(dgh_ctx *c, int cur, bool update) {
     return A;
 }
 
+int tc_code(int precision) {
+    return precision == DGH_PREC_BF16_TC ? TC_BF16 : precision == DGH_PREC_FP16_TC ? TC_FP16 : TC_SPLIT_BF16;
+}
+
+// Operator images of the tensor-core kernel: the B operands D_r, D_s, D_t
+// (NPAD x NPAD) and LIFT (NPAD x 4 FPAD, face f's nodes at K = f FPAD + m),
+// rows = output nodes, in the K-major canonical layout without swizzle:
+// 8-row x 16-byte core matrices, element (n, k) of a matrix with R rows at
+// byte (k/8)(R/8)128 + (n/8)128 + (n%8)16 + (k%8)2; zero padding.  The
+// split variant appends the BF16 residuals x - hi(x) of every entry.
+std::vector<uint8_t> tc_operator_images(const RefTet &T3, int precision) {
+    const int Np = T3.Np, Nfp = T3.Nfp;
+    const int NPAD = (Np + 15) / 16 * 16, FPAD = (Nfp + 15) / 16 * 16, KL = 4 * FPAD;
+    const bool split = precision == DGH_PREC_SPLIT_BF16, half = precision == DGH_PREC_FP16_TC;
+    const size_t BD = size_t(NPAD) * NPAD * 2, BL = size_t(NPAD) * KL * 2, BOPS = 3 * BD + BL;
+    std::vector<uint8_t> img(BOPS * (split ? 2 : 1), 0);
+    auto put = [&](size_t base, int n, int k, double x) {
+        const size_t off = base + size_t(k / 8) * (NPAD / 8) * 128 + size_t(n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+        uint16_t hi = 0, lo = 0;
+        if (half) {
+            const __half h = __float2half_rn(float(x));
+            std::memcpy(&hi, &h, 2);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(float(x));
+            std::memcpy(&hi, &h, 2);
+            if (split) {
+                const __nv_bfloat16 l = __float2bfloat16_rn(float(x - double(__bfloat162float(h))));
+                std::memcpy(&lo, &l, 2);
+            }
+        }
+        std::memcpy(&img[off], &hi, 2);
+        if (split) std::memcpy(&img[BOPS + off], &lo, 2);
+    };
+    const Mat *Dj[3] = {&T3.Dr, &T3.Ds, &T3.Dt};
+    for (int j = 0; j < 3; ++j)
+        for (int n = 0; n < Np; ++n)
+            for (int k = 0; k < Np; ++k) put(j * BD, n, k, (*Dj[j])(n, k));
+    for (int n = 0; n < Np; ++n)
+        for (int f = 0; f < 4; ++f)
+            for (int m = 0; m < Nfp; ++m) put(3 * BD, n, f * FPAD + m, T3.LIFT(n, f * Nfp + m));
+    return img;
+}
+
 // part: 0 = all cells, 1 = interior blocks, 2 = blocks with HABC faces
 template <int N>
 struct Launch3 {
@@ -251,8 +296,17 @@ struct Launch3 {
         if (part == 2) A.blk_begin = c->Ki32;
         const int64_t nblk = A.blk_end - A.blk_begin;
         if (nblk <= 0) return DGH_OK;
-        const int grid = (int)std::min<int64_t>(nblk, c->grid3);   // persistent CTAs, blocks claimed dynamically
         A.max_tiles = int(std::min<int64_t>(nblk, int64_t(1) << 30));
+        if (c->precision != DGH_PREC_FP32) {   // tensor-core kernel: tiles of four 32-cell blocks
+            const int grid = (int)std::min<int64_t>((nblk + 3) / 4, c->grid3);
+            switch (tc_code(c->precision)) {
+                case TC_BF16: k3d_tc<N, TC_BF16><<<grid, 256, CfgTC<N, TC_BF16>::SMEM, st>>>(A, sc, c->tcops); break;
+                case TC_FP16: k3d_tc<N, TC_FP16><<<grid, 256, CfgTC<N, TC_FP16>::SMEM, st>>>(A, sc, c->tcops); break;
+                default: k3d_tc<N, TC_SPLIT_BF16><<<grid, 256, CfgTC<N, TC_SPLIT_BF16>::SMEM, st>>>(A, sc, c->tcops); break;
+            }
+            return DGH_OK;
+        }
+        const int grid = (int)std::min<int64_t>(nblk, c->grid3);   // persistent CTAs, blocks claimed dynamically
         k3d_stage<N><<<grid, Cfg3<N>::NW * 32, Cfg3<N>::SMEM, st>>>(A, sc);
         return DGH_OK;
     }
@@ -328,7 +382,22 @@ struct SetAttrs {
         cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         c->smem_optin = optin;
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N>, Cfg3<N>::NW * 32, c->smem3);
+        if (c->precision == DGH_PREC_FP32) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N>, Cfg3<N>::NW * 32, c->smem3);
+        } else {
+            // one CTA owns TCOLS tensor-memory columns (512 per SM)
+            auto occ = [&](auto kern, size_t smem, int tcols) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, smem);
+                nb = std::min(nb, 512 / tcols);
+                c->smem3 = smem;
+            };
+            switch (tc_code(c->precision)) {
+                case TC_BF16: occ(k3d_tc<N, TC_BF16>, CfgTC<N, TC_BF16>::SMEM, CfgTC<N, TC_BF16>::TCOLS); break;
+                case TC_FP16: occ(k3d_tc<N, TC_FP16>, CfgTC<N, TC_FP16>::SMEM, CfgTC<N, TC_FP16>::TCOLS); break;
+                default: occ(k3d_tc<N, TC_SPLIT_BF16>, CfgTC<N, TC_SPLIT_BF16>::SMEM, CfgTC<N, TC_SPLIT_BF16>::TCOLS); break;
+            }
+        }
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         c->occ3 = nb;
@@ -351,7 +420,8 @@ struct Shapes {
         if ((int64_t)c->smem2 > c->smem_optin || (int64_t)c->smem1 > c->smem_optin) return DGH_EINVAL;
         const int sms = c->sms;
         const int per_sm = c->cta3_per_sm > 0 ? std::min(c->cta3_per_sm, std::max(c->occ3, 1)) : std::max(c->occ3, 1);
-        c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(c->K32, (int64_t)per_sm * sms));
+        const int64_t tiles3 = c->precision == DGH_PREC_FP32 ? c->K32 : (c->K32 + 3) / 4;
+        c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)per_sm * sms));
         int nb2 = 0, nb1 = 0;
         if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, 256, c->smem2);
         if (c->L) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k1d_stage<N, true>, 256, c->smem1);
@@ -527,8 +597,9 @@ static int validate_desc(const dgh_desc *d) {
         g_create_error = "order N must be 1..6 and HABC order P 0..8";
         return DGH_EUNSUPPORTED;
     }
-    if (d->precision != DGH_PREC_FP32) {
-        g_create_error = "precision not supported by this build";
+    if (d->precision != DGH_PREC_FP32 && d->precision != DGH_PREC_BF16_TC && d->precision != DGH_PREC_FP16_TC &&
+        d->precision != DGH_PREC_SPLIT_BF16) {
+        g_create_error = "unknown precision code";
         return DGH_EUNSUPPORTED;
     }
     if (d->n_cells > (int64_t(1) << 26)) {
@@ -764,6 +835,8 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
             (rc = upload(ctx, ctx->fperm3, fperm)) || (rc = upload(ctx, ctx->nslot3, nslot)) ||
             (rc = upload(ctx, ctx->cellv, cellv)) || (rc = upload(ctx, ctx->rst, rst)) || (rc = upload(ctx, ctx->ew, ew)))
             return fail(rc, "");
+        if (ctx->precision != DGH_PREC_FP32 && (rc = upload(ctx, ctx->tcops, tc_operator_images(T3, ctx->precision))))
+            return fail(rc, "");
     }
     // ---------------------------------------------------------------- 2D
     const int64_t Tn = m.Ktri;
@@ -938,6 +1011,7 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
     cudaGetDevice(&ctx->device);
     ctx->N = d->order;
     ctx->P = d->habc_order;
+    ctx->precision = d->precision;
     int rc = host_setup(d, ctx->mesh, ctx->ref3, ctx->ref2, ctx->ref1, ctx->habc);
     if (rc) {
         dgh_destroy(ctx);
@@ -1564,7 +1638,7 @@ int batch_build_graph(dgh_batch *b) {
 
 // Host-only grouping of problems by (N, P), in order of first appearance.
 std::vector<int> group_by_order(const std::vector<std::pair<int, int>> &np, int &ngroups) {
-    std::vector<std::pair<int, int>> keys;
+    std::vector<std::pair<int, int>> keys;   // (N, P * 8 + precision) in order of first appearance
     std::vector<int> g(np.size());
     for (size_t i = 0; i < np.size(); ++i) {
         size_t j = 0;
@@ -1604,7 +1678,7 @@ int dgh_batch_plan(const dgh_desc *descs, int count, int *group_of, dgh_info *gr
     for (int i = 0; i < count; ++i) {
         int rc = validate_desc(&descs[i]);
         if (rc) return rc;
-        np[i] = {descs[i].order, descs[i].habc_order};
+        np[i] = {descs[i].order, descs[i].habc_order * 8 + descs[i].precision};
     }
     int ng = 0;
     std::vector<int> g = group_by_order(np, ng);
@@ -1660,7 +1734,7 @@ int dgh_batch_create(dgh_ctx *const *problems, int count, dgh_batch **out) {
             g_create_error = "all problems must live on the current device";
             return DGH_EINVAL;
         }
-        np[i] = {problems[i]->N, problems[i]->P};
+        np[i] = {problems[i]->N, problems[i]->P * 8 + problems[i]->precision};
     }
     int ng = 0;
     std::vector<int> gof = group_by_order(np, ng);
@@ -1686,6 +1760,7 @@ int dgh_batch_create(dgh_ctx *const *problems, int count, dgh_batch **out) {
         u->device = dev;
         u->N = first->N;
         u->P = first->P;
+        u->precision = first->precision;
         u->ref3 = first->ref3;
         u->ref2 = first->ref2;
         u->ref1 = first->ref1;

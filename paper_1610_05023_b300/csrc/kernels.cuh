@@ -108,6 +108,7 @@ __device__ __forceinline__ double ricker_integral_d(double t, double f, double t
 
 }  // namespace dgh
 #include "k3d.cuh"
+#include "k3d_tc.cuh"
 namespace dgh {
 
 // ==================================================================== 2D
