@@ -192,7 +192,10 @@ __global__ void __launch_bounds__(256, 1) k3d_tc(Args3 A, StageCoef sc, const ui
     }
     for (int i = tid; i < NF; i += G::NTHR) sFm[i] = A.fmask[i];
     for (int i = tid; i < 6 * NFP; i += G::NTHR) sFp[i] = A.fperm[i];
-    for (int i = tid; i < 3 * NP; i += G::NTHR) sNs[i] = A.nslot[i];
+    for (int i = tid; i < 3 * NP; i += G::NTHR) {   // face slots of every node, decoded to (f << 8 | m)
+        const int v = A.nslot[i];
+        sNs[i] = v < 0 ? -1 : ((v / NFP) << 8) | (v % NFP);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -390,15 +393,17 @@ __global__ void __launch_bounds__(256, 1) k3d_tc(Args3 A, StageCoef sc, const ui
             return false;
         };
         {
+            // one call site of each (instruction-cache footprint); the next
+            // slab's values are copied into place after the current one is done
             constexpr int NS = G::NSV + G::NSF;
             float va[48], vb[48];
             load_slab(0, va);
-            for (int s = 0; s < NS; s += 2) {
+#pragma unroll 1
+            for (int s = 0; s < NS; ++s) {
                 if (s + 1 < NS) load_slab(s + 1, vb);
                 if ((stop = process_slab(s, va))) break;
-                if (s + 1 >= NS) break;
-                if (s + 2 < NS) load_slab(s + 2, va);
-                if ((stop = process_slab(s + 1, vb))) break;
+#pragma unroll
+                for (int i = 0; i < 48; ++i) va[i] = vb[i];
             }
         }
         if (stop) break;
@@ -461,11 +466,11 @@ __global__ void __launch_bounds__(256, 1) k3d_tc(Args3 A, StageCoef sc, const ui
                             qn[fl] = qo[c][fl] + sc.b * r;
                             qg[idx] = qn[fl];
                         }
-#pragma unroll
+#pragma unroll 1
                         for (int sl = 0; sl < 3; ++sl) {
                             const int slotn = sNs[n * 3 + sl];
                             if (slotn < 0) break;
-                            const int f = slotn / NFP, m = slotn % NFP;
+                            const int f = slotn >> 8, m = slotn & 255;
                             const float nx = f == 0 ? nrm[0][0] : f == 1 ? nrm[1][0] : f == 2 ? nrm[2][0] : nrm[3][0];
                             const float ny = f == 0 ? nrm[0][1] : f == 1 ? nrm[1][1] : f == 2 ? nrm[2][1] : nrm[3][1];
                             const float nz = f == 0 ? nrm[0][2] : f == 1 ? nrm[1][2] : f == 2 ? nrm[2][2] : nrm[3][2];
