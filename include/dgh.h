@@ -303,6 +303,62 @@ int dgh_batch_get_launch(const dgh_batch *b, int group, dgh_launch *out);
  * batch steps; fields, times and step counts are restored afterwards. */
 int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after);
 
+/* ---------------------------------------------------------------- learned closure
+ * A learned correction of the face condition of a low-order HABC chain:
+ * the exterior state seen by the 3D flux at a boundary face node becomes
+ * 2 (r^- + MLP(x)) instead of 2 r^- (eq. proc:pi00Star, r^- = (1/M) sum c_a p*_a),
+ * with x = (p, n.u, p_1, p_2, dp*_1/dt, dp*_2/dt) at that node: the 3D trace
+ * pressure and outward normal velocity, the full auxiliary pressures of sets
+ * 1 and 2 (p_a = p*_a + r^- + r^+) and the time derivatives of p*_1, p*_2 of
+ * the stage just computed (0 for sets beyond P).  The chain's own algebra
+ * keeps the uncorrected r^-.  The paper has no learned component.
+ * MLP 6 -> 64 (tanh) -> 64 (tanh) -> 1, DGH_MLP_NPARAM = 4673 parameters:
+ * W1 [64][6], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 (row-major, in
+ * that order).  Inference uses the weights rounded to BF16, FP32 arithmetic. */
+#define DGH_MLP_NPARAM 4673
+
+/* Enables the closure on this context with the given weights (n = 4673), or
+ * disables it (w = NULL).  DGH_EINVAL without HABC faces (P = 0).  Not
+ * supported inside a batch. */
+int dgh_closure_set_weights(dgh_ctx *ctx, const float *w, size_t n);
+
+/* Training data: adds a shadow HABC chain of order shadow_order (its own 2D
+ * face, 1D edge and 0D corner fields, zero at start and after
+ * dgh_init_gaussian) driven one-way by this context's 3D traces, and records
+ * on every step that is a multiple of `every` (at its first stage) the rows
+ * (x of the shadow chain, r^-_this - r^-_shadow) of a hashed fraction of the
+ * boundary face nodes into a device buffer of max_samples rows (further rows
+ * are dropped).  The shadow chain never changes this context's solution. */
+int dgh_closure_record(dgh_ctx *ctx, int shadow_order, int every, double fraction, int64_t max_samples, uint64_t seed);
+
+/* Copies up to max_rows recorded rows [row][7] (6 features, target) into out
+ * (host, caller-owned); *count = rows recorded (at most max_samples). */
+int dgh_closure_samples(dgh_ctx *ctx, float *out, int64_t max_rows, int64_t *count);
+
+/* Context-free device calls (current device; errors via dgh_last_error(NULL)).
+ * dgh_closure_eval: y[r] = MLP(X[r]) with the inference kernel (BF16-rounded
+ * weights), X [n][6] host, y [n] host.
+ * dgh_mlp_loss_grad: FP32 weights w, loss = (1/2n) sum (MLP(X_r) - Y_r)^2 and
+ * its gradient with respect to w (host arrays), by the training kernels.
+ * dgh_mlp_train: minibatch Adam (Kingma & Ba) on the GPU from seeded
+ * Glorot-uniform weights, on standardised inputs and target; the returned
+ * weights w_out take raw features and return the raw target.  loss_hist
+ * (cfg->steps entries, or NULL) receives each minibatch's mean-squared error
+ * and *final_mse (or NULL) that of all rows, both in target units. */
+typedef struct dgh_train_cfg {
+    int64_t steps;        /* Adam steps                                 */
+    int64_t batch;        /* samples per step (drawn with replacement)  */
+    float   lr;           /* learning rate                              */
+    float   beta1, beta2; /* <= 0: 0.9, 0.999                           */
+    float   eps;          /* <= 0: 1e-8                                 */
+    uint64_t seed;        /* initial weights and batches                */
+} dgh_train_cfg;
+
+int dgh_closure_eval(const float *w, const float *X, int64_t n, float *y);
+int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n, double *loss, float *grad);
+int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
+                  double *final_mse);
+
 #ifdef __cplusplus
 }
 #endif

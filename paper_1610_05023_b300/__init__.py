@@ -52,6 +52,16 @@ class _Info(ctypes.Structure):
     ]
 
 
+MLP_NPARAM = 4673
+MLP_IN = 6
+
+
+class _TrainCfg(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("batch", ctypes.c_int64), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
 class _Launch(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in
                 ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1", "occ3", "sms")]
@@ -106,6 +116,18 @@ def load_library(path=LIB_PATH):
         "dgh_batch_get_energy": (ctypes.c_int, [P, ctypes.c_int, D]),
         "dgh_batch_get_launch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_Launch)]),
         "dgh_batch_tune": (ctypes.c_int, [P, ctypes.c_int, D, D]),
+        "dgh_closure_set_weights": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+        "dgh_closure_record": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                              ctypes.c_uint64]),
+        "dgh_closure_samples": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
+                                               ctypes.POINTER(ctypes.c_int64)]),
+        "dgh_closure_eval": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_float)]),
+        "dgh_mlp_loss_grad": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_float), ctypes.c_int64, D,
+                                             ctypes.POINTER(ctypes.c_float)]),
+        "dgh_mlp_train": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
+                                         ctypes.POINTER(_TrainCfg), ctypes.POINTER(ctypes.c_float), D, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -117,6 +139,55 @@ def load_library(path=LIB_PATH):
 
 def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _lib_check(rc):
+    if rc != DGH_OK:
+        raise DghError(rc, load_library().dgh_last_error(None).decode())
+
+
+def closure_eval(w, X):
+    """MLP(X) [n] of the device inference kernel (BF16-rounded weights)."""
+    lib = load_library()
+    w = _f32(w, (MLP_NPARAM,))
+    X = _f32(X)
+    y = np.empty(X.shape[0], np.float32)
+    _lib_check(lib.dgh_closure_eval(_fptr(w), _fptr(X), X.shape[0], _fptr(y)))
+    return y
+
+
+def mlp_loss_grad(w, X, Y):
+    """(loss, grad) of loss = mean (MLP(X) - Y)^2 / 2 by the device training kernels."""
+    lib = load_library()
+    w, X, Y = _f32(w, (MLP_NPARAM,)), _f32(X), _f32(Y)
+    loss = ctypes.c_double()
+    g = np.empty(MLP_NPARAM, np.float32)
+    _lib_check(lib.dgh_mlp_loss_grad(_fptr(w), _fptr(X), _fptr(Y), X.shape[0], ctypes.byref(loss), _fptr(g)))
+    return loss.value, g
+
+
+def mlp_train(X, Y, steps=2000, batch=4096, lr=1e-3, seed=1, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Adam on the GPU; returns (weights for raw features, minibatch MSE history, final MSE)."""
+    lib = load_library()
+    X, Y = _f32(X), _f32(Y)
+    cfg = _TrainCfg(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(seed))
+    w = np.empty(MLP_NPARAM, np.float32)
+    hist = np.empty(max(int(steps), 1))
+    fin = ctypes.c_double()
+    _lib_check(lib.dgh_mlp_train(_fptr(X), _fptr(Y), X.shape[0], ctypes.byref(cfg), _fptr(w), _dptr(hist),
+                                 ctypes.byref(fin)))
+    return w, hist[:int(steps)], fin.value
 
 
 def _make_desc(VX, EToV, N, P, bc, c, rho, dt, cfl, precision=PREC_FP32):
@@ -312,6 +383,27 @@ class Solver:
     def load_state(self, blob):
         buf = ctypes.create_string_buffer(bytes(blob), len(blob))
         self._check(self._lib.dgh_load_state(self._h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+
+    def closure_set_weights(self, w):
+        """Enable the learned closure with MLP weights w (4673), or disable it (None)."""
+        if w is None:
+            self._check(self._lib.dgh_closure_set_weights(self._h, None, 0))
+            return
+        w = _f32(w, (MLP_NPARAM,))
+        self._check(self._lib.dgh_closure_set_weights(self._h, _fptr(w), w.size))
+
+    def closure_record(self, shadow_order=2, every=1, fraction=1.0, max_samples=1 << 20, seed=0):
+        self._check(self._lib.dgh_closure_record(self._h, int(shadow_order), int(every), float(fraction),
+                                                 int(max_samples), int(seed)))
+
+    def closure_samples(self, max_rows=None):
+        """Recorded rows [n][7]: 6 features, target (r^-_this - r^-_shadow)."""
+        cnt = ctypes.c_int64()
+        self._check(self._lib.dgh_closure_samples(self._h, None, 0, ctypes.byref(cnt)))
+        n = cnt.value if max_rows is None else min(cnt.value, int(max_rows))
+        out = np.empty((n, 7), np.float32)
+        self._check(self._lib.dgh_closure_samples(self._h, _fptr(out), n, ctypes.byref(cnt)))
+        return out
 
     @property
     def launch(self):

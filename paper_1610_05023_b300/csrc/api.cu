@@ -94,6 +94,28 @@ struct dgh_ctx {
     unsigned long long *tile_ctr = nullptr;   // [11] block counters of the 3D launches of a step
     size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
     int smem_optin = 0;
+    // learned closure (inference on this context's chain)
+    bool cl_on = false;
+    float *cl_w = nullptr;            // MLP weights (BF16-rounded, stored FP32) [MLP_NPARAM]
+    float *cl_feat = nullptr;         // [T][Np2][6]
+    float *cl_rm = nullptr;           // [T][Np2] r^- of this chain
+    // shadow chain of another HABC order driven one-way by the 3D traces (sample recording)
+    struct Shadow {
+        int P = 0, M = 1, tile2 = 1, tile1 = 1, grid2 = 1, grid1 = 1;
+        size_t smem2 = 0, smem1 = 0, smem0 = 0;
+        HabcOps habc;
+        float *q2 = nullptr, *res2 = nullptr, *tr2[2] = {nullptr, nullptr}, *qb2 = nullptr, *q0_3 = nullptr;
+        float *q1 = nullptr, *res1 = nullptr, *tr1[2] = {nullptr, nullptr}, *qb1 = nullptr, *q0_2 = nullptr;
+        float *H1 = nullptr, *H2 = nullptr, *Hc = nullptr, *cP = nullptr;
+        float *feat = nullptr, *rm = nullptr, *rm_main = nullptr;
+        float *samples = nullptr;
+        unsigned long long *count = nullptr;
+        int64_t max_samples = 0;
+        int every = 1;
+        uint32_t threshold = 0;
+        uint64_t seed = 0;
+    };
+    Shadow *sh = nullptr;
     // graphs (one per trace parity)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     // host copies needed by read-back
@@ -181,7 +203,24 @@ Args3 args3(dgh_ctx *c, int cur) {
     return A;
 }
 
-Args2 args2(dgh_ctx *c, int cur, bool update) {
+Args2 args2(dgh_ctx *c, int cur, bool update, bool shadow = false) {
+    if (shadow) {   // same geometry, the shadow chain's order and state; no exterior state written
+        const dgh_ctx::Shadow *h = c->sh;
+        Args2 A = args2(c, cur, update, false);
+        A.q = h->q2;
+        A.res = h->res2;
+        A.tr_in = h->tr2[cur];
+        A.tr_out = update ? h->tr2[cur ^ 1] : h->tr2[cur];
+        A.qb = h->qb2;
+        A.q0 = h->q0_3;
+        A.tin3 = nullptr;
+        A.feat = h->feat;
+        A.rm_out = h->rm;
+        A.cP = h->cP;
+        A.invM = 1.0f / float(h->M);
+        A.P = h->P;
+        return A;
+    }
     Args2 A;
     A.q = c->q2;
     A.res = c->res2;
@@ -191,7 +230,9 @@ Args2 args2(dgh_ctx *c, int cur, bool update) {
     A.conn = c->conn2;
     A.qb = c->qb2;
     A.q0 = c->q0_3;
-    A.tin3 = update ? c->tin3[cur ^ 1] : c->tin3[cur];
+    A.tin3 = c->cl_on ? nullptr : (update ? c->tin3[cur ^ 1] : c->tin3[cur]);   // the closure writes it instead
+    A.feat = c->cl_on ? c->cl_feat : nullptr;
+    A.rm_out = c->cl_on ? c->cl_rm : (c->sh ? c->sh->rm_main : nullptr);
     A.trb = c->trb;
     A.tri_face = c->tri_face;
     A.tri_bface = c->tri_bface;
@@ -205,7 +246,25 @@ Args2 args2(dgh_ctx *c, int cur, bool update) {
     return A;
 }
 
-Args1 args1(dgh_ctx *c, int cur, bool update) {
+Args1 args1(dgh_ctx *c, int cur, bool update, bool shadow = false) {
+    if (shadow) {
+        const dgh_ctx::Shadow *h = c->sh;
+        Args1 A = args1(c, cur, update, false);
+        A.q = h->q1;
+        A.res = h->res1;
+        A.tr_in = h->tr1[cur];
+        A.tr_out = update ? h->tr1[cur ^ 1] : h->tr1[cur];
+        A.qb = h->qb1;
+        A.q0 = h->q0_2;
+        A.qb2 = h->qb2;
+        A.tr2 = update ? h->tr2[cur ^ 1] : h->tr2[cur];
+        A.H1 = h->H1;
+        A.H2 = h->H2;
+        A.cP = h->cP;
+        A.invM = 1.0f / float(h->M);
+        A.P = h->P;
+        return A;
+    }
     Args1 A;
     A.q = c->q1;
     A.res = c->res1;
@@ -314,56 +373,88 @@ struct Launch3 {
 
 template <int N>
 struct Launch2 {
-    static int run(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st = nullptr) {
+    static int run(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st = nullptr, bool shadow = false) {
         if (!st) st = c->stream;
-        if (c->T == 0) return DGH_OK;
+        if (c->T == 0 || (!shadow && c->P == 0)) return DGH_OK;
         StageCoef sc;
         sc.a = float(kRkA[stage]);
         sc.b = float(kRkB[stage]);
         sc.dt = float(c->dt);
         sc.c_dt = 0.0;
         sc.time = c->d_time;
-        Args2 A = args2(c, cur, update);
+        Args2 A = args2(c, cur, update, shadow);
+        const int grid = shadow ? c->sh->grid2 : c->grid2, tile = shadow ? c->sh->tile2 : c->tile2;
+        const size_t smem = shadow ? c->sh->smem2 : c->smem2;
         if (update)
-            k2d_stage<N, true><<<c->grid2, 256, c->smem2, st>>>(A, sc, c->tile2);
+            k2d_stage<N, true><<<grid, 256, smem, st>>>(A, sc, tile);
         else
-            k2d_stage<N, false><<<c->grid2, 256, c->smem2, st>>>(A, sc, c->tile2);
+            k2d_stage<N, false><<<grid, 256, smem, st>>>(A, sc, tile);
+        if (!shadow && c->cl_on) {   // learned closure: exterior state 2 (r^- + MLP(features))
+            const int64_t rows = c->T * c->Np2;
+            const int blocks = (int)std::min<int64_t>((rows + 255) / 256, int64_t(4) * c->sms);
+            k_closure_apply<<<blocks, 256, 0, st>>>(c->cl_w, c->cl_feat, c->cl_rm, rows, c->Np2, c->tri_face,
+                                                    update ? c->tin3[cur ^ 1] : c->tin3[cur], nullptr);
+        }
         return DGH_OK;
     }
 };
 
 template <int N>
 struct Launch1 {
-    static int run(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st = nullptr) {
+    static int run(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st = nullptr, bool shadow = false) {
         if (!st) st = c->stream;
-        if (c->L == 0) return DGH_OK;
+        if (c->L == 0 || (!shadow && c->P == 0)) return DGH_OK;
         StageCoef sc;
         sc.a = float(kRkA[stage]);
         sc.b = float(kRkB[stage]);
         sc.dt = float(c->dt);
         sc.c_dt = 0.0;
         sc.time = c->d_time;
-        Args1 A = args1(c, cur, update);
+        Args1 A = args1(c, cur, update, shadow);
+        const int grid = shadow ? c->sh->grid1 : c->grid1, tile = shadow ? c->sh->tile1 : c->tile1;
+        const size_t smem = shadow ? c->sh->smem1 : c->smem1;
         if (update)
-            k1d_stage<N, true><<<c->grid1, 256, c->smem1, st>>>(A, sc, c->tile1);
+            k1d_stage<N, true><<<grid, 256, smem, st>>>(A, sc, tile);
         else
-            k1d_stage<N, false><<<c->grid1, 256, c->smem1, st>>>(A, sc, c->tile1);
+            k1d_stage<N, false><<<grid, 256, smem, st>>>(A, sc, tile);
         return DGH_OK;
     }
 };
 
-void launch0(dgh_ctx *c, int cur_traces, cudaStream_t st = nullptr) {
+void launch0(dgh_ctx *c, int cur_traces, cudaStream_t st = nullptr, bool shadow = false) {
     if (!st) st = c->stream;
-    if (c->C == 0) return;
+    if (c->C == 0 || (!shadow && c->P == 0)) return;
     Args0 A;
-    A.tr1 = c->tr1[cur_traces];
-    A.qb1 = c->qb1;
+    A.tr1 = shadow ? c->sh->tr1[cur_traces] : c->tr1[cur_traces];
+    A.qb1 = shadow ? c->sh->qb1 : c->qb1;
     A.corner = c->corner;
     A.cornerZ = c->cornerZ;
-    A.Hc = c->Hc;
-    A.P = c->P;
+    A.Hc = shadow ? c->sh->Hc : c->Hc;
+    A.P = shadow ? c->sh->P : c->P;
     A.C = c->C;
-    k0d_stage<<<c->C, 128, c->smem0, st>>>(A);
+    k0d_stage<<<c->C, 128, shadow ? c->sh->smem0 : c->smem0, st>>>(A);
+}
+
+// The shadow chain of one stage (2D, 1D, 0D of the shadow order; no
+// exterior state) and, after stage 0, the sample recorder.  part 1 is the
+// 2D kernel (it reads the 3D boundary traces, so it must finish before the
+// next 3D launch of the boundary cells), part 2 the rest.
+int launch_shadow(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st, int part = 0) {
+    if (!c->sh) return DGH_OK;
+    int rc = DGH_OK;
+    if (part != 2 && (rc = dispatchN<Launch2>(c->N, c, cur, stage, update, st, true))) return rc;
+    if (part == 1) return DGH_OK;
+    rc = dispatchN<Launch1>(c->N, c, cur, stage, update, st, true);
+    if (rc) return rc;
+    launch0(c, update ? cur ^ 1 : cur, st, true);
+    if (update && stage == 0 && c->T > 0) {
+        dgh_ctx::Shadow *h = c->sh;
+        const int64_t rows = c->T * c->Np2;
+        const int blocks = (int)std::min<int64_t>((rows + 255) / 256, int64_t(4) * c->sms);
+        k_record_samples<<<blocks, 256, 0, st>>>(h->feat, h->rm, h->rm_main, rows, c->d_step, h->every, h->threshold,
+                                                 h->seed, h->samples, h->count, h->max_samples);
+    }
+    return DGH_OK;
 }
 
 template <int N>
@@ -443,6 +534,7 @@ int run_closure(dgh_ctx *c) {
     rc = dispatchN<Launch1>(c->N, c, cur, 0, false);
     if (rc) return rc;
     launch0(c, cur);
+    if ((rc = launch_shadow(c, cur, 0, false, c->stream))) return rc;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         c->err = std::string("closure launch: ") + cudaGetErrorString(e);
@@ -476,10 +568,12 @@ int enqueue_step(dgh_ctx *c, int cur, bool overlap, cudaStream_t ms = nullptr) {
         }
         rc = dispatchN<Launch2>(c->N, c, cur, s, true, ss);
         if (rc) return rc;
+        if ((rc = launch_shadow(c, cur, s, true, ss, 1))) return rc;
         if (overlap) cudaEventRecord(c->ev2d[s], ss);
         rc = dispatchN<Launch1>(c->N, c, cur, s, true, ss);
         if (rc) return rc;
         launch0(c, cur ^ 1, ss);
+        if ((rc = launch_shadow(c, cur, s, true, ss, 2))) return rc;
         cur ^= 1;
     }
     k_advance_time<<<1, 1, 0, ms>>>(c->d_time, c->d_step, c->dt);
@@ -585,6 +679,7 @@ void dgh_destroy(dgh_ctx *ctx) {
     if (ctx->evjoin) cudaEventDestroy(ctx->evjoin);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     for (auto &b : ctx->bufs) cudaFree(b.p);
+    delete ctx->sh;
     delete ctx;
 }
 
@@ -1112,6 +1207,14 @@ int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp
         if (lv == 3) n = size_t(ctx->K32) * 32 * 4 * ctx->Np;
         CK(cudaMemsetAsync(level_ptr(ctx, lv, false), 0, n * sizeof(float), ctx->stream));
         CK(cudaMemsetAsync(level_ptr(ctx, lv, true), 0, n * sizeof(float), ctx->stream));
+    }
+    if (ctx->sh) {   // shadow chain restarts at zero with the fields
+        dgh_ctx::Shadow *h = ctx->sh;
+        const size_t n2 = size_t(ctx->T) * h->P * 3 * ctx->Np2, n1 = size_t(ctx->L) * h->P * h->P * 2 * ctx->Np1;
+        CK(cudaMemsetAsync(h->q2, 0, std::max<size_t>(n2, 1) * sizeof(float), ctx->stream));
+        CK(cudaMemsetAsync(h->res2, 0, std::max<size_t>(n2, 1) * sizeof(float), ctx->stream));
+        CK(cudaMemsetAsync(h->q1, 0, std::max<size_t>(n1, 1) * sizeof(float), ctx->stream));
+        CK(cudaMemsetAsync(h->res1, 0, std::max<size_t>(n1, 1) * sizeof(float), ctx->stream));
     }
     const int64_t total = ctx->K32 * 32 * ctx->Np;
     const int blocks = int((total + 255) / 256);
@@ -1734,6 +1837,10 @@ int dgh_batch_create(dgh_ctx *const *problems, int count, dgh_batch **out) {
             g_create_error = "all problems must live on the current device";
             return DGH_EINVAL;
         }
+        if (problems[i]->cl_on || problems[i]->sh) {
+            g_create_error = "a learned closure or sample recording is not supported in a batch";
+            return DGH_EUNSUPPORTED;
+        }
         np[i] = {problems[i]->N, problems[i]->P * 8 + problems[i]->precision};
     }
     int ng = 0;
@@ -2008,6 +2115,290 @@ int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after)
     b->step_count = sc0;
     for (size_t i = 0; i < b->groups.size(); ++i) b->groups[i]->step_count = gsc[i];
     return rc;
+}
+
+
+// ---------------------------------------------------------------- learned closure
+int dgh_closure_set_weights(dgh_ctx *ctx, const float *w, size_t n) {
+    if (!ctx) return DGH_EINVAL;
+    if (!w) {   // disable
+        ctx->cl_on = false;
+        ctx->dirty = true;
+        drop_graphs(ctx);
+        return DGH_OK;
+    }
+    if (n != size_t(MLP_NPARAM)) {
+        ctx->err = "closure weights: expected " + std::to_string(MLP_NPARAM) + " values";
+        return DGH_EINVAL;
+    }
+    if (ctx->P < 1 || ctx->T == 0) {
+        ctx->err = "closure needs HABC faces (P >= 1)";
+        return DGH_EINVAL;
+    }
+    std::vector<float> wb(n);   // BF16 weights (FP32 arithmetic)
+    for (size_t i = 0; i < n; ++i) wb[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+    int rc = DGH_OK;
+    if (!ctx->cl_w && ((rc = dalloc(ctx, ctx->cl_w, n)) || (rc = dalloc(ctx, ctx->cl_feat, size_t(ctx->T) * ctx->Np2 * MLP_IN)) ||
+                       (rc = dalloc(ctx, ctx->cl_rm, size_t(ctx->T) * ctx->Np2))))
+        return rc;
+    CK(cudaMemcpy(ctx->cl_w, wb.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    ctx->cl_on = true;
+    ctx->dirty = true;   // the exterior state is rebuilt with the closure before the next step
+    drop_graphs(ctx);
+    return DGH_OK;
+}
+
+int dgh_closure_record(dgh_ctx *ctx, int shadow_order, int every, double fraction, int64_t max_samples, uint64_t seed) {
+    if (!ctx) return DGH_EINVAL;
+    if (ctx->sh) {
+        ctx->err = "recording is already enabled on this context";
+        return DGH_ESTATE;
+    }
+    if (shadow_order < 1 || shadow_order > MAXP || every < 1 || !(fraction > 0.0 && fraction <= 1.0) || max_samples < 1) {
+        ctx->err = "record: shadow order 1..8, every >= 1, 0 < fraction <= 1, max_samples >= 1";
+        return DGH_EINVAL;
+    }
+    if (ctx->P < 1 || ctx->T == 0) {
+        ctx->err = "record needs HABC faces (P >= 1)";
+        return DGH_EINVAL;
+    }
+    auto *h = new dgh_ctx::Shadow();
+    ctx->sh = h;
+    h->P = shadow_order;
+    std::string err;
+    if (!build_habc(h->P, h->habc, err)) {
+        ctx->err = err;
+        return DGH_EINVAL;
+    }
+    h->M = h->habc.M;
+    const int P = h->P, N = ctx->N, Np2 = ctx->Np2, Np1 = ctx->Np1;
+    const int64_t T = ctx->T, L = ctx->L;
+    std::vector<float> cP(static_cast<size_t>(P));
+    for (int a = 0; a < P; ++a) cP[a] = float(h->habc.c[a]);
+    int rc;
+    if ((rc = dalloc(ctx, h->q2, size_t(T) * P * 3 * Np2)) || (rc = dalloc(ctx, h->res2, size_t(T) * P * 3 * Np2)) ||
+        (rc = dalloc(ctx, h->tr2[0], size_t(T) * P * 3 * 2 * (N + 1))) || (rc = dalloc(ctx, h->tr2[1], size_t(T) * P * 3 * 2 * (N + 1))) ||
+        (rc = dalloc(ctx, h->qb2, size_t(T) * 3 * P * (N + 1))) || (rc = dalloc(ctx, h->q0_3, size_t(T) * Np2)) ||
+        (rc = dalloc(ctx, h->q1, size_t(L) * P * P * 2 * Np1)) || (rc = dalloc(ctx, h->res1, size_t(L) * P * P * 2 * Np1)) ||
+        (rc = dalloc(ctx, h->tr1[0], size_t(L) * P * P * 4)) || (rc = dalloc(ctx, h->tr1[1], size_t(L) * P * P * 4)) ||
+        (rc = dalloc(ctx, h->qb1, size_t(L) * 2 * P * P)) || (rc = dalloc(ctx, h->q0_2, size_t(L) * 2 * P * Np1)) ||
+        (rc = upload(ctx, h->H1, to_f(h->habc.H1))) || (rc = upload(ctx, h->H2, to_f(h->habc.H2))) ||
+        (rc = upload(ctx, h->Hc, to_f(h->habc.Hc))) || (rc = upload(ctx, h->cP, cP)) ||
+        (rc = dalloc(ctx, h->feat, size_t(T) * Np2 * MLP_IN)) || (rc = dalloc(ctx, h->rm, size_t(T) * Np2)) ||
+        (rc = dalloc(ctx, h->rm_main, size_t(T) * Np2)) || (rc = dalloc(ctx, h->samples, size_t(max_samples) * SAMPLE_W)) ||
+        (rc = dalloc(ctx, h->count, 1)))
+        return rc;
+    h->max_samples = max_samples;
+    h->every = every;
+    h->threshold = fraction >= 1.0 ? 0xFFFFFFFFu : uint32_t(fraction * 4294967296.0);
+    h->seed = seed;
+    h->tile2 = std::max(1, 256 / std::max(1, P * Np2));
+    h->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
+    h->smem2 = k2d_smem(N, P, h->tile2);
+    h->smem1 = k1d_smem(N, P, h->tile1);
+    h->smem0 = sizeof(float) * 3 * P * P;
+    if ((int64_t)h->smem2 > ctx->smem_optin || (int64_t)h->smem1 > ctx->smem_optin) {
+        ctx->err = "shadow chain tile does not fit in shared memory";
+        return DGH_EUNSUPPORTED;
+    }
+    h->grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((T + h->tile2 - 1) / h->tile2, int64_t(8) * ctx->sms));
+    h->grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((L + h->tile1 - 1) / h->tile1, int64_t(8) * ctx->sms));
+    ctx->dirty = true;
+    drop_graphs(ctx);
+    return DGH_OK;
+}
+
+int dgh_closure_samples(dgh_ctx *ctx, float *out, int64_t max_rows, int64_t *count) {
+    if (!ctx || !count || (!out && max_rows > 0)) return DGH_EINVAL;
+    if (!ctx->sh) {
+        ctx->err = "recording is not enabled on this context";
+        return DGH_ESTATE;
+    }
+    unsigned long long c = 0;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(&c, ctx->sh->count, sizeof(c), cudaMemcpyDeviceToHost));
+    const int64_t have = std::min<int64_t>((int64_t)c, ctx->sh->max_samples);
+    *count = have;
+    const int64_t rows = std::min<int64_t>(have, max_rows);
+    if (rows > 0) CK(cudaMemcpy(out, ctx->sh->samples, size_t(rows) * SAMPLE_W * sizeof(float), cudaMemcpyDeviceToHost));
+    return DGH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// scoped device buffers of the context-free MLP calls
+struct DevScratch {
+    std::vector<void *> ptrs;
+    ~DevScratch() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+};
+
+int mlp_fail(const std::string &msg, int rc) {
+    g_create_error = msg;
+    return rc;
+}
+
+// loss and gradient on the device: rows idx (or 0..n-1), weights already on the device
+int mlp_loss_grad_dev(const float *dw, const float *dX, const float *dY, const int64_t *didx, int64_t n, float *dpart,
+                      int nblocks, float *dgrad, double *dloss) {
+    k_mlp_grad<<<nblocks, MLP_BS, mlp_grad_smem()>>>(dw, dX, dY, didx, n, 1.0 / double(n), dpart);
+    k_mlp_reduce<<<(MLP_NPARAM + 1 + 255) / 256, 256>>>(dpart, nblocks, dgrad, dloss);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DGH_OK : mlp_fail(std::string("mlp kernels: ") + cudaGetErrorString(e), DGH_ECUDA);
+}
+
+int mlp_setup(int &sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_grad_smem()) != cudaSuccess)
+        return mlp_fail("mlp: shared memory attribute", DGH_ECUDA);
+    return DGH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgh_closure_eval(const float *w, const float *X, int64_t n, float *y) {
+    if (!w || (n > 0 && (!X || !y)) || n < 0) return mlp_fail("closure eval: invalid arguments", DGH_EINVAL);
+    if (n == 0) return DGH_OK;
+    std::vector<float> wb(MLP_NPARAM);
+    for (int i = 0; i < MLP_NPARAM; ++i) wb[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+    DevScratch d;
+    float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dy = d.get<float>(size_t(n));
+    if (!dw || !dX || !dy) return mlp_fail("closure eval: device allocation failed", DGH_ENOMEM);
+    cudaMemcpy(dw, wb.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_closure_apply<<<blocks, 256>>>(dw, dX, nullptr, n, 1, nullptr, nullptr, dy);
+    cudaError_t e = cudaMemcpy(y, dy, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mlp_fail(std::string("closure eval: ") + cudaGetErrorString(e), DGH_ECUDA);
+    return DGH_OK;
+}
+
+int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n, double *loss, float *grad) {
+    if (!w || !X || !Y || n < 1 || !loss || !grad) return mlp_fail("mlp loss/grad: invalid arguments", DGH_EINVAL);
+    int sms = 1, rc = mlp_setup(sms);
+    if (rc) return rc;
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
+    DevScratch d;
+    float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dY = d.get<float>(size_t(n));
+    float *dpart = d.get<float>(size_t(nblocks) * (MLP_NPARAM + 1)), *dg = d.get<float>(MLP_NPARAM);
+    double *dl = d.get<double>(1);
+    if (!dw || !dX || !dY || !dpart || !dg || !dl) return mlp_fail("mlp loss/grad: device allocation failed", DGH_ENOMEM);
+    cudaMemcpy(dw, w, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(dY, Y, size_t(n) * sizeof(float), cudaMemcpyHostToDevice);
+    if ((rc = mlp_loss_grad_dev(dw, dX, dY, nullptr, n, dpart, nblocks, dg, dl))) return rc;
+    cudaMemcpy(grad, dg, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(loss, dl, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mlp_fail(std::string("mlp loss/grad: ") + cudaGetErrorString(e), DGH_ECUDA);
+    return DGH_OK;
+}
+
+int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
+                  double *final_mse) {
+    if (!X || !Y || n < 2 || !cfg || !w_out || cfg->steps < 0 || cfg->batch < 1 || !(cfg->lr > 0.f))
+        return mlp_fail("mlp train: invalid arguments", DGH_EINVAL);
+    int sms = 1, rc = mlp_setup(sms);
+    if (rc) return rc;
+    // standardise inputs and target (folded back into the weights at the end)
+    double mu[MLP_IN + 1] = {0}, sd[MLP_IN + 1] = {0};
+    for (int64_t r = 0; r < n; ++r) {
+        for (int i = 0; i < MLP_IN; ++i) mu[i] += X[r * MLP_IN + i];
+        mu[MLP_IN] += Y[r];
+    }
+    for (int i = 0; i <= MLP_IN; ++i) mu[i] /= double(n);
+    for (int64_t r = 0; r < n; ++r) {
+        for (int i = 0; i < MLP_IN; ++i) sd[i] += (X[r * MLP_IN + i] - mu[i]) * (X[r * MLP_IN + i] - mu[i]);
+        sd[MLP_IN] += (Y[r] - mu[MLP_IN]) * (Y[r] - mu[MLP_IN]);
+    }
+    for (int i = 0; i <= MLP_IN; ++i) sd[i] = std::sqrt(sd[i] / double(n)) > 1e-30 ? std::sqrt(sd[i] / double(n)) : 1.0;
+    std::vector<float> Xn(static_cast<size_t>(n) * MLP_IN), Yn(static_cast<size_t>(n));
+    for (int64_t r = 0; r < n; ++r) {
+        for (int i = 0; i < MLP_IN; ++i) Xn[r * MLP_IN + i] = float((X[r * MLP_IN + i] - mu[i]) / sd[i]);
+        Yn[r] = float((Y[r] - mu[MLP_IN]) / sd[MLP_IN]);
+    }
+    // Glorot-uniform initial weights (splitmix64 stream), zero biases
+    std::vector<float> w(MLP_NPARAM, 0.f);
+    uint64_t st = cfg->seed;
+    auto uni = [&]() {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return double(z >> 11) / double(1ull << 53);
+    };
+    auto glorot = [&](int off, int fan_in, int fan_out, int count) {
+        const double a = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int i = 0; i < count; ++i) w[off + i] = float((2.0 * uni() - 1.0) * a);
+    };
+    glorot(MLP_OW1, MLP_IN, MLP_H, MLP_H * MLP_IN);
+    glorot(MLP_OW2, MLP_H, MLP_H, MLP_H * MLP_H);
+    glorot(MLP_OW3, MLP_H, 1, MLP_H);
+    const int64_t bs = std::min<int64_t>(cfg->batch, n);
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((bs + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
+    DevScratch d;
+    float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dY = d.get<float>(size_t(n));
+    float *dm = d.get<float>(MLP_NPARAM), *dv = d.get<float>(MLP_NPARAM), *dg = d.get<float>(MLP_NPARAM);
+    float *dpart = d.get<float>(size_t(2 * sms) * (MLP_NPARAM + 1));
+    int64_t *didx = d.get<int64_t>(size_t(bs));
+    double *dl = d.get<double>(size_t(std::max<int64_t>(cfg->steps, 1)) + 1);
+    if (!dw || !dX || !dY || !dm || !dv || !dg || !dpart || !didx || !dl)
+        return mlp_fail("mlp train: device allocation failed", DGH_ENOMEM);
+    cudaMemcpy(dw, w.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(dX, Xn.data(), Xn.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(dY, Yn.data(), Yn.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemset(dm, 0, MLP_NPARAM * sizeof(float));
+    cudaMemset(dv, 0, MLP_NPARAM * sizeof(float));
+    const float b1 = cfg->beta1 > 0.f ? cfg->beta1 : 0.9f, b2 = cfg->beta2 > 0.f ? cfg->beta2 : 0.999f;
+    const float eps = cfg->eps > 0.f ? cfg->eps : 1e-8f;
+    double pb1 = 1.0, pb2 = 1.0;
+    for (int64_t it = 0; it < cfg->steps; ++it) {
+        k_batch_indices<<<(int)((bs + 255) / 256), 256>>>(didx, bs, n, cfg->seed * 0x100000001B3ull + uint64_t(it));
+        if ((rc = mlp_loss_grad_dev(dw, dX, dY, didx, bs, dpart, nblocks, dg, dl + it))) return rc;
+        pb1 *= b1;
+        pb2 *= b2;
+        k_adam<<<(MLP_NPARAM + 255) / 256, 256>>>(dw, dg, dm, dv, MLP_NPARAM, cfg->lr, b1, b2, eps, float(1.0 - pb1),
+                                                  float(1.0 - pb2));
+    }
+    // final loss on all rows (normalised units)
+    const int nbf = (int)std::max<int64_t>(1, std::min<int64_t>((n + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
+    if ((rc = mlp_loss_grad_dev(dw, dX, dY, nullptr, n, dpart, nbf, dg, dl + cfg->steps))) return rc;
+    std::vector<double> hist(size_t(cfg->steps) + 1);
+    cudaMemcpy(w.data(), dw, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(hist.data(), dl, hist.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mlp_fail(std::string("mlp train: ") + cudaGetErrorString(e), DGH_ECUDA);
+    // losses are 0.5 * mean squared error of the standardised target
+    if (loss_hist)
+        for (int64_t it = 0; it < cfg->steps; ++it) loss_hist[it] = 2.0 * hist[size_t(it)] * sd[MLP_IN] * sd[MLP_IN];
+    if (final_mse) *final_mse = 2.0 * hist[size_t(cfg->steps)] * sd[MLP_IN] * sd[MLP_IN];
+    // fold the standardisation into the weights: raw features in, raw target out
+    for (int j = 0; j < MLP_H; ++j) {
+        double b = w[MLP_OB1 + j];
+        for (int i = 0; i < MLP_IN; ++i) {
+            const double wi = w[MLP_OW1 + j * MLP_IN + i] / sd[i];
+            b -= wi * mu[i];
+            w_out[MLP_OW1 + j * MLP_IN + i] = float(wi);
+        }
+        w_out[MLP_OB1 + j] = float(b);
+    }
+    for (int i = MLP_OW2; i < MLP_OW3; ++i) w_out[i] = w[i];
+    for (int j = 0; j < MLP_H; ++j) w_out[MLP_OW3 + j] = float(w[MLP_OW3 + j] * sd[MLP_IN]);
+    w_out[MLP_OB3] = float(w[MLP_OB3] * sd[MLP_IN] + mu[MLP_IN]);
+    return DGH_OK;
 }
 
 }  // extern "C"

@@ -56,7 +56,9 @@ struct Args2 {
     const int *conn;        // >=0: (t'*3+e')<<1 | flip ; -1: HABC edge (qb2) ; -2: Dirichlet edge
     const float *qb;        // [T][3][P][Nfp2]  incoming 2D characteristic at domain-edge nodes
     float *q0;              // [T][Np2]         r^- + r^+ of the 3D field at the triangle nodes
-    float *tin3;            // out: 3D incoming traces [K32][4][2][Nfp][32], exterior state (2 r^-, 0)
+    float *tin3;            // out: 3D incoming traces [K32][4][2][Nfp][32], exterior state (2 r^-, 0); NULL: not written
+    float *feat;            // out (optional): closure features per triangle node [T][Np2][6]
+    float *rm_out;          // out (optional): r^- per triangle node [T][Np2]
     const float *trb;       // own 3D traces of the boundary faces [Fb][2][Nfp]
     const int *tri_face;    // [T] global face id k*4+f of the owning tet face
     const int *tri_bface;   // [T] boundary face index
@@ -109,6 +111,7 @@ __device__ __forceinline__ double ricker_integral_d(double t, double f, double t
 }  // namespace dgh
 #include "k3d.cuh"
 #include "k3d_tc.cuh"
+#include "closure.cuh"
 namespace dgh {
 
 // ==================================================================== 2D
@@ -127,7 +130,8 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
     float *sg = sx + tile_tris * P * 2 * NE;          // tile*GEO2
     float *s0 = sg + tile_tris * GEO2;                // tile*NP2 q0
     float *sn = s0 + tile_tris * NP2;                 // tile*P*3*NP2 new (p*, v1, v2)
-    int *sfm = reinterpret_cast<int *>(sn + tile_tris * P * 3 * NP2);
+    float *sr = sn + tile_tris * P * 3 * NP2;         // tile*P*NP2 dp*/dt of this stage (closure features)
+    int *sfm = reinterpret_cast<int *>(sr + tile_tris * P * NP2);
     const int tid = threadIdx.x, nth = blockDim.x;
     if (UPDATE) {
         for (int i = tid; i < 2 * NP2 * NP2; i += nth) sD[i] = A.D[i];
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
                 rhs[1] = -irho * (g[0] * dpr + g[2] * dps + g[4] * lp[0] + g[10] * lp[1] + g[16] * lp[2]);
                 rhs[2] = -irho * (g[1] * dpr + g[3] * dps + g[5] * lp[0] + g[11] * lp[1] + g[17] * lp[2]);
                 const int64_t base = ((t0 + t) * P + a) * 3 * NP2;
+                sr[(t * P + a) * NP2 + n] = rhs[0];
                 for (int fl = 0; fl < 3; ++fl) {
                     const float rr = sc.a * A.res[base + fl * NP2 + n] + sc.dt * rhs[fl];
                     A.res[base + fl * NP2 + n] = rr;
@@ -233,12 +238,22 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
             float rm = 0.f;
             for (int a = 0; a < P; ++a) rm += A.cP[a] * sq[(t * P + a) * 3 * NP2 + n];
             rm *= A.invM;
-            {
+            if (A.tin3) {
                 const int64_t gf = A.tri_face[tg], kc = gf >> 2;
                 const int fc = (int)(gf & 3);
                 A.tin3[(((kc >> 5) * 4 + fc) * 2 * NP2 + n) * 32 + (kc & 31)] = 2.0f * rm;   // exterior p; n.u = 0
             }
             const float q0 = rm + rp;
+            if (A.rm_out) A.rm_out[tg * NP2 + n] = rm;
+            if (A.feat) {   // (p, n.u, p_1, p_2, dp*_1/dt, dp*_2/dt) at this face node
+                float *f = A.feat + (tg * NP2 + n) * 6;
+                f[0] = tr[n];
+                f[1] = tr[NP2 + n];
+                f[2] = P >= 1 ? sq[(t * P + 0) * 3 * NP2 + n] + q0 : 0.f;
+                f[3] = P >= 2 ? sq[(t * P + 1) * 3 * NP2 + n] + q0 : 0.f;
+                f[4] = (UPDATE && P >= 1) ? sr[(t * P + 0) * NP2 + n] : 0.f;
+                f[5] = (UPDATE && P >= 2) ? sr[(t * P + 1) * NP2 + n] : 0.f;
+            }
             A.q0[tg * NP2 + n] = q0;
             s0[t * NP2 + n] = q0;
         }
@@ -258,7 +273,7 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
 
 inline size_t k2d_smem(int N, int P, int tile) {
     const int NP2 = (N + 1) * (N + 2) / 2, NFP2 = N + 1, NE = 3 * NFP2;
-    return sizeof(float) * (2 * NP2 * NP2 + NE * NP2 + tile * (2 * P * 3 * NP2 + P * NP2 + P * 2 * NE + GEO2 + NP2)) +
+    return sizeof(float) * (2 * NP2 * NP2 + NE * NP2 + tile * (2 * P * 3 * NP2 + 2 * P * NP2 + P * 2 * NE + GEO2 + NP2)) +
            sizeof(int) * NE;
 }
 

@@ -1,0 +1,156 @@
+"""Learned boundary closure: the FP64 MLP reference (pinned by central
+finite differences and a closed-form linear limit), the device training and
+inference kernels against it, the shadow-chain sample recorder and the
+closure in the time step."""
+import numpy as np
+import pytest
+
+import paper_1610_05023_b300 as dgh
+from oracle import closure as C
+from paper_1610_05023_b300 import workloads as W
+
+
+def _weights(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0.0, 1.0, C.NPARAM)
+    W1, b1, W2, b2, w3, b3 = C.unpack(w)
+    w[:C.NH * C.NIN] *= scale / np.sqrt(C.NIN)
+    o = C.NH * C.NIN + C.NH
+    w[o:o + C.NH * C.NH] *= scale / np.sqrt(C.NH)
+    w[o + C.NH * C.NH + C.NH:o + C.NH * C.NH + 2 * C.NH] *= scale / np.sqrt(C.NH)
+    return w
+
+
+def _data(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0.0, 1.0, (n, C.NIN))
+    Y = 0.3 * np.tanh(X[:, 0] - 0.5 * X[:, 1]) + 0.1 * X[:, 2] * X[:, 3] - 0.05 * X[:, 4] + 0.02 * X[:, 5]
+    return X, Y
+
+
+# ---------------------------------------------------------------- CPU pins
+def test_oracle_gradient_matches_central_differences():
+    w = _weights(1)
+    X, Y = _data(2, 40)
+    _, g = C.loss_grad(w, X, Y)
+    o1 = C.NH * C.NIN
+    o2 = o1 + C.NH
+    o3 = o2 + C.NH * C.NH
+    idx = [0, 7, o1 - 1, o1, o1 + 9, o2, o2 + 777, o3 - 1, o3 + 3, o3 + C.NH + 5, C.NPARAM - 1]
+    fd = C.finite_difference_grad(w, X, Y, idx)
+    assert np.allclose(g[idx], fd, rtol=1e-6, atol=1e-10)
+
+
+def test_oracle_forward_linear_limit_and_constant_output():
+    """Small weights: tanh(z) = z + O(z^3), so the network reduces to the
+    affine map b3 + w3.(W2 (W1 x + b1) + b2).  With W2 = b2 = 0 the hidden
+    layer 2 vanishes and the output is b3."""
+    eps = 1e-4
+    w = eps * np.random.default_rng(3).normal(0.0, 1.0, C.NPARAM)   # every weight and bias small
+    w[-1] = 0.3
+    X, _ = _data(4, 8)
+    W1, b1, W2, b2, w3, b3 = C.unpack(w)
+    lin = b3 + (((X @ W1.T + b1) @ W2.T + b2) @ w3)
+    assert np.allclose(C.forward(w, X), lin, rtol=0, atol=1e-10 * max(1.0, abs(b3)))
+    w0 = w.copy()
+    o = C.NH * C.NIN + C.NH
+    w0[o:o + C.NH * C.NH + C.NH] = 0.0
+    assert np.allclose(C.forward(w0, X), b3, atol=0)
+
+
+# ---------------------------------------------------------------- GPU
+@pytest.mark.gpu
+def test_gpu_loss_and_gradient_match_fp64():
+    w = _weights(5).astype(np.float32)
+    X, Y = _data(6, 3000)
+    X, Y = X.astype(np.float32), Y.astype(np.float32)
+    L, g = dgh.mlp_loss_grad(w, X, Y)
+    Lr, gr = C.loss_grad(w.astype(np.float64), X, Y)
+    assert abs(L - Lr) <= 1e-5 * Lr
+    assert np.linalg.norm(g - gr) <= 1e-5 * np.linalg.norm(gr)
+
+
+@pytest.mark.gpu
+def test_gpu_inference_matches_fp64_with_bf16_weights():
+    import torch
+    w = _weights(7).astype(np.float32)
+    X, _ = _data(8, 5000)
+    X = X.astype(np.float32)
+    y = dgh.closure_eval(w, X)
+    wb = torch.tensor(w).to(torch.bfloat16).to(torch.float64).numpy()   # the weights the kernel uses
+    yr = C.forward(wb, X.astype(np.float64))
+    assert np.linalg.norm(y - yr) <= 1e-5 * np.linalg.norm(yr)
+    y64 = C.forward(w.astype(np.float64), X.astype(np.float64))
+    assert np.linalg.norm(y - y64) <= 1e-2 * np.linalg.norm(y64)   # BF16 weight rounding
+
+
+@pytest.mark.gpu
+def test_gpu_training_fits_smooth_target():
+    X, Y = _data(9, 20000)
+    w, hist, mse = dgh.mlp_train(X, Y, steps=1500, batch=2048, lr=2e-3, seed=3)
+    var = float(np.var(Y))
+    assert mse < 0.05 * var, (mse, var)
+    assert np.mean(hist[-100:]) < 0.2 * np.mean(hist[:20])
+    # the returned weights take raw features (standardisation folded in)
+    yr = C.forward(w.astype(np.float64), X)
+    assert abs(np.mean((yr - Y) ** 2) - mse) <= 1e-3 * var + 0.05 * mse
+
+
+def _solver(P, seed=50):
+    VX, EToV = W.kuhn_mesh(3, 1.0, 0.02, seed=seed)
+    g = dgh.Solver(VX, EToV, 3, P)
+    g.init_gaussian([0.3, 0.2, -0.1], 0.3)
+    return g
+
+
+@pytest.mark.gpu
+def test_recorder_shadow_equal_order_gives_zero_targets():
+    """A shadow chain of the context's own order reproduces its r^- exactly:
+    every recorded target is 0; features are the chain's own values."""
+    g = _solver(2)
+    g.closure_record(shadow_order=2, every=1, fraction=1.0, max_samples=1 << 20, seed=1)
+    g.init_gaussian([0.3, 0.2, -0.1], 0.3)
+    g.step(30)
+    S = g.closure_samples()
+    T, Np2 = g.info["n_tris"], g.info["Np2"]
+    assert S.shape == (30 * T * Np2, 7)
+    assert np.all(S[:, 6] == 0.0)
+    assert np.all(np.isfinite(S)) and np.abs(S[:, 0]).max() > 0
+
+
+@pytest.mark.gpu
+def test_recorder_lower_order_shadow_and_sampling():
+    g = _solver(6)
+    g.closure_record(shadow_order=2, every=5, fraction=0.25, max_samples=1 << 20, seed=2)
+    g.init_gaussian([0.3, 0.2, -0.1], 0.3)
+    g.step(60)
+    S = g.closure_samples()
+    T, Np2 = g.info["n_tris"], g.info["Np2"]
+    rows = T * Np2 * 12          # steps 0, 5, ..., 55
+    assert 0.2 * rows < S.shape[0] < 0.3 * rows
+    assert np.abs(S[:, 6]).max() > 0          # orders 6 and 2 differ once the wave is at the faces
+    base = dgh.Solver(*W.kuhn_mesh(3, 1.0, 0.02, seed=50), 3, 6)
+    base.init_gaussian([0.3, 0.2, -0.1], 0.3)
+    base.step(60)
+    assert np.array_equal(base.get_state(3), g.get_state(3))   # the shadow never feeds back
+
+
+@pytest.mark.gpu
+def test_closure_zero_output_is_bit_identical_and_output_changes_solution():
+    w = _weights(11).astype(np.float32)
+    o3 = C.NPARAM - C.NH - 1
+    w[o3:] = 0.0                       # w3 = 0, b3 = 0: MLP == 0
+    a, b = _solver(2), _solver(2)
+    b.closure_set_weights(w)
+    a.step(25)
+    b.step(25)
+    for lv in (3, 2, 1):
+        assert np.array_equal(a.get_state(lv), b.get_state(lv))
+    w[-1] = 1e-3                       # constant correction of r^-
+    c = _solver(2)
+    c.closure_set_weights(w)
+    c.step(25)
+    d = np.linalg.norm(c.get_state(3) - a.get_state(3))
+    assert 0 < d < 1e-1 * np.linalg.norm(a.get_state(3))
+    c.closure_set_weights(None)        # disabling restores the plain chain from here on
+    assert np.isfinite(c.energy())
