@@ -297,6 +297,135 @@ def run_precision_form(args):
     print(json.dumps(line), flush=True)
 
 
+CLOSURE_SEED = 5000
+
+
+def _closure_runs(dgh, W, n_runs, n_hex, T, every, fraction, seed):
+    """Training data: n_runs seeded runs (N = 4, HABC P = 8, n_hex^3 x 6 tets,
+    jitter 2% h) with a P = 2 shadow chain recording (features, r^-_8 - r^-_2);
+    each run has a Gaussian pulse (width ~ U[0.08, 0.15]) or a Ricker source
+    (f0 ~ U[2, 6], t_s = 1.25/f0) at x ~ U[-0.6, 0.6]^3.  Yields (run, rows)."""
+    for r in range(n_runs):
+        u = [float(W.hashed_uniform(seed, r, j)[0]) for j in range(6)]
+        x = [(2.0 * u[a] - 1.0) * 0.6 for a in range(3)]
+        VX, EToV = W.kuhn_mesh(n_hex, 1.0, 0.02, seed=seed + r)
+        g = dgh.Solver(VX, EToV, 4, 8)
+        g.closure_record(shadow_order=2, every=every, fraction=fraction, max_samples=1 << 22, seed=seed + r)
+        if u[3] < 0.5:
+            g.init_gaussian(x, 0.08 + 0.07 * u[4])
+        else:
+            f0 = 2.0 + 4.0 * u[4]
+            g.add_point_source(x, f0, 1.25 / f0)
+            g.init_gaussian(x, 0.1, 0.0)
+        g.step(int(math.ceil(T / g.info["dt"])))
+        rows = g.closure_samples()
+        g.close()
+        yield r, rows
+
+
+def run_closure_form(args):
+    """Learned closure: record, train, evaluate.  Evaluation on the 40^3 x 6
+    unjittered cube (N = 4, c = rho = 1, Gaussian pulse of width 0.12 at
+    (0.35, -0.25, 0.30), t in [0, 1.5]): plain P = 2, P = 2 with the closure
+    (MLP(x) - MLP(0), and the homogeneous form), plain P = 8, against a
+    large-domain reference whose inner mesh is the same cube (its boundary is
+    too far for reflections to return by t = 1.5).
+    Error(t)^2 = energy of the difference in the cube / initial energy."""
+    import torch
+    import paper_1610_05023_b300 as dgh
+    from paper_1610_05023_b300 import workloads as W
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    n_runs = args.closure_runs
+    per_run, run_of = [], []
+    for r, rows in _closure_runs(dgh, W, n_runs, args.closure_train_n, 2.5, 20, 0.01, CLOSURE_SEED):
+        per_run.append(rows)
+        run_of.append(np.full(rows.shape[0], r))
+    data, run_of = np.concatenate(per_run), np.concatenate(run_of)
+    t1 = time.perf_counter()
+    n_val = max(1, n_runs - int(round(0.9 * n_runs)))   # 90 / 10 split by run (at least one run held out)
+    val = run_of >= n_runs - n_val
+    Xtr, Ytr = data[~val, :6], data[~val, 6]
+    Xva, Yva = data[val, :6], data[val, 6]
+    w, hist, mse_tr = dgh.mlp_train(Xtr, Ytr, steps=args.closure_steps, batch=8192, lr=1e-3, seed=CLOSURE_SEED)
+    loss_va, _ = dgh.mlp_loss_grad(w, Xva, Yva)
+    wh, _, mse_h = dgh.closure_fit_homogeneous(Xtr, Ytr, steps=args.closure_steps, batch=8192, lr=1e-3,
+                                               seed=CLOSURE_SEED)
+    mse_hv = float(np.mean((dgh.closure_eval(wh, Xva) - Yva) ** 2))
+    mse_mv = float(np.mean((dgh.closure_eval(w, Xva) - Yva) ** 2))
+    t2 = time.perf_counter()
+
+    # ---- evaluation
+    n, T, sigma, x0 = args.closure_eval_n, 1.5, 0.12, [0.35, -0.25, 0.30]
+    h = 2.0 / n
+    pad = int(math.ceil((T / 2 + 2 * sigma) / h))
+    VXs, EToVs = W.kuhn_mesh(n, 1.0, 0.0, seed=0)
+    VXl, EToVl = W.kuhn_mesh(n + 2 * pad, 1.0 + pad * h, 0.0, seed=0)
+    cs = VXs[EToVs].mean(axis=1)
+    cl = VXl[EToVl].mean(axis=1)
+    key = lambda c: [tuple(v) for v in np.round(c / (h / 64.0)).astype(np.int64)]
+    where = {k: i for i, k in enumerate(key(cl))}
+    inner = np.array([where[k] for k in key(cs)])
+    ref = dgh.Solver(VXl, EToVl, 4, 0)
+    dt = min(ref.info["dt"], dgh.plan(VXs, EToVs, 4, 8)["dt"])
+    ref.close()
+    nck = 15
+    nst = int(math.ceil(T / dt))
+    nst += (-nst) % nck
+    dt = T / nst
+    arms = {"P2": (2, None), "P2_closure": (2, w), "P2_closure_homogeneous": (2, wh), "P8": (8, None)}
+    solvers = {}
+    for name, (P, wts) in arms.items():
+        g = dgh.Solver(VXs, EToVs, 4, P, dt=dt)
+        if wts is not None:
+            g.closure_set_weights(wts)
+        g.init_gaussian(x0, sigma)
+        solvers[name] = g
+    ref = dgh.Solver(VXl, EToVl, 4, 0, dt=dt)
+    ref.init_gaussian(x0, sigma)
+    scratch = dgh.Solver(VXs, EToVs, 4, 0, dt=dt)
+    scratch.init_gaussian(x0, sigma)
+    E0 = scratch.energy()
+    errs = {k: [] for k in arms}
+    times = []
+    step_ms = {}
+    for ck in range(1, nck + 1):
+        ref.step(nst // nck)
+        qr = ref.get_state(3)[inner]
+        for name, g in solvers.items():
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            g.step(nst // nck)
+            g.sync()
+            step_ms.setdefault(name, []).append((time.perf_counter() - ta) * 1e3 / (nst // nck))
+            scratch.set_state(3, g.get_state(3) - qr)
+            errs[name].append(math.sqrt(max(scratch.energy(), 0.0) / E0))
+        times.append(ck * T / nck)
+    t3 = time.perf_counter()
+    t_hit = (1.0 - max(abs(v) for v in x0) - 2 * sigma)
+    summary = {}
+    for name in arms:
+        after = [e for t, e in zip(times, errs[name]) if t >= t_hit]
+        summary[name] = {"error_max_after_hit": max(after), "error_at_T": errs[name][-1],
+                         "ms_per_step": float(np.median(step_ms[name]))}
+    line = {"form": "closure", "metric": "reflection error (energy norm, relative)",
+            "config": {"train": "%d runs, %d^3 x 6 tets, N = 4, P = 8, shadow P = 2, T = 2.5, every 20 steps, "
+                                "1%% of the face nodes" % (n_runs, args.closure_train_n),
+                       "eval": "%d^3 x 6 tets (unjittered), N = 4, Gaussian width %.2f at %s, T = %.1f, "
+                               "reference %d^3 x 6 tets" % (n, sigma, x0, T, n + 2 * pad), "dt": dt},
+            "samples": {"train": int(Xtr.shape[0]), "val": int(Xva.shape[0])},
+            "training": {"steps": args.closure_steps, "train_mse": mse_tr, "val_mse": 2.0 * loss_va,
+                         "val_mse_of_correction": mse_mv, "val_mse_homogeneous": mse_hv,
+                         "homogeneous_fit_mse_relative_target": mse_h,
+                         "target_var_val": float(np.var(Yva)), "first_batches_mse": float(np.mean(hist[:20])),
+                         "last_batches_mse": float(np.mean(hist[-20:]))},
+            "errors": summary, "times": times, "error_curves": errs,
+            "seconds": {"record": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}
+    print(json.dumps(line), flush=True)
+    if args.closure_weights_out:
+        np.save(args.closure_weights_out, w)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,7 +434,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=48, help="hexes per axis (48 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "batch", "precision"],
+    ap.add_argument("--closure-runs", type=int, default=64)
+    ap.add_argument("--closure-train-n", type=int, default=24)
+    ap.add_argument("--closure-eval-n", type=int, default=40)
+    ap.add_argument("--closure-steps", type=int, default=4000)
+    ap.add_argument("--closure-weights-out", default="", help="save the trained closure weights (.npy)")
+    ap.add_argument("--form", default="plain", choices=["plain", "batch", "precision", "closure"],
                     help="batch: the batching form (48 independent problems); precision: the N = 6 layered "
                          "workload with the FP32 and tensor-core 3D kernels")
     args = ap.parse_args()
@@ -315,6 +449,8 @@ def main():
         return run_batch_form(args)
     if args.form == "precision":
         return run_precision_form(args)
+    if args.form == "closure":
+        return run_closure_form(args)
 
     import torch
     import paper_1610_05023_b300 as dgh

@@ -306,7 +306,8 @@ int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after)
 /* ---------------------------------------------------------------- learned closure
  * A learned correction of the face condition of a low-order HABC chain:
  * the exterior state seen by the 3D flux at a boundary face node becomes
- * 2 (r^- + MLP(x)) instead of 2 r^- (eq. proc:pi00Star, r^- = (1/M) sum c_a p*_a),
+ * 2 (r^- + MLP(x) - MLP(0)) instead of 2 r^- (eq. proc:pi00Star, r^- = (1/M) sum c_a p*_a;
+ * the fields enter linearly, so zero fields give exactly zero correction),
  * with x = (p, n.u, p_1, p_2, dp*_1/dt, dp*_2/dt) at that node: the 3D trace
  * pressure and outward normal velocity, the full auxiliary pressures of sets
  * 1 and 2 (p_a = p*_a + r^- + r^+) and the time derivatives of p*_1, p*_2 of
@@ -317,9 +318,13 @@ int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after)
  * that order).  Inference uses the weights rounded to BF16, FP32 arithmetic. */
 #define DGH_MLP_NPARAM 4673
 
-/* Enables the closure on this context with the given weights (n = 4673), or
- * disables it (w = NULL).  DGH_EINVAL without HABC faces (P = 0).  Not
- * supported inside a batch. */
+/* Enables the closure on this context with the given weights, or disables
+ * it (w = NULL).  n = 4673: correction MLP(x) - MLP(0).  n = 4680: the
+ * homogeneous form sigma_y |x~| MLP(x~ / |x~|) with x~_i = x_i / sigma_i,
+ * the 4673 weights followed by 1/sigma_1..6 and sigma_y (kept FP32); it is of
+ * degree one in the fields, as the linear equations require, and zero at
+ * zero fields.  DGH_EINVAL without HABC faces (P = 0).  Not supported inside
+ * a batch. */
 int dgh_closure_set_weights(dgh_ctx *ctx, const float *w, size_t n);
 
 /* Training data: adds a shadow HABC chain of order shadow_order (its own 2D
@@ -336,8 +341,9 @@ int dgh_closure_record(dgh_ctx *ctx, int shadow_order, int every, double fractio
 int dgh_closure_samples(dgh_ctx *ctx, float *out, int64_t max_rows, int64_t *count);
 
 /* Context-free device calls (current device; errors via dgh_last_error(NULL)).
- * dgh_closure_eval: y[r] = MLP(X[r]) with the inference kernel (BF16-rounded
- * weights), X [n][6] host, y [n] host.
+ * dgh_closure_eval: the correction y[r] of the inference kernel for the
+ * weights w of nw = 4673 or 4680 values (as dgh_closure_set_weights;
+ * BF16-rounded network weights), X [n][6] host, y [n] host.
  * dgh_mlp_loss_grad: FP32 weights w, loss = (1/2n) sum (MLP(X_r) - Y_r)^2 and
  * its gradient with respect to w (host arrays), by the training kernels.
  * dgh_mlp_train: minibatch Adam (Kingma & Ba) on the GPU from seeded
@@ -354,7 +360,7 @@ typedef struct dgh_train_cfg {
     uint64_t seed;        /* initial weights and batches                */
 } dgh_train_cfg;
 
-int dgh_closure_eval(const float *w, const float *X, int64_t n, float *y);
+int dgh_closure_eval(const float *w, size_t nw, const float *X, int64_t n, float *y);
 int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n, double *loss, float *grad);
 int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
                   double *final_mse);

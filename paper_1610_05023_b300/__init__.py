@@ -121,8 +121,9 @@ def load_library(path=LIB_PATH):
                                               ctypes.c_uint64]),
         "dgh_closure_samples": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
                                                ctypes.POINTER(ctypes.c_int64)]),
-        "dgh_closure_eval": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
-                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_float)]),
+        "dgh_closure_eval": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_float)]),
         "dgh_mlp_loss_grad": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                              ctypes.POINTER(ctypes.c_float), ctypes.c_int64, D,
                                              ctypes.POINTER(ctypes.c_float)]),
@@ -158,13 +159,33 @@ def _lib_check(rc):
 
 
 def closure_eval(w, X):
-    """MLP(X) [n] of the device inference kernel (BF16-rounded weights)."""
+    """The correction [n] of the device inference kernel for weights w (4673
+    values: MLP(x) - MLP(0); 4680: the homogeneous form), features X [n][6]."""
     lib = load_library()
-    w = _f32(w, (MLP_NPARAM,))
+    w = _f32(w)
     X = _f32(X)
     y = np.empty(X.shape[0], np.float32)
-    _lib_check(lib.dgh_closure_eval(_fptr(w), _fptr(X), X.shape[0], _fptr(y)))
+    _lib_check(lib.dgh_closure_eval(_fptr(w), w.size, _fptr(X), X.shape[0], _fptr(y)))
     return y
+
+
+def closure_fit_homogeneous(X, Y, **train_kw):
+    """Train the homogeneous closure: per-feature RMS scales sigma, directions
+    u = x~ / |x~| (x~ = x / sigma), relative targets v = y / (sigma_y |x~|);
+    returns the 4680 values for Solver.closure_set_weights (rows with zero
+    features are dropped).  Keyword arguments go to mlp_train."""
+    X = np.asarray(X, np.float64)
+    Y = np.asarray(Y, np.float64)
+    sx = np.sqrt(np.mean(X * X, axis=0))
+    sx[sx <= 0] = 1.0
+    sy = float(np.sqrt(np.mean(Y * Y))) or 1.0
+    Xt = X / sx
+    s = np.linalg.norm(Xt, axis=1)
+    keep = s > 0
+    U = Xt[keep] / s[keep, None]
+    V = Y[keep] / (sy * s[keep])
+    w, hist, mse = mlp_train(U, V, **train_kw)
+    return np.concatenate([w, 1.0 / sx, [sy]]).astype(np.float32), hist, mse
 
 
 def mlp_loss_grad(w, X, Y):
@@ -385,11 +406,12 @@ class Solver:
         self._check(self._lib.dgh_load_state(self._h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
 
     def closure_set_weights(self, w):
-        """Enable the learned closure with MLP weights w (4673), or disable it (None)."""
+        """Enable the learned closure with weights w (4673, or 4680 for the
+        homogeneous form), or disable it (None)."""
         if w is None:
             self._check(self._lib.dgh_closure_set_weights(self._h, None, 0))
             return
-        w = _f32(w, (MLP_NPARAM,))
+        w = _f32(w)
         self._check(self._lib.dgh_closure_set_weights(self._h, _fptr(w), w.size))
 
     def closure_record(self, shadow_order=2, every=1, fraction=1.0, max_samples=1 << 20, seed=0):

@@ -96,7 +96,8 @@ struct dgh_ctx {
     int smem_optin = 0;
     // learned closure (inference on this context's chain)
     bool cl_on = false;
-    float *cl_w = nullptr;            // MLP weights (BF16-rounded, stored FP32) [MLP_NPARAM]
+    bool cl_homog = false;            // homogeneous form: 7 scales follow the weights
+    float *cl_w = nullptr;            // MLP weights (BF16-rounded, stored FP32) [MLP_NPARAM] (+ 7 FP32 scales)
     float *cl_feat = nullptr;         // [T][Np2][6]
     float *cl_rm = nullptr;           // [T][Np2] r^- of this chain
     // shadow chain of another HABC order driven one-way by the 3D traces (sample recording)
@@ -392,7 +393,8 @@ struct Launch2 {
         if (!shadow && c->cl_on) {   // learned closure: exterior state 2 (r^- + MLP(features))
             const int64_t rows = c->T * c->Np2;
             const int blocks = (int)std::min<int64_t>((rows + 255) / 256, int64_t(4) * c->sms);
-            k_closure_apply<<<blocks, 256, 0, st>>>(c->cl_w, c->cl_feat, c->cl_rm, rows, c->Np2, c->tri_face,
+            k_closure_apply<<<blocks, 256, 0, st>>>(c->cl_w, c->cl_homog ? c->cl_w + MLP_NPARAM : nullptr, c->cl_feat,
+                                                    c->cl_rm, rows, c->Np2, c->tri_face,
                                                     update ? c->tin3[cur ^ 1] : c->tin3[cur], nullptr);
         }
         return DGH_OK;
@@ -2127,22 +2129,24 @@ int dgh_closure_set_weights(dgh_ctx *ctx, const float *w, size_t n) {
         drop_graphs(ctx);
         return DGH_OK;
     }
-    if (n != size_t(MLP_NPARAM)) {
-        ctx->err = "closure weights: expected " + std::to_string(MLP_NPARAM) + " values";
+    if (n != size_t(MLP_NPARAM) && n != size_t(MLP_NPARAM + MLP_IN + 1)) {
+        ctx->err = "closure weights: expected " + std::to_string(MLP_NPARAM) + " values (or " +
+                   std::to_string(MLP_NPARAM + MLP_IN + 1) + " for the homogeneous form)";
         return DGH_EINVAL;
     }
     if (ctx->P < 1 || ctx->T == 0) {
         ctx->err = "closure needs HABC faces (P >= 1)";
         return DGH_EINVAL;
     }
-    std::vector<float> wb(n);   // BF16 weights (FP32 arithmetic)
-    for (size_t i = 0; i < n; ++i) wb[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+    std::vector<float> wb(n);   // BF16 weights (FP32 arithmetic); the scales of the homogeneous form stay FP32
+    for (size_t i = 0; i < n; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
     int rc = DGH_OK;
-    if (!ctx->cl_w && ((rc = dalloc(ctx, ctx->cl_w, n)) || (rc = dalloc(ctx, ctx->cl_feat, size_t(ctx->T) * ctx->Np2 * MLP_IN)) ||
+    if (!ctx->cl_w && ((rc = dalloc(ctx, ctx->cl_w, size_t(MLP_NPARAM + MLP_IN + 1))) || (rc = dalloc(ctx, ctx->cl_feat, size_t(ctx->T) * ctx->Np2 * MLP_IN)) ||
                        (rc = dalloc(ctx, ctx->cl_rm, size_t(ctx->T) * ctx->Np2))))
         return rc;
     CK(cudaMemcpy(ctx->cl_w, wb.data(), n * sizeof(float), cudaMemcpyHostToDevice));
     ctx->cl_on = true;
+    ctx->cl_homog = n != size_t(MLP_NPARAM);
     ctx->dirty = true;   // the exterior state is rebuilt with the closure before the next step
     drop_graphs(ctx);
     return DGH_OK;
@@ -2270,18 +2274,20 @@ int mlp_setup(int &sms) {
 
 extern "C" {
 
-int dgh_closure_eval(const float *w, const float *X, int64_t n, float *y) {
-    if (!w || (n > 0 && (!X || !y)) || n < 0) return mlp_fail("closure eval: invalid arguments", DGH_EINVAL);
+int dgh_closure_eval(const float *w, size_t nw, const float *X, int64_t n, float *y) {
+    if (!w || (n > 0 && (!X || !y)) || n < 0 || (nw != size_t(MLP_NPARAM) && nw != size_t(MLP_NPARAM + MLP_IN + 1)))
+        return mlp_fail("closure eval: invalid arguments", DGH_EINVAL);
     if (n == 0) return DGH_OK;
-    std::vector<float> wb(MLP_NPARAM);
-    for (int i = 0; i < MLP_NPARAM; ++i) wb[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+    std::vector<float> wb(nw);
+    for (size_t i = 0; i < nw; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
     DevScratch d;
-    float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dy = d.get<float>(size_t(n));
+    float *dw = d.get<float>(nw), *dX = d.get<float>(size_t(n) * MLP_IN), *dy = d.get<float>(size_t(n));
     if (!dw || !dX || !dy) return mlp_fail("closure eval: device allocation failed", DGH_ENOMEM);
-    cudaMemcpy(dw, wb.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(dw, wb.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    k_closure_apply<<<blocks, 256>>>(dw, dX, nullptr, n, 1, nullptr, nullptr, dy);
+    k_closure_apply<<<blocks, 256>>>(dw, nw == size_t(MLP_NPARAM) ? nullptr : dw + MLP_NPARAM, dX, nullptr, n, 1,
+                                     nullptr, nullptr, dy);
     cudaError_t e = cudaMemcpy(y, dy, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return mlp_fail(std::string("closure eval: ") + cudaGetErrorString(e), DGH_ECUDA);
     return DGH_OK;

@@ -1,6 +1,7 @@
 // Learned boundary closure: a small MLP that corrects the incoming
 // characteristic of a low-order HABC chain,
-//   r^-_used = r^-_P + MLP(p, n.u, p_1, p_2, dp*_1/dt, dp*_2/dt),
+//   r^-_used = r^-_P + MLP(x) - MLP(0),  x = (p, n.u, p_1, p_2, dp*_1/dt, dp*_2/dt),
+// or its homogeneous form sigma_y |x~| MLP(x~ / |x~|), x~ = x / sigma,
 // evaluated per boundary face node; the data pipeline that records training
 // samples from a high-order run with a low-order shadow chain; and the
 // training kernels (forward, backward, gradient reduction, Adam).  The paper
@@ -42,19 +43,53 @@ __device__ __forceinline__ float mlp_forward(const float *w, const float (&x)[ML
     return y;
 }
 
-// Inference: y = MLP(feat) for n feature rows; when tin3 is given, the
-// corrected exterior state 2 (r^- + y) of every boundary face node of the
-// chain goes to the 3D incoming traces (rows = triangle nodes t * NP2 + node).
-__global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const float *feat, const float *rm, int64_t n,
-                                                       int np2, const int *tri_face, float *tin3, float *y_out) {
+// Inference: the correction y = MLP(feat) - MLP(0) for n feature rows (the
+// fields enter linearly, so no fields must give no correction; MLP(0) is
+// evaluated by the same code with the same weights, so y(0) = 0 exactly).
+// When tin3 is given, the corrected exterior state 2 (r^- + y) of every
+// boundary face node of the chain goes to the 3D incoming traces (rows =
+// triangle nodes t * NP2 + node).
+// Homogeneous form (scales != NULL: 1/sigma_i of the 6 features, then
+// sigma_y): x~ = x / sigma, s = |x~|, y = sigma_y s MLP(x~ / s), 0 at s = 0 --
+// the correction is then of degree one in the fields, as the linear wave
+// equation requires, and the network sees only the direction of x.
+__global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const float *scales, const float *feat,
+                                                       const float *rm, int64_t n, int np2, const int *tri_face,
+                                                       float *tin3, float *y_out) {
     __shared__ float sw[MLP_NPARAM];
+    __shared__ float y0, ssc[MLP_IN + 1];
     for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sw[i] = wts[i];
+    if (threadIdx.x <= MLP_IN) ssc[threadIdx.x] = scales ? scales[threadIdx.x] : 1.f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float z[MLP_IN] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        y0 = scales ? 0.f : mlp_forward(sw, z);
+    }
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         float x[MLP_IN];
 #pragma unroll
         for (int i = 0; i < MLP_IN; ++i) x[i] = feat[r * MLP_IN + i];
-        const float y = mlp_forward(sw, x);
+        float y;
+        if (scales) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < MLP_IN; ++i) {
+                x[i] *= ssc[i];
+                s2 += x[i] * x[i];
+            }
+            const float sn = sqrtf(s2);
+            if (sn > 1e-30f) {
+                const float inv = 1.0f / sn;
+#pragma unroll
+                for (int i = 0; i < MLP_IN; ++i) x[i] *= inv;
+                y = ssc[MLP_IN] * sn * mlp_forward(sw, x);
+            } else {
+                y = 0.f;
+            }
+        } else {
+            y = mlp_forward(sw, x) - y0;
+        }
         if (y_out) y_out[r] = y;
         if (tin3) {
             const int64_t t = r / np2;

@@ -76,12 +76,14 @@ def test_gpu_inference_matches_fp64_with_bf16_weights():
     w = _weights(7).astype(np.float32)
     X, _ = _data(8, 5000)
     X = X.astype(np.float32)
-    y = dgh.closure_eval(w, X)
+    y = dgh.closure_eval(w, X)           # the correction MLP(x) - MLP(0)
     wb = torch.tensor(w).to(torch.bfloat16).to(torch.float64).numpy()   # the weights the kernel uses
-    yr = C.forward(wb, X.astype(np.float64))
+    z = np.zeros((1, C.NIN))
+    yr = C.forward(wb, X.astype(np.float64)) - C.forward(wb, z)
     assert np.linalg.norm(y - yr) <= 1e-5 * np.linalg.norm(yr)
-    y64 = C.forward(w.astype(np.float64), X.astype(np.float64))
+    y64 = C.forward(w.astype(np.float64), X.astype(np.float64)) - C.forward(w.astype(np.float64), z)
     assert np.linalg.norm(y - y64) <= 1e-2 * np.linalg.norm(y64)   # BF16 weight rounding
+    assert dgh.closure_eval(w, np.zeros((3, C.NIN)))[0] == 0.0
 
 
 @pytest.mark.gpu
@@ -146,7 +148,12 @@ def test_closure_zero_output_is_bit_identical_and_output_changes_solution():
     b.step(25)
     for lv in (3, 2, 1):
         assert np.array_equal(a.get_state(lv), b.get_state(lv))
-    w[-1] = 1e-3                       # constant correction of r^-
+    c0 = _solver(2)
+    w[-1] = 1e-3                       # a constant output is removed by the MLP(0) subtraction
+    c0.closure_set_weights(w)
+    c0.step(25)
+    assert np.array_equal(c0.get_state(3), a.get_state(3))
+    w[o3:o3 + C.NH] = 1e-3 * np.random.default_rng(12).normal(size=C.NH)   # a field-dependent correction
     c = _solver(2)
     c.closure_set_weights(w)
     c.step(25)
@@ -154,3 +161,23 @@ def test_closure_zero_output_is_bit_identical_and_output_changes_solution():
     assert 0 < d < 1e-1 * np.linalg.norm(a.get_state(3))
     c.closure_set_weights(None)        # disabling restores the plain chain from here on
     assert np.isfinite(c.energy())
+
+
+@pytest.mark.gpu
+def test_homogeneous_form_is_degree_one_and_zero_at_zero():
+    w = _weights(13).astype(np.float32)
+    rng = np.random.default_rng(14)
+    scales = np.concatenate([1.0 / rng.uniform(0.5, 2.0, C.NIN), [0.7]]).astype(np.float32)
+    wh = np.concatenate([w, scales])
+    X, _ = _data(15, 200)
+    y1 = dgh.closure_eval(wh, X)
+    y3 = dgh.closure_eval(wh, 3.0 * X)
+    assert np.allclose(y3, 3.0 * y1, rtol=1e-5, atol=1e-7)
+    assert np.all(dgh.closure_eval(wh, np.zeros((4, C.NIN))) == 0.0)
+    # against FP64: sigma_y |x~| MLP(x~ / |x~|) with the BF16-rounded weights
+    import torch
+    wb = torch.tensor(w).to(torch.bfloat16).to(torch.float64).numpy()
+    Xt = X * scales[:C.NIN].astype(np.float64)
+    s = np.linalg.norm(Xt, axis=1)
+    yr = scales[C.NIN] * s * C.forward(wb, Xt / s[:, None])
+    assert np.linalg.norm(y1 - yr) <= 1e-5 * np.linalg.norm(yr)
