@@ -243,27 +243,46 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
         }
         __syncthreads();
         // ---------------- volume term for the chunk of warp w
-        float div[CP], dr[CP], ds[CP], dt[CP];
+        // Output nodes in pairs: packed FP32x2 FMAs (each half an ordinary
+        // round-to-nearest FP32 FMA) on the pairs of a float4 row.
+        float2 div2[CP / 2], dr2[CP / 2], ds2[CP / 2], dt2[CP / 2];
 #pragma unroll
-        for (int c = 0; c < CP; ++c) div[c] = dr[c] = ds[c] = dt[c] = 0.f;
+        for (int c = 0; c < CP / 2; ++c) div2[c] = dr2[c] = ds2[c] = dt2[c] = make_float2(0.f, 0.f);
         const float4 *D4 = reinterpret_cast<const float4 *>(sD) + w * (CP / 4);
 #pragma unroll 5
         for (int m = 0; m < NP; ++m) {
             const float p = sQ[m * 32 + e], fr = sF[m * 32 + e], fs = sF[(NP + m) * 32 + e], ft = sF[(2 * NP + m) * 32 + e];
+            const float2 p2 = make_float2(p, p), fr2 = make_float2(fr, fr), fs2 = make_float2(fs, fs), ft2 = make_float2(ft, ft);
             const float4 *Dm = D4 + m * 3 * NW * (CP / 4);
 #pragma unroll
             for (int c4 = 0; c4 < CP / 4; ++c4) {
                 const float4 a = Dm[c4], b = Dm[NW * (CP / 4) + c4], d = Dm[2 * NW * (CP / 4) + c4];
-                const float ar[4] = {a.x, a.y, a.z, a.w}, br[4] = {b.x, b.y, b.z, b.w}, dd[4] = {d.x, d.y, d.z, d.w};
+                const float2 a2[2] = {make_float2(a.x, a.y), make_float2(a.z, a.w)};
+                const float2 b2[2] = {make_float2(b.x, b.y), make_float2(b.z, b.w)};
+                const float2 d2[2] = {make_float2(d.x, d.y), make_float2(d.z, d.w)};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int c = 4 * c4 + q;
-                    div[c] += ar[q] * fr + br[q] * fs + dd[q] * ft;
-                    dr[c] += ar[q] * p;
-                    ds[c] += br[q] * p;
-                    dt[c] += dd[q] * p;
+                for (int h = 0; h < 2; ++h) {
+                    const int c = 2 * c4 + h;
+                    div2[c] = __ffma2_rn(a2[h], fr2, div2[c]);
+                    div2[c] = __ffma2_rn(b2[h], fs2, div2[c]);
+                    div2[c] = __ffma2_rn(d2[h], ft2, div2[c]);
+                    dr2[c] = __ffma2_rn(a2[h], p2, dr2[c]);
+                    ds2[c] = __ffma2_rn(b2[h], p2, ds2[c]);
+                    dt2[c] = __ffma2_rn(d2[h], p2, dt2[c]);
                 }
             }
+        }
+        float div[CP], dr[CP], ds[CP], dt[CP];
+#pragma unroll
+        for (int c = 0; c < CP / 2; ++c) {
+            div[2 * c] = div2[c].x;
+            div[2 * c + 1] = div2[c].y;
+            dr[2 * c] = dr2[c].x;
+            dr[2 * c + 1] = dr2[c].y;
+            ds[2 * c] = ds2[c].x;
+            ds[2 * c + 1] = ds2[c].y;
+            dt[2 * c] = dt2[c].x;
+            dt[2 * c + 1] = dt2[c].y;
         }
         // gradient of p in physical coordinates; reuse dr/ds/dt as the velocity right-hand sides
 #pragma unroll
@@ -277,24 +296,36 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
         const float4 *L4 = reinterpret_cast<const float4 *>(sL) + w * (CP / 4);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            float lp[CP];
+            float2 lp2[CP / 2], dv2[CP / 2];
 #pragma unroll
-            for (int c = 0; c < CP; ++c) lp[c] = 0.f;
+            for (int c = 0; c < CP / 2; ++c) {
+                lp2[c] = make_float2(0.f, 0.f);
+                dv2[c] = make_float2(div[2 * c], div[2 * c + 1]);
+            }
 #pragma unroll 5
             for (int m = 0; m < NFP; ++m) {
                 const int fm = f * NFP + m;
                 const float xu = sTi[((2 * f + 1) * NFP + m) * 32 + e], xp = sTi[((2 * f) * NFP + m) * 32 + e];
+                const float2 xu2 = make_float2(xu, xu), xp2 = make_float2(xp, xp);
                 const float4 *Lm = L4 + fm * NW * (CP / 4);
 #pragma unroll
                 for (int c4 = 0; c4 < CP / 4; ++c4) {
                     const float4 l = Lm[c4];
-                    const float lr[4] = {l.x, l.y, l.z, l.w};
+                    const float2 l2[2] = {make_float2(l.x, l.y), make_float2(l.z, l.w)};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        div[4 * c4 + q] += lr[q] * xu;
-                        lp[4 * c4 + q] += lr[q] * xp;
+                    for (int h = 0; h < 2; ++h) {
+                        dv2[2 * c4 + h] = __ffma2_rn(l2[h], xu2, dv2[2 * c4 + h]);
+                        lp2[2 * c4 + h] = __ffma2_rn(l2[h], xp2, lp2[2 * c4 + h]);
                     }
                 }
+            }
+            float lp[CP];
+#pragma unroll
+            for (int c = 0; c < CP / 2; ++c) {
+                div[2 * c] = dv2[c].x;
+                div[2 * c + 1] = dv2[c].y;
+                lp[2 * c] = lp2[c].x;
+                lp[2 * c + 1] = lp2[c].y;
             }
             const float nx = nrm[f][0], ny = nrm[f][1], nz = nrm[f][2];
 #pragma unroll
