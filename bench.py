@@ -31,6 +31,9 @@ WORKLOAD = {"workload": "cube48_N4_P6_gaussian", "mesh": "48^3 hex x 6 Kuhn tets
             "N": 4, "P": 6, "c": 1.0, "rho": 1.0, "pulse_width": 0.1}
 METRIC = "DOF-updates/s per RK stage"
 SEED = 2000
+# dram__bytes_read.sum + dram__bytes_write.sum of k3d_stage<4> for one full stage (interior and
+# boundary-cell launches) of this workload, from one ncu capture of this build (one pass)
+K3D_TRAFFIC_BYTES = 2106660096 + 84734464
 
 
 def build_inputs(n=48):
@@ -532,7 +535,9 @@ def main():
                        l2_policy="inputs larger than L2 (state %.0f MB per array)" % (q3.size * 4 / 1e6),
                        parallelism="replicas" if world > 1 else "single"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k3d_stage<4>",
+                     "frac": achieved / peak, "traffic": K3D_TRAFFIC_BYTES if args.n == 48 else None,
+                     "traffic_over_algorithmic": K3D_TRAFFIC_BYTES / (K * bytes_per_tet) if args.n == 48 else None,
+                     "kernel": "k3d_stage<4>",
                      "peak_kind": peak_kind, "bytes_per_tet": bytes_per_tet,
                      "launch_ms": kt["k3d"]},
         "kernel_ms": kt,
