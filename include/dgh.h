@@ -221,17 +221,18 @@ int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size);
 typedef struct dgh_launch {
     int32_t tile2, tile1, cta3_per_sm;
     int32_t grid3, grid2, grid1, occ3, sms;
+    int32_t thr2, thr1;      /* threads per CTA of the 2D / 1D kernels: 32, 64, 128 or 256 */
 } dgh_launch;
 
 int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *out);
 
-/* Sets tile2, tile1 and cta3_per_sm (the other fields are ignored).  No
+/* Sets tile2, tile1, cta3_per_sm, thr2 and thr1 (the other fields are ignored).  No
  * result changes: every element's arithmetic is the same whatever the shape.
  * DGH_EINVAL if a value is out of range or the tile does not fit in shared
  * memory (the previous shape is kept). */
 int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in);
 
-/* Autotuner: coordinate search over tile2, tile1 and cta3_per_sm, each
+/* Autotuner: coordinate search over thr2, tile2, thr1, tile1 and cta3_per_sm, each
  * candidate timed with CUDA events over `steps` whole steps (best of two),
  * kept when at least 1% faster.  The fields, time and step count are saved
  * before and restored after (host copy of the state), so the search changes

@@ -64,7 +64,7 @@ class _TrainCfg(ctypes.Structure):
 
 class _Launch(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in
-                ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1", "occ3", "sms")]
+                ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1", "occ3", "sms", "thr2", "thr1")]
 
 
 _lib = None
@@ -434,12 +434,14 @@ class Solver:
         self._check(self._lib.dgh_get_launch(self._h, ctypes.byref(o)))
         return {f: getattr(o, f) for f, _ in _Launch._fields_}
 
-    def set_launch(self, tile2=None, tile1=None, cta3_per_sm=None):
+    def set_launch(self, tile2=None, tile1=None, cta3_per_sm=None, thr2=None, thr1=None):
         cur = self.launch
         o = _Launch()
         o.tile2 = cur["tile2"] if tile2 is None else int(tile2)
         o.tile1 = cur["tile1"] if tile1 is None else int(tile1)
         o.cta3_per_sm = cur["cta3_per_sm"] if cta3_per_sm is None else int(cta3_per_sm)
+        o.thr2 = cur["thr2"] if thr2 is None else int(thr2)
+        o.thr1 = cur["thr1"] if thr1 is None else int(thr1)
         self._check(self._lib.dgh_set_launch(self._h, ctypes.byref(o)))
 
     def tune(self, steps=5):

@@ -89,6 +89,7 @@ struct dgh_ctx {
     // launch shapes
     int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0, sms = 1;
     int cta3_per_sm = 0;              // tunable: persistent 3D CTAs per SM (0 = occupancy limit)
+    int thr2 = 256, thr1 = 256;       // tunable: threads per CTA of the 2D / 1D kernels
     int precision = DGH_PREC_FP32;    // arithmetic of the 3D contractions (DGH_PREC_*)
     uint8_t *tcops = nullptr;         // tensor-core operand images of D_r, D_s, D_t, LIFT (hi, then lo)
     unsigned long long *tile_ctr = nullptr;   // [11] block counters of the 3D launches of a step
@@ -385,11 +386,12 @@ struct Launch2 {
         sc.time = c->d_time;
         Args2 A = args2(c, cur, update, shadow);
         const int grid = shadow ? c->sh->grid2 : c->grid2, tile = shadow ? c->sh->tile2 : c->tile2;
+        const int thr = shadow ? 256 : c->thr2;
         const size_t smem = shadow ? c->sh->smem2 : c->smem2;
         if (update)
-            k2d_stage<N, true><<<grid, 256, smem, st>>>(A, sc, tile);
+            k2d_stage<N, true><<<grid, thr, smem, st>>>(A, sc, tile);
         else
-            k2d_stage<N, false><<<grid, 256, smem, st>>>(A, sc, tile);
+            k2d_stage<N, false><<<grid, thr, smem, st>>>(A, sc, tile);
         if (!shadow && c->cl_on) {   // learned closure: exterior state 2 (r^- + MLP(features))
             const int64_t rows = c->T * c->Np2;
             const int blocks = (int)std::min<int64_t>((rows + 255) / 256, int64_t(4) * c->sms);
@@ -414,11 +416,12 @@ struct Launch1 {
         sc.time = c->d_time;
         Args1 A = args1(c, cur, update, shadow);
         const int grid = shadow ? c->sh->grid1 : c->grid1, tile = shadow ? c->sh->tile1 : c->tile1;
+        const int thr = shadow ? 256 : c->thr1;
         const size_t smem = shadow ? c->sh->smem1 : c->smem1;
         if (update)
-            k1d_stage<N, true><<<grid, 256, smem, st>>>(A, sc, tile);
+            k1d_stage<N, true><<<grid, thr, smem, st>>>(A, sc, tile);
         else
-            k1d_stage<N, false><<<grid, 256, smem, st>>>(A, sc, tile);
+            k1d_stage<N, false><<<grid, thr, smem, st>>>(A, sc, tile);
         return DGH_OK;
     }
 };
@@ -516,8 +519,8 @@ struct Shapes {
         const int64_t tiles3 = c->precision == DGH_PREC_FP32 ? c->K32 : (c->K32 + 3) / 4;
         c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)per_sm * sms));
         int nb2 = 0, nb1 = 0;
-        if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, 256, c->smem2);
-        if (c->L) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k1d_stage<N, true>, 256, c->smem1);
+        if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, c->thr2, c->smem2);
+        if (c->L) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k1d_stage<N, true>, c->thr1, c->smem1);
         const int64_t tiles2 = (c->T + c->tile2 - 1) / c->tile2;
         const int64_t tiles1 = (c->L + c->tile1 - 1) / c->tile1;
         c->grid2 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles2, (int64_t)std::max(nb2, 1) * sms));
@@ -1534,22 +1537,29 @@ int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *o) {
     o->grid1 = ctx->grid1;
     o->occ3 = ctx->occ3;
     o->sms = ctx->sms;
+    o->thr2 = ctx->thr2;
+    o->thr1 = ctx->thr1;
     return DGH_OK;
 }
 
 int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in) {
-    if (!ctx || !in || in->tile2 < 1 || in->tile1 < 1 || in->cta3_per_sm < 0) {
-        if (ctx) ctx->err = "tile2, tile1 must be >= 1 and cta3_per_sm >= 0";
+    auto thr_ok = [](int t) { return t == 32 || t == 64 || t == 128 || t == 256; };
+    if (!ctx || !in || in->tile2 < 1 || in->tile1 < 1 || in->cta3_per_sm < 0 || !thr_ok(in->thr2) || !thr_ok(in->thr1)) {
+        if (ctx) ctx->err = "tile2, tile1 must be >= 1, cta3_per_sm >= 0, thr2 / thr1 one of 32, 64, 128, 256";
         return DGH_EINVAL;
     }
-    const int t2 = ctx->tile2, t1 = ctx->tile1, c3 = ctx->cta3_per_sm;
+    const int t2 = ctx->tile2, t1 = ctx->tile1, c3 = ctx->cta3_per_sm, h2 = ctx->thr2, h1 = ctx->thr1;
     ctx->tile2 = in->tile2;
     ctx->tile1 = in->tile1;
     ctx->cta3_per_sm = in->cta3_per_sm;
+    ctx->thr2 = in->thr2;
+    ctx->thr1 = in->thr1;
     if (dispatchN<Shapes>(ctx->N, ctx) != DGH_OK) {
         ctx->tile2 = t2;
         ctx->tile1 = t1;
         ctx->cta3_per_sm = c3;
+        ctx->thr2 = h2;
+        ctx->thr1 = h1;
         dispatchN<Shapes>(ctx->N, ctx);
         ctx->err = "launch shape does not fit in shared memory";
         return DGH_EINVAL;
@@ -1591,8 +1601,9 @@ int time_per_step(cudaStream_t st, int steps, Run run, double &ms, std::string &
     return rc;
 }
 
-// Coordinate search over the launch shape of every context (2D triangles per
-// CTA, 1D lines per CTA, persistent 3D CTAs per SM), the paper's tuning of
+// Coordinate search over the launch shape of every context (2D threads and
+// triangles per CTA, 1D threads and lines per CTA, persistent 3D CTAs per
+// SM), the paper's tuning of
 // elements per block (K_blk) carried over to these kernels: each candidate
 // is timed on whole steps and kept if it is at least 1% faster.  The fields
 // are saved before and restored after, so the search changes no result.
@@ -1615,14 +1626,17 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
     if (rc) return rc;
     if (ms_before) *ms_before = best;
     for (dgh_ctx *c : cs) {
-        for (int param = 0; param < 3 && rc == DGH_OK; ++param) {
-            int *slot = param == 0 ? &c->tile2 : param == 1 ? &c->tile1 : &c->cta3_per_sm;
+        for (int param = 0; param < 5 && rc == DGH_OK; ++param) {
+            int *slot = param == 0 ? &c->thr2 : param == 1 ? &c->tile2 : param == 2 ? &c->thr1 : param == 3 ? &c->tile1
+                                                                                                    : &c->cta3_per_sm;
             std::vector<int> cand;
-            if (param == 0 && c->T > 0)
+            if ((param == 0 && c->T > 0) || (param == 2 && c->L > 0))
+                for (int v = 32; v <= 256; v *= 2) cand.push_back(v);
+            if (param == 1 && c->T > 0)
                 for (int v = 1; v <= 32 && v <= c->T; v *= 2) cand.push_back(v);
-            if (param == 1 && c->L > 0)
+            if (param == 3 && c->L > 0)
                 for (int v = 1; v <= 32 && v <= c->L; v *= 2) cand.push_back(v);
-            if (param == 2)
+            if (param == 4)
                 for (int v = 0; v <= c->occ3; ++v) cand.push_back(v);
             int keep = *slot;
             for (int v : cand) {

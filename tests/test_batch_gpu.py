@@ -127,9 +127,9 @@ def test_solver_launch_shape_and_tune_change_no_result():
         g = dgh.Solver(VX, EToV, 3, 3)
         g.init_gaussian([0.1, -0.1, 0.2], 0.3)
         if mode == "shape":
-            g.set_launch(tile2=1, tile1=3, cta3_per_sm=1)
+            g.set_launch(tile2=1, tile1=3, cta3_per_sm=1, thr2=32, thr1=64)
             L = g.launch
-            assert (L["tile2"], L["tile1"], L["cta3_per_sm"]) == (1, 3, 1)
+            assert (L["tile2"], L["tile1"], L["cta3_per_sm"], L["thr2"], L["thr1"]) == (1, 3, 1, 32, 64)
         if mode == "tuned":
             g.tune(steps=2)
             assert g.info["step_count"] == 0
@@ -149,4 +149,6 @@ def test_set_launch_rejects_bad_shapes():
         g.set_launch(tile2=0)
     with pytest.raises(dgh.DghError):
         g.set_launch(tile2=100000)   # shared memory of the 2D tile does not fit
+    with pytest.raises(dgh.DghError):
+        g.set_launch(thr2=48)
     assert g.launch == before
