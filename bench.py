@@ -100,35 +100,47 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(seconds_budget=20.0):
+def _cpu_oracle_sample_here(seconds_budget):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     the same degree, HABC order, jitter and pulse on a 6^3-hex (1296-tet)
-    cube, timed over whole LSERK4 steps; single thread (BLAS limited to 1)."""
-    from threadpoolctl import threadpool_limits
+    cube, timed over whole LSERK4 steps (this process; its BLAS/OpenMP
+    thread counts are set by the caller through the environment)."""
     from oracle.mesh import CuboidMesh
     from oracle.solver import Solver
     from paper_1610_05023_b300 import workloads as W
     n = 6
     VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=SEED)
     x0 = W.seeded_point(SEED, [0.70, 0.65, 0.60], 0.05)
-    with threadpool_limits(1):
-        m = CuboidMesh(VX, EToV, 4, 6, [0] * 6, 1.0, 1.0)
-        s = Solver(m)
-        Y = s.gaussian_state(x0, 0.1)
-        res = {k: np.zeros_like(v) for k, v in Y.items()}
-        dt = m.dt_rule()
-        t0 = time.perf_counter()
-        steps, t = 0, 0.0
-        while True:
-            t = s.step(Y, res, t, dt)
-            steps += 1
-            el = time.perf_counter() - t0
-            if el > seconds_budget or steps >= 50:
-                break
+    m = CuboidMesh(VX, EToV, 4, 6, [0] * 6, 1.0, 1.0)
+    s = Solver(m)
+    Y = s.gaussian_state(x0, 0.1)
+    res = {k: np.zeros_like(v) for k, v in Y.items()}
+    dt = m.dt_rule()
+    t0 = time.perf_counter()
+    steps, t = 0, 0.0
+    while True:
+        t = s.step(Y, res, t, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget or steps >= 50:
+            break
     return {"value": m.ndof() * 5 * steps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": "%d LSERK4 steps of the same N=4, P=6, jittered Gaussian-pulse problem on a "
                       "6^3-hex (1296-tet) cube, FP64 numpy, 1 thread (%.1f s)" % (steps, el),
             "steps": steps, "seconds": el}
+
+
+def cpu_oracle_sample(seconds_budget=20.0):
+    """Runs _cpu_oracle_sample_here in a child process whose BLAS and OpenMP
+    pools are limited to one thread (environment set before numpy loads)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+              "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-sample", str(seconds_budget)],
+                         env=env, capture_output=True, text=True, check=True, cwd=ROOT)
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
@@ -437,6 +449,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=48, help="hexes per axis (48 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--closure-runs", type=int, default=64)
     ap.add_argument("--closure-train-n", type=int, default=24)
     ap.add_argument("--closure-eval-n", type=int, default=40)
@@ -446,6 +459,9 @@ def main():
                     help="batch: the batching form (48 independent problems); precision: the N = 6 layered "
                          "workload with the FP32 and tensor-core 3D kernels")
     args = ap.parse_args()
+    if args.cpu_oracle_sample is not None:   # child process of cpu_oracle_sample()
+        print(json.dumps(_cpu_oracle_sample_here(args.cpu_oracle_sample)), flush=True)
+        return
     if args.impl == "reference":
         return run_reference(args)
     if args.form == "batch":
