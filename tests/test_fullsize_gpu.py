@@ -1,0 +1,113 @@
+"""The benchmark workload at full size (48^3 x 6 = 663,552 tets, N = 4,
+HABC P = 6) in the launch configuration bench.py times: tuned launch shapes,
+one CUDA graph per step replayed on a user stream, the HABC chain on a side
+stream overlapping the interior cells.  The FP64 oracle cannot run this size,
+so the checks are properties that hold at any size:
+
+* the graph / overlap path equals plain direct launches on the legacy
+  stream bit for bit (each cell's arithmetic does not depend on scheduling);
+* with the basic ABC (P = 0) the discrete energy never increases;
+* against the exact solution of a Gaussian pulse in free space the error is
+  at least 10 times below the oracle's own error on a 6x coarser mesh.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1610_05023_b300 as dgh
+from paper_1610_05023_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+N48 = 48
+
+
+@pytest.fixture(scope="module")
+def mesh48():
+    VX, EToV = W.kuhn_mesh(N48, 1.0, 0.02, seed=2000)
+    x0 = W.seeded_point(2000, [0.70, 0.65, 0.60], 0.05)
+    return VX, EToV, x0
+
+
+def test_fullsize_graph_overlap_equals_direct_launches(mesh48):
+    import torch
+    VX, EToV, x0 = mesh48
+    s = torch.cuda.Stream()
+    a = dgh.Solver(VX, EToV, 4, 6, stream=s)
+    a.init_gaussian(x0, 0.1)
+    a.tune(steps=2)                      # the shapes bench.py uses
+    b = dgh.Solver(VX, EToV, 4, 6)       # legacy stream: direct launches, no side stream
+    b.init_gaussian(x0, 0.1)
+    for g in (a, b):
+        g.step(40)
+        g.sync()
+    for lv in (3, 2, 1):
+        assert np.array_equal(a.get_state(lv), b.get_state(lv)), lv
+    assert a.info["step_count"] == b.info["step_count"] == 40
+    a.close()
+    b.close()
+
+
+def test_fullsize_energy_nonincreasing_with_abc(mesh48):
+    VX, EToV, x0 = mesh48
+    g = dgh.Solver(VX, EToV, 4, 0)
+    g.init_gaussian(x0, 0.1)
+    E = [g.energy()]
+    for _ in range(30):
+        g.step(20)
+        E.append(g.energy())
+    E = np.array(E)
+    assert np.all(np.diff(E) <= 1e-6 * E[0]), np.diff(E).max()
+    assert E[-1] < 0.9 * E[0]            # the pulse has started to leave through the faces
+    g.close()
+
+
+def _exact_q3(x, t, sigma):
+    r = np.linalg.norm(x, axis=-1)
+    F = lambda s: s * np.exp(-s ** 2 / sigma ** 2)
+    A = lambda s: -0.5 * sigma ** 2 * np.exp(-s ** 2 / sigma ** 2)
+    rs = np.maximum(r, 1e-12)
+    p = (F(rs - t) + F(rs + t)) / (2 * rs)
+    ur = -((F(rs + t) - F(rs - t)) / (2 * rs) - (A(rs + t) - A(rs - t)) / (2 * rs ** 2))
+    q = np.zeros(x.shape[:-1] + (4,))
+    q[..., 0] = p
+    for i in range(3):
+        q[..., 1 + i] = ur * x[..., i] / rs
+    return np.moveaxis(q, -1, 1)          # [K][4][Np]
+
+
+def _energy_error(VX, EToV, N, P, sigma, T, dt_from=None):
+    g = dgh.Solver(VX, EToV, N, P)
+    nst = int(math.ceil(T / g.info["dt"]))
+    g.close()
+    g = dgh.Solver(VX, EToV, N, P, dt=T / nst)
+    g.init_gaussian([0, 0, 0], sigma)
+    E0 = g.energy()
+    g.step(nst)
+    diff = g.get_state(3) - _exact_q3(g.nodes(3), T, sigma)
+    scratch = dgh.Solver(VX, EToV, N, 0)
+    scratch.set_state(3, diff)
+    err = math.sqrt(scratch.energy() / E0)
+    g.close()
+    scratch.close()
+    return err
+
+
+def test_fullsize_gaussian_pulse_against_exact_solution(mesh48):
+    from oracle.mesh import CuboidMesh
+    from oracle.solver import Solver
+    VX, EToV, _ = mesh48
+    sigma, T = 0.15, 0.3
+    err48 = _energy_error(VX, EToV, 4, 6, sigma, T)
+    # the oracle's own error on an 8^3 x 6 mesh (6x coarser)
+    VX8, EToV8 = W.kuhn_mesh(8, 1.0, 0.02, seed=2000)
+    m = CuboidMesh(VX8, EToV8, 4, 6, [0] * 6, 1.0, 1.0)
+    o = Solver(m)
+    nst = int(math.ceil(T / m.dt_rule()))
+    Y = o.gaussian_state([0, 0, 0], sigma)
+    E0 = o.energy(Y)
+    Y, _, _ = o.run(Y, 0.0, T / nst, nst)
+    d = {"q3": Y["q3"] - _exact_q3(m.x, T, sigma), "q2": 0 * Y["q2"], "q1": 0 * Y["q1"]}
+    err8 = math.sqrt(o.energy(d) / E0)
+    print("energy-norm error vs exact: 48^3 GPU %.3e, 8^3 oracle %.3e" % (err48, err8))
+    assert err48 <= 0.1 * err8
