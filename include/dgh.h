@@ -203,6 +203,15 @@ int dgh_get_energy(dgh_ctx *ctx, double *E);
  *  -- e.g. on two streams at once -- race and must be serialised. */
 int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stream);
 
+/* Failure-detection self-test: a one-thread kernel waits, with the bounded
+ * wait of the stage kernels and a limit of `limit` polls, on an mbarrier
+ * phase that nothing completes; it gives up and sets the context's error
+ * word, and the call returns what dgh_sync then reports (DGH_ETIMEOUT).  No
+ * fault, trap or endless wait is involved; the context stays usable.
+ * dgh_clear_error resets the error word (synchronising). */
+int dgh_selftest_wait(dgh_ctx *ctx, int64_t limit);
+int dgh_clear_error(dgh_ctx *ctx);
+
 /* Serialises the complete time-stepping state (all levels, residuals,
  * boundary algebra, time, step count) into buf.  Call with buf == NULL to
  * query the size in *size.  dgh_load_state restores it into a context

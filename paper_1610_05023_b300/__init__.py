@@ -22,7 +22,9 @@ PREC_BF16_TC = 1
 PREC_FP16_TC = 2
 PREC_SPLIT_BF16 = 3
 
-_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -6: "ESTATE", -7: "EUNSUPPORTED"}
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ETIMEOUT", -6: "ESTATE",
+           -7: "EUNSUPPORTED"}
+DGH_ETIMEOUT = -5
 
 
 class DghError(RuntimeError):
@@ -116,6 +118,8 @@ def load_library(path=LIB_PATH):
         "dgh_batch_get_energy": (ctypes.c_int, [P, ctypes.c_int, D]),
         "dgh_batch_get_launch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_Launch)]),
         "dgh_batch_tune": (ctypes.c_int, [P, ctypes.c_int, D, D]),
+        "dgh_selftest_wait": (ctypes.c_int, [P, ctypes.c_int64]),
+        "dgh_clear_error": (ctypes.c_int, [P]),
         "dgh_closure_set_weights": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
         "dgh_closure_record": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                               ctypes.c_uint64]),
@@ -381,6 +385,13 @@ class Solver:
 
     def sync(self):
         self._check(self._lib.dgh_sync(self._h))
+
+    def selftest_wait(self, limit=1000):
+        """Return code of the bounded-wait self-test (DGH_ETIMEOUT = -5 expected)."""
+        return self._lib.dgh_selftest_wait(self._h, int(limit))
+
+    def clear_error(self):
+        self._check(self._lib.dgh_clear_error(self._h))
 
     def energy(self):
         e = ctypes.c_double()

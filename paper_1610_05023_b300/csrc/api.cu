@@ -2421,6 +2421,40 @@ int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg
     return DGH_OK;
 }
 
+
+}  // extern "C"
+
+namespace {
+
+// One thread waits, with the kernels' bounded-wait helper and a short limit,
+// on an mbarrier phase that nothing completes; it gives up, sets the error
+// word and returns.
+__global__ void k_selftest_wait(int *err, unsigned long long limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait(&bar, 0, err, limit);
+    }
+}
+
+}  // namespace
+
+extern "C" int dgh_selftest_wait(dgh_ctx *ctx, int64_t limit) {
+    if (!ctx || limit < 1) return DGH_EINVAL;
+    k_selftest_wait<<<1, 32, 0, ctx->stream>>>(ctx->d_err, (unsigned long long)limit);
+    CK(cudaGetLastError());
+    return dgh_sync(ctx);
+}
+
+extern "C" int dgh_clear_error(dgh_ctx *ctx) {
+    if (!ctx) return DGH_EINVAL;
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DGH_OK;
+}
+
+extern "C" {
 }  // extern "C"
 
 // ============================================================================

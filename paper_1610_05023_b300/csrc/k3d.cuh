@@ -110,9 +110,10 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // bounded wait on an mbarrier phase; returns false (and sets *err) on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          unsigned long long limit = kWaitLimit) {
     const uint32_t a = smem_addr(bar);
-    for (unsigned long long it = 0; it < kWaitLimit; ++it) {
+    for (unsigned long long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"

@@ -222,3 +222,19 @@ def test_stream_and_graph_path_equals_default_stream():
         x.sync()
     for lv in (3, 2, 1):
         assert np.array_equal(a.get_state(lv), b.get_state(lv))
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A bounded device-side wait that nothing completes gives up: the call
+    reports DGH_ETIMEOUT, and after clearing the error word the context
+    steps and reads back normally."""
+    VX, EToV = W.kuhn_mesh(2, 1.0, 0.02, seed=13)
+    g = dgh.Solver(VX, EToV, 3, 2)
+    g.init_gaussian([0.1, 0.0, 0.0], 0.3)
+    assert g.selftest_wait(2000) == dgh.DGH_ETIMEOUT
+    with pytest.raises(dgh.DghError):
+        g.sync()                      # the error word stays set until cleared
+    g.clear_error()
+    g.step(5)
+    g.sync()
+    assert np.all(np.isfinite(g.get_state(3)))
