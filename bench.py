@@ -538,7 +538,7 @@ def main():
     out = g.get_state(3)
     t1 = time.perf_counter()
     e2e_value = world * ndof * 5 * e2e_steps / (t1 - t0)
-    state_bytes = q3.size * 4
+    state_bytes = q3.size * 8      # FP64 host arrays copied as they are (converted on the device)
 
     parts3 = 2 if info["n_tris"] > 0 else 1      # interior cells, then cells with HABC faces
     launches_per_step = 5 * (parts3 + (info["n_tris"] > 0) + (info["n_lines"] > 0) + (info["n_corners"] > 0)) + 1

@@ -47,6 +47,7 @@ struct dgh_ctx {
     bool no_overlap = false;          // union of a batch: one launch over all cells, no side stream
     std::vector<int64_t> part_blk0;   // first 32-cell block of every part (batch problem), + end
     std::vector<int64_t> can2dev;     // canonical cell -> device cell slot
+    int *can2dev_d = nullptr;         // the same map on the device (state transfers)
     cudaStream_t side = nullptr;      // HABC chain stream (overlaps the interior 3D work)
     cudaEvent_t ev3d[5] = {}, ev2d[5] = {}, evjoin = nullptr;
     int C = 0;
@@ -635,35 +636,84 @@ float *level_ptr(dgh_ctx *c, int level, bool res) {
     return res ? c->res1 : c->q1;
 }
 
-// canonical [K][4][Np] index -> interleaved [K32][4][Np][32] index
-inline size_t il3(const dgh_ctx *c, size_t i) {
-    const size_t per = size_t(4) * c->Np;
-    const size_t k = size_t(c->can2dev[i / per]), r = i % per;
-    return ((k / 32) * per + r) * 32 + (k % 32);
+// State transfers convert and reorder on the device: the host copies plain
+// FP64 arrays in canonical order, the kernels below map them to and from the
+// FP32 device layouts (cell-interleaved for the 3D fields).
+__global__ void k_scatter3(const double *src, float *q, const int *c2d, int64_t n, int per) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / per;
+        const int r = (int)(i % per);
+        const int64_t kd = c2d[k];
+        q[((kd >> 5) * per + r) * 32 + (kd & 31)] = (float)src[i];
+    }
 }
 
-int copy_out3(dgh_ctx *c, const float *dptr, double *out, size_t n) {
-    std::vector<float> h(size_t(c->K32) * 32 * 4 * c->Np);
-    cudaError_t e = cudaMemcpyAsync(h.data(), dptr, h.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+__global__ void k_gather3(const float *q, double *dst, const int *c2d, int64_t n, int per) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / per;
+        const int r = (int)(i % per);
+        const int64_t kd = c2d[k];
+        dst[i] = (double)q[((kd >> 5) * per + r) * 32 + (kd & 31)];
+    }
+}
+
+__global__ void k_d2f(const double *a, float *b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+__global__ void k_f2d(const float *a, double *b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+int xfer_grid(const dgh_ctx *c, size_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)((n + 255) / 256), int64_t(8) * std::max(c->sms, 1)));
+}
+
+// device array dptr (level layout) -> host doubles out (canonical), n values
+int copy_out_level(dgh_ctx *c, int level, const float *dptr, double *out, size_t n) {
+    if (n == 0) return DGH_OK;
+    double *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&tmp, n * sizeof(double), c->stream);
+    if (e == cudaSuccess) {
+        if (level == 3)
+            k_gather3<<<xfer_grid(c, n), 256, 0, c->stream>>>(dptr, tmp, c->can2dev_d, (int64_t)n, 4 * c->Np);
+        else
+            k_f2d<<<xfer_grid(c, n), 256, 0, c->stream>>>(dptr, tmp, (int64_t)n);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        cudaFreeAsync(tmp, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
     if (e != cudaSuccess) {
-        c->err = std::string("device to host copy: ") + cudaGetErrorString(e);
+        c->err = std::string("device to host transfer: ") + cudaGetErrorString(e);
         return DGH_ECUDA;
     }
-    for (size_t i = 0; i < n; ++i) out[i] = h[il3(c, i)];
     return DGH_OK;
 }
 
-int copy_out(dgh_ctx *c, const float *dptr, double *out, size_t n) {
+// host doubles in (canonical), n values -> device array dptr (level layout)
+int copy_in_level(dgh_ctx *c, int level, const double *in, float *dptr, size_t n) {
     if (n == 0) return DGH_OK;
-    std::vector<float> h(n);
-    cudaError_t e = cudaMemcpyAsync(h.data(), dptr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    double *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&tmp, n * sizeof(double), c->stream);
+    if (e == cudaSuccess) {
+        e = cudaMemcpyAsync(tmp, in, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) {
+            if (level == 3)
+                k_scatter3<<<xfer_grid(c, n), 256, 0, c->stream>>>(tmp, dptr, c->can2dev_d, (int64_t)n, 4 * c->Np);
+            else
+                k_d2f<<<xfer_grid(c, n), 256, 0, c->stream>>>(tmp, dptr, (int64_t)n);
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(tmp, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
     if (e != cudaSuccess) {
-        c->err = std::string("device to host copy: ") + cudaGetErrorString(e);
+        c->err = std::string("host to device transfer: ") + cudaGetErrorString(e);
         return DGH_ECUDA;
     }
-    for (size_t i = 0; i < n; ++i) out[i] = h[i];
     return DGH_OK;
 }
 
@@ -937,6 +987,8 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
             return fail(rc, "");
         if (ctx->precision != DGH_PREC_FP32 && (rc = upload(ctx, ctx->tcops, tc_operator_images(T3, ctx->precision))))
             return fail(rc, "");
+        std::vector<int> c2d(ctx->can2dev.begin(), ctx->can2dev.end());
+        if ((rc = upload(ctx, ctx->can2dev_d, c2d))) return fail(rc, "");
     }
     // ---------------------------------------------------------------- 2D
     const int64_t Tn = m.Ktri;
@@ -1249,17 +1301,8 @@ int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count) {
         return DGH_EINVAL;
     }
     if (n == 0) return DGH_OK;
-    std::vector<float> h;
-    if (level == 3) {
-        h.assign(size_t(ctx->K32) * 32 * 4 * ctx->Np, 0.f);
-        for (size_t i = 0; i < n; ++i) h[il3(ctx, i)] = float(in[i]);
-    } else {
-        h.resize(n);
-        for (size_t i = 0; i < n; ++i) h[i] = float(in[i]);
-    }
-    CK(cudaMemcpyAsync(level_ptr(ctx, level, false), h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    int rc = copy_in_level(ctx, level, in, level_ptr(ctx, level, false), n);
+    if (rc) return rc;
     ctx->dirty = true;
     return DGH_OK;
 }
@@ -1271,8 +1314,7 @@ int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count) {
         ctx->err = "state size mismatch";
         return DGH_EINVAL;
     }
-    if (level == 3) return copy_out3(ctx, ctx->q3, out, n);
-    return copy_out(ctx, level_ptr(ctx, level, false), out, n);
+    return copy_out_level(ctx, level, level_ptr(ctx, level, false), out, n);
 }
 
 int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count) {
@@ -1282,7 +1324,7 @@ int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count) {
         ctx->err = "field size mismatch";
         return DGH_EINVAL;
     }
-    if (level == 3) return copy_out3(ctx, ctx->q3, out, n);
+    if (level == 3) return copy_out_level(ctx, 3, ctx->q3, out, n);
     if (n == 0) return DGH_OK;
     if (ctx->dirty) {
         int rc = run_closure(ctx);
@@ -1295,7 +1337,7 @@ int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count) {
         k_full2<<<blocks, 256, 0, ctx->stream>>>(ctx->q2, ctx->q0_3, tmp, ctx->T, ctx->P, ctx->Np2);
     else
         k_full1<<<blocks, 256, 0, ctx->stream>>>(ctx->q1, ctx->q0_2, ctx->cP, tmp, ctx->L, ctx->P, ctx->Np1);
-    int rc = copy_out(ctx, tmp, out, n);
+    int rc = copy_out_level(ctx, level, tmp, out, n);
     cudaFreeAsync(tmp, ctx->stream);
     return rc;
 }
