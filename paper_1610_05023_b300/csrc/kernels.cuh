@@ -131,7 +131,10 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
     float *s0 = sg + tile_tris * GEO2;                // tile*NP2 q0
     float *sn = s0 + tile_tris * NP2;                 // tile*P*3*NP2 new (p*, v1, v2)
     float *sr = sn + tile_tris * P * 3 * NP2;         // tile*P*NP2 dp*/dt of this stage (closure features)
-    int *sfm = reinterpret_cast<int *>(sr + tile_tris * P * NP2);
+    float *sres = sr + tile_tris * P * NP2;           // tile*P*3*NP2 residuals (update only)
+    float *sxin = sres + tile_tris * P * 3 * NP2;     // tile*P*NE*2 exterior (p, v.n) at the edge nodes (update only)
+    float *strb = sxin + tile_tris * P * NE * 2;      // tile*2*NP2 own 3D traces of the triangle
+    int *sfm = reinterpret_cast<int *>(strb + tile_tris * 2 * NP2);
     const int tid = threadIdx.x, nth = blockDim.x;
     if (UPDATE) {
         for (int i = tid; i < 2 * NP2 * NP2; i += nth) sD[i] = A.D[i];
@@ -143,9 +146,39 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
         const int64_t t0 = tile * tile_tris;
         const int nt = (int)((A.T - t0) < tile_tris ? (A.T - t0) : tile_tris);
         __syncthreads();
-        for (int i = tid; i < nt * P * 3 * NP2; i += nth) sq[i] = A.q[t0 * P * 3 * NP2 + i];
+        // every global input of the tile in one phase (one memory round trip):
+        // fields, residuals, geometry, q0, the exterior states at the edge
+        // nodes (neighbour traces / edge characteristic) and the own 3D traces
+        for (int i = tid; i < nt * P * 3 * NP2; i += nth) {
+            sq[i] = A.q[t0 * P * 3 * NP2 + i];
+            if (UPDATE) sres[i] = A.res[t0 * P * 3 * NP2 + i];
+        }
         for (int i = tid; i < nt * GEO2; i += nth) sg[i] = A.geo[t0 * GEO2 + i];
         for (int i = tid; i < nt * NP2; i += nth) s0[i] = A.q0[t0 * NP2 + i];
+        for (int i = tid; i < nt * 2 * NP2; i += nth) {
+            const int t = i / (2 * NP2), r = i % (2 * NP2);
+            strb[i] = A.trb[(int64_t)A.tri_bface[t0 + t] * 2 * NP2 + r];
+        }
+        if (UPDATE) {
+            for (int i = tid; i < nt * P * NE; i += nth) {
+                const int t = i / (P * NE), r = i % (P * NE), a = r / NE, em = r % NE, e = em / NFP2, m = em % NFP2;
+                const int64_t tg = t0 + t;
+                const int c = A.conn[tg * 3 + e];
+                float pp = 0.f, vnp = 0.f;
+                if (c >= 0) {
+                    const int nb = c >> 1;
+                    const int mm = (c & 1) ? (NFP2 - 1 - m) : m;
+                    const int tn = nb / 3, en = nb % 3;
+                    const float *tr = A.tr_in + (((int64_t)tn * P + a) * 3 + en) * 2 * NFP2;
+                    pp = tr[mm];
+                    vnp = -tr[NFP2 + mm];
+                } else if (c != -2) {
+                    pp = 2.0f * A.qb[((tg * 3 + e) * P + a) * NFP2 + m];
+                }
+                sxin[2 * i] = pp;
+                sxin[2 * i + 1] = vnp;
+            }
+        }
         __syncthreads();
         if (UPDATE) {
             for (int i = tid; i < nt * P * NP2; i += nth) {
@@ -164,20 +197,10 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
                 const float vnm = nx * qa[NP2 + n] + ny * qa[2 * NP2 + n];
                 const int64_t tg = t0 + t;
                 const int c = A.conn[tg * 3 + e];
-                float pp, vnp;
-                if (c >= 0) {
-                    const int nb = c >> 1;
-                    const int mm = (c & 1) ? (NFP2 - 1 - m) : m;
-                    const int tn = nb / 3, en = nb % 3;
-                    const float *tr = A.tr_in + (((int64_t)tn * P + a) * 3 + en) * 2 * NFP2;
-                    pp = tr[mm];
-                    vnp = -tr[NFP2 + mm];
-                } else if (c == -2) {
+                float pp = sxin[2 * i], vnp = sxin[2 * i + 1];
+                if (c == -2) {   // p = 0 edge: mirror state
                     pp = -pm;
                     vnp = vnm;
-                } else {
-                    pp = 2.0f * A.qb[((tg * 3 + e) * P + a) * NFP2 + m];
-                    vnp = 0.0f;
                 }
                 const float fs = g[6 + 6 * e], wm = g[7 + 6 * e], zz = g[8 + 6 * e], iz = g[9 + 6 * e];
                 const float dP = wm * (pp - pm) + zz * (vnm - vnp);
@@ -217,7 +240,7 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
                 const int64_t base = ((t0 + t) * P + a) * 3 * NP2;
                 sr[(t * P + a) * NP2 + n] = rhs[0];
                 for (int fl = 0; fl < 3; ++fl) {
-                    const float rr = sc.a * A.res[base + fl * NP2 + n] + sc.dt * rhs[fl];
+                    const float rr = sc.a * sres[(t * P + a) * 3 * NP2 + fl * NP2 + n] + sc.dt * rhs[fl];
                     A.res[base + fl * NP2 + n] = rr;
                     const float qv = qa[fl * NP2 + n] + sc.b * rr;
                     A.q[base + fl * NP2 + n] = qv;
@@ -232,7 +255,7 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
         for (int i = tid; i < nt * NP2; i += nth) {
             const int t = i / NP2, n = i % NP2;
             const int64_t tg = t0 + t;
-            const float *tr = A.trb + (int64_t)A.tri_bface[tg] * 2 * NP2;   // tet face traces (Nfp == Np2)
+            const float *tr = strb + t * 2 * NP2;   // own tet face traces (Nfp == Np2)
             const float Z = sg[t * GEO2 + 24];
             const float rp = 0.5f * (tr[n] + Z * tr[NP2 + n]);
             float rm = 0.f;
@@ -273,7 +296,8 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
 
 inline size_t k2d_smem(int N, int P, int tile) {
     const int NP2 = (N + 1) * (N + 2) / 2, NFP2 = N + 1, NE = 3 * NFP2;
-    return sizeof(float) * (2 * NP2 * NP2 + NE * NP2 + tile * (2 * P * 3 * NP2 + 2 * P * NP2 + P * 2 * NE + GEO2 + NP2)) +
+    return sizeof(float) * (2 * NP2 * NP2 + NE * NP2 +
+                            tile * (3 * P * 3 * NP2 + 2 * P * NP2 + 2 * P * 2 * NE + GEO2 + NP2 + 2 * NP2)) +
            sizeof(int) * NE;
 }
 
