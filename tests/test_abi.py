@@ -98,3 +98,47 @@ def test_batch_plan_groups_and_sums():
         for k in ("n_cells", "n_tris", "n_lines", "n_corners", "n_bfaces", "ndof"):
             assert info[k] == sum(m[k] for m in members), (g, k)
         assert (info["order"], info["habc_order"]) == (members[0]["order"], members[0]["habc_order"])
+
+
+def test_plan_rejects_edge_inputs():
+    """Empty and oversized meshes, out-of-range codes, a degenerate cell and a
+    dangling vertex id are rejected with the documented codes, before any
+    array beyond the stated sizes is read."""
+    L = dgh.load_library()
+    VX, EToV = W.kuhn_mesh(1)
+    info = dgh._Info()
+
+    def code(**kw):
+        args = dict(VX=VX, EToV=EToV, N=2, P=1, bc=(0,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0)
+        args.update(kw)
+        d, keep = dgh._make_desc(args["VX"], args["EToV"], args["N"], args["P"], args["bc"], args["c"], args["rho"],
+                                 args["dt"], args["cfl"], kw.get("precision", 0))
+        for k, v in kw.get("patch", {}).items():
+            setattr(d, k, v)
+        return L.dgh_plan(ctypes.byref(d), ctypes.byref(info))
+
+    assert code() == 0
+    assert code(patch={"n_cells": 0}) == -1                     # empty mesh
+    assert code(patch={"n_cells": (1 << 26) + 1}) == -7          # beyond the 32-bit connectivity encoding
+    assert code(P=9) == -7                                       # HABC order above 8
+    assert code(N=0) == -7
+    assert code(precision=7) == -7                               # unknown precision code
+    assert code(bc=(0, 0, 0, 0, 0, 5)) == -1                     # unknown boundary code
+    flat = VX.copy()
+    E = EToV.copy()
+    E[0] = [0, 1, 2, 3]
+    flat[3] = flat[0] + (flat[1] - flat[0]) + (flat[2] - flat[0])  # vertex 3 in the plane of 0, 1, 2
+    assert code(VX=flat, EToV=E) == -1                           # degenerate cell (or broken conformity)
+    E2 = EToV.copy()
+    E2[0, 0] = VX.shape[0]                                        # dangling vertex id
+    assert code(EToV=E2) == -1
+    # the tensor-core modes plan on the CPU like the FP32 path
+    assert code(precision=dgh.PREC_SPLIT_BF16) == 0 and info.n_cells == 6
+
+
+def test_batch_plan_separates_precisions():
+    VX, EToV = W.kuhn_mesh(2, 1.0, 0.02, seed=9)
+    probs = [dict(VX=VX, EToV=EToV, N=3, P=2), dict(VX=VX, EToV=EToV, N=3, P=2, precision=dgh.PREC_SPLIT_BF16),
+             dict(VX=VX, EToV=EToV, N=3, P=2)]
+    gof, infos = dgh.batch_plan(probs)
+    assert gof == [0, 1, 0] and len(infos) == 2

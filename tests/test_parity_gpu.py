@@ -238,3 +238,19 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     g.step(5)
     g.sync()
     assert np.all(np.isfinite(g.get_state(3)))
+
+
+@pytest.mark.parametrize("prec", [dgh.PREC_FP32, dgh.PREC_SPLIT_BF16])
+def test_parity_single_hexahedron(prec):
+    """One hexahedron = 6 tets, every cell on the boundary (the interior-cell
+    launch is empty), all 6 faces, 12 edges and 8 corners active."""
+    VX, EToV = W.kuhn_mesh(1, 1.0, 0.0, seed=0)
+    m = CuboidMesh(VX, EToV, 3, 2, [BC_HABC] * 6, 1.0, 1.0)
+    dt = m.dt_rule()
+    o = Solver(m)
+    g = dgh.Solver(VX, EToV, 3, 2, dt=dt, precision=prec)
+    Y = o.gaussian_state([0.2, -0.1, 0.1], 0.5)
+    g.init_gaussian([0.2, -0.1, 0.1], 0.5)
+    Y, _, _ = o.run(Y, 0.0, dt, 30)
+    g.step(30)
+    assert_close(rel_errors(gpu_levels(g), Y), 1e-5 if prec == dgh.PREC_FP32 else 5e-5)
