@@ -356,8 +356,15 @@ class Solver:
             raise ValueError("state shape %s != %s" % (a.shape, self.shape(level)))
         self._check(self._lib.dgh_set_state(self._h, level, _dptr(a), a.size))
 
-    def get_state(self, level):
-        out = np.empty(self.shape(level))
+    def get_state(self, level, out=None):
+        """Time-stepped variables of a level (canonical layout, FP64); out: an
+        optional C-contiguous float64 array of the right shape to fill (e.g. in
+        pinned host memory)."""
+        shape = self.shape(level)
+        if out is None:
+            out = np.empty(shape)
+        elif out.dtype != np.float64 or out.shape != shape or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of shape %s" % (shape,))
         self._check(self._lib.dgh_get_state(self._h, level, _dptr(out), out.size))
         return out
 
