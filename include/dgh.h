@@ -183,6 +183,13 @@ int dgh_sync(dgh_ctx *ctx);
  * reduced on the GPU with FP64 accumulation (synchronising). */
 int dgh_get_energy(dgh_ctx *ctx, double *E);
 
+/* Error reduction (Error(t)^2 = E(q - ref) / E_ref of the paper's accuracy
+ * study, Sec. 4.1): *E = the discrete energy of the difference between the
+ * 3D fields and ref, a HOST array [K][4][Np] in the canonical order of
+ * dgh_get_state (count = K*4*Np doubles), with the FP64 mass matrix and FP64
+ * arithmetic on the device (synchronising). */
+int dgh_get_error_energy(dgh_ctx *ctx, const double *ref, size_t count, double *E);
+
 /* Energy as dgh_get_energy, but the call allocates no memory at all: the
  * per-block partial sums live in a fixed static device array of the library
  * (65,536 doubles = 512 KiB, held on every GPU that loads the library until

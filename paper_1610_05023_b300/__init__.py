@@ -98,6 +98,7 @@ def load_library(path=LIB_PATH):
         "dgh_sync": (ctypes.c_int, [P]),
         "dgh_time_kernels": (ctypes.c_int, [P, ctypes.c_int64, D]),
         "dgh_get_energy": (ctypes.c_int, [P, D]),
+        "dgh_get_error_energy": (ctypes.c_int, [P, D, ctypes.c_size_t, D]),
         "dgh_get_energy_noalloc": (ctypes.c_int, [P, ctypes.c_void_p, P]),
         "dgh_save_state": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "dgh_load_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
@@ -403,6 +404,15 @@ class Solver:
     def energy(self):
         e = ctypes.c_double()
         self._check(self._lib.dgh_get_energy(self._h, ctypes.byref(e)))
+        return e.value
+
+    def error_energy(self, ref3):
+        """Energy of (3D fields - ref3), ref3 [K][4][Np] FP64 (device reduction, FP64)."""
+        r = np.ascontiguousarray(ref3, dtype=np.float64)
+        if r.shape != self.shape(3):
+            raise ValueError("reference shape %s != %s" % (r.shape, self.shape(3)))
+        e = ctypes.c_double()
+        self._check(self._lib.dgh_get_error_energy(self._h, _dptr(r), r.size, ctypes.byref(e)))
         return e.value
 
     def energy_noalloc(self, d_out, stream=None):

@@ -63,6 +63,7 @@ struct dgh_ctx {
     int *d_err = nullptr;
     int *conn3 = nullptr;
     float *D3 = nullptr, *L3 = nullptr, *M3 = nullptr;
+    double *M3d = nullptr;            // FP64 mass matrix (error reductions)
     int *fmask3 = nullptr, *fperm3 = nullptr, *nslot3 = nullptr;
     double *cellv = nullptr, *rst = nullptr, *ew = nullptr;
     // 2D
@@ -717,6 +718,54 @@ int copy_in_level(dgh_ctx *c, int level, const double *in, float *dptr, size_t n
     return DGH_OK;
 }
 
+// Energy of the difference between the 3D fields and a reference field given
+// in canonical order (FP64), per cell |J| [d_p^T M d_p / (2 rho c^2) +
+// (rho/2) sum_i d_u_i^T M d_u_i], all in FP64 with the FP64 mass matrix.
+template <int N>
+__global__ void __launch_bounds__(256) k_energy_diff_partial(const float *q, const double *ref, const double *Md,
+                                                             const double *ew, const int *c2d, int64_t K,
+                                                             double *partial) {
+    constexpr int NP = Ord<N>::NP;
+    extern __shared__ double sMd[];
+    __shared__ double red[256];
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sMd[i] = Md[i];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < K * 4; it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = it / 4;
+        const int fl = (int)(it % 4);
+        const int64_t kd = c2d[k];
+        const float *x = q + (kd >> 5) * (4 * NP * 32) + fl * NP * 32 + (kd & 31);
+        const double *r = ref + it * NP;
+        double sacc = 0.0;
+        for (int n = 0; n < NP; ++n) {
+            double y = 0.0;
+            for (int m = 0; m < NP; ++m) y += sMd[n * NP + m] * ((double)x[m * 32] - r[m]);
+            sacc += ((double)x[n * 32] - r[n]) * y;
+        }
+        acc += sacc * ew[2 * kd + (fl == 0 ? 0 : 1)];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+template <int N>
+struct EnergyDiff {
+    static int run(dgh_ctx *c, const double *dref) {
+        constexpr int NP = Ord<N>::NP;
+        const size_t smem = sizeof(double) * NP * NP;
+        cudaFuncSetAttribute(k_energy_diff_partial<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_energy_diff_partial<N><<<c->energy_blocks, 256, smem, c->stream>>>(c->q3, dref, c->M3d, c->ew, c->can2dev_d,
+                                                                            c->K, c->partial);
+        return DGH_OK;
+    }
+};
+
 }  // namespace
 
 // ============================================================================
@@ -988,7 +1037,7 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
         if (ctx->precision != DGH_PREC_FP32 && (rc = upload(ctx, ctx->tcops, tc_operator_images(T3, ctx->precision))))
             return fail(rc, "");
         std::vector<int> c2d(ctx->can2dev.begin(), ctx->can2dev.end());
-        if ((rc = upload(ctx, ctx->can2dev_d, c2d))) return fail(rc, "");
+        if ((rc = upload(ctx, ctx->can2dev_d, c2d)) || (rc = upload(ctx, ctx->M3d, T3.M.a))) return fail(rc, "");
     }
     // ---------------------------------------------------------------- 2D
     const int64_t Tn = m.Ktri;
@@ -1493,6 +1542,32 @@ int dgh_get_energy(dgh_ctx *ctx, double *E) {
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return DGH_OK;
+}
+
+int dgh_get_error_energy(dgh_ctx *ctx, const double *ref, size_t count, double *E) {
+    if (!ctx || !ref || !E) return DGH_EINVAL;
+    size_t n = 0;
+    level_count(ctx, 3, n);
+    if (count != n) {
+        ctx->err = "reference size mismatch";
+        return DGH_EINVAL;
+    }
+    double *dref = nullptr;
+    CK(cudaMallocAsync((void **)&dref, n * sizeof(double), ctx->stream));
+    cudaError_t e = cudaMemcpyAsync(dref, ref, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        dispatchN<EnergyDiff>(ctx->N, ctx, (const double *)dref);
+        k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, ctx->energy_blocks, ctx->d_energy);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(dref, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("error energy: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
     return DGH_OK;
 }
 

@@ -84,12 +84,8 @@ def _energy_error(VX, EToV, N, P, sigma, T, dt_from=None):
     g.init_gaussian([0, 0, 0], sigma)
     E0 = g.energy()
     g.step(nst)
-    diff = g.get_state(3) - _exact_q3(g.nodes(3), T, sigma)
-    scratch = dgh.Solver(VX, EToV, N, 0)
-    scratch.set_state(3, diff)
-    err = math.sqrt(scratch.energy() / E0)
+    err = math.sqrt(g.error_energy(_exact_q3(g.nodes(3), T, sigma)) / E0)
     g.close()
-    scratch.close()
     return err
 
 

@@ -254,3 +254,18 @@ def test_parity_single_hexahedron(prec):
     Y, _, _ = o.run(Y, 0.0, dt, 30)
     g.step(30)
     assert_close(rel_errors(gpu_levels(g), Y), 1e-5 if prec == dgh.PREC_FP32 else 5e-5)
+
+
+@pytest.mark.parametrize("N", [2, 6])
+def test_error_energy_matches_oracle(N):
+    """The device error reduction E(q - ref) equals the oracle's energy of the
+    same difference (FP64 on both sides, same inputs)."""
+    m, o, g, dt = make_pair(2, N, 1, jitter=0.03, seed=30 + N)
+    Y = o.gaussian_state([0.1, -0.2, 0.05], 0.4)
+    g.init_gaussian([0.1, -0.2, 0.05], 0.4)
+    g.step(7)
+    ref = W.random_state(55, Y["q3"].shape) * 0.1 + Y["q3"]
+    diff = g.get_state(3) - ref
+    Eo = o.energy({"q3": diff, "q2": np.zeros_like(Y["q2"]), "q1": np.zeros_like(Y["q1"])})
+    Eg = g.error_energy(ref)
+    assert abs(Eg - Eo) <= 1e-11 * Eo
