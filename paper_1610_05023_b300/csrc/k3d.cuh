@@ -35,7 +35,7 @@ struct Cfg3 {
     static constexpr int NP = (N + 1) * (N + 2) * (N + 3) / 6;
     static constexpr int NFP = (N + 1) * (N + 2) / 2;
     static constexpr int NF = 4 * NFP;
-    static constexpr int NW = N == 1 ? 1 : N == 2 ? 2 : N == 3 ? 4 : N == 4 ? 5 : 7;  // warps per CTA
+    static constexpr int NW = N == 1 ? 1 : N == 2 ? 2 : N == 3 ? 5 : N == 4 ? 9 : N == 5 ? 14 : 7;  // warps per CTA
     static constexpr int C = (NP + NW - 1) / NW;       // output nodes per warp
     static constexpr int CP = (C + 3) / 4 * 4;         // padded to float4
     static constexpr int MAXSLOT = 3;                  // a node lies on at most 3 faces
@@ -45,10 +45,10 @@ struct Cfg3 {
     static constexpr int CS = 4 * 32;                  // connectivity of one block (ints)
     static constexpr int STAGE = QS + TI + GS + CS;    // one pipeline stage (4-byte words)
     static constexpr int SPW = (NF + NW - 1) / NW;     // face slots per warp
-    static constexpr int NSTAGE = (N >= 6 || N == 3 || N == 4) ? 1 : 2;   // input pipeline depth (N = 6: no room for two; N = 3, 4: one more CTA per SM instead)
+    static constexpr int NSTAGE = (N >= 6 || N == 3) ? 1 : 2;   // input pipeline depth (N = 6: no room for two; N = 3: one more CTA per SM instead)
     static constexpr int SM_WORDS = NP * 3 * NW * CP + NF * NW * CP + NSTAGE * STAGE + 3 * NP * 32 + NF + 6 * NFP + NP * MAXSLOT;
     static constexpr size_t SMEM = 16 + sizeof(float) * SM_WORDS;  // 16: two mbarriers
-    static constexpr int MINB = N <= 3 ? 4 : N == 4 ? 3 : N == 5 ? 2 : 1;
+    static constexpr int MINB = N <= 3 ? 4 : N == 4 ? 2 : 1;
 };
 
 struct Args3 {
