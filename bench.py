@@ -438,6 +438,151 @@ def run_closure_form(args):
         np.save(args.closure_weights_out, w)
 
 
+def _ricker(t, f, ts):
+    a = (math.pi * f * (t - ts)) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def _ricker_integral(t, f, ts):
+    return (t - ts) * np.exp(-(math.pi * f * (t - ts)) ** 2)
+
+
+def _point_source_fields(x, xs, t, f, ts):
+    """Free-space field of a point source S(t) delta(x - xs) in the pressure
+    equation, rho = c = 1 (Sec. 4.1): p = s(t - r) / (4 pi r) with s = S' the
+    Ricker wavelet, u = x^ [s(t - r) / (4 pi r) + S(t - r) / (4 pi r^2)]
+    (from rho du/dt = -grad p).  x [K][Np][3] -> [K][4][Np]."""
+    d = x - np.asarray(xs)
+    r = np.maximum(np.linalg.norm(d, axis=-1), 1e-12)
+    s_ = _ricker(t - r, f, ts)
+    S_ = _ricker_integral(t - r, f, ts)
+    p = s_ / (4 * math.pi * r)
+    ur = s_ / (4 * math.pi * r) + S_ / (4 * math.pi * r * r)
+    q = np.empty((x.shape[0], 4, x.shape[1]))
+    q[:, 0] = p
+    for i in range(3):
+        q[:, 1 + i] = ur * d[..., i] / r
+    return q
+
+
+def run_validation_form(args):
+    """Validation study of the paper (Sec. 4.1): Omega = [-0.5, 0.5]^3, here
+    23^3 x 6 = 73,002 Kuhn tets (jitter 2% h, standing in for the paper's
+    70,895-tet mesh), degree 3, rho = c = 1, Ricker source f_peak = 2.5,
+    t_s = 0.5 at (0, 0, 0) and at (0.2, 0.1, 0), HABC order P = 0 (basic ABC),
+    2, ..., 12, t in [0, 5].  Error(t)^2 = energy of (computed - analytic free-
+    space field) / E_src, outside the ball of radius 0.15 around the source
+    (where the analytic field is singular), E_src = the largest energy of the
+    analytic field in that region over the sampled times."""
+    import torch
+    import paper_1610_05023_b300 as dgh
+    from paper_1610_05023_b300 import workloads as W
+    torch.cuda.set_device(0)
+    n, f, ts, T, r_ex = 23, 2.5, 0.5, 5.0, 0.15
+    VX, EToV = W.kuhn_mesh(n, 0.5, 0.02, seed=6000)
+    cen = VX[EToV].mean(axis=1)
+    times = [0.25 * (i + 1) for i in range(20)]
+    out = {}
+    for xs in ([0.0, 0.0, 0.0], [0.2, 0.1, 0.0]):
+        excl = np.linalg.norm(cen - np.asarray(xs), axis=1) < r_ex
+        x = None
+        E_src = 0.0
+        refs = []
+        for P in (0, 2, 4, 6, 8, 10, 12):
+            st = torch.cuda.Stream()
+            g = dgh.Solver(VX, EToV, 3, P, stream=st)
+            if x is None:
+                x = g.nodes(3)
+                zero = dgh.Solver(VX, EToV, 3, 0)
+                for t in times:
+                    a = _point_source_fields(x, xs, t, f, ts)
+                    a[excl] = 0.0
+                    refs.append(a)
+                    E_src = max(E_src, zero.error_energy(a))       # energy of the analytic field
+                zero.close()
+            g.add_point_source(xs, f, ts)
+            g.init_gaussian(xs, 0.1, 0.0)
+            dt = g.info["dt"]
+            errs, t_now, ms = [], 0.0, []
+            for t, a in zip(times, refs):
+                k = int(round((t - t_now) / dt))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                g.step(k)
+                e1.record(st)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1) / max(k, 1))
+                t_now += k * dt
+                q = g.get_state(3)
+                ref = a.copy()
+                ref[excl] = q[excl]
+                errs.append(math.sqrt(max(g.error_energy(ref), 0.0) / E_src))
+            out.setdefault(str(xs), {})["P=%d" % P] = {
+                "error_max_t>=1.5": max(e for t, e in zip(times, errs) if t >= 1.5), "error_at_T": errs[-1],
+                "curve": errs, "ms_per_step": float(np.median(ms)), "ndof": g.info["ndof"], "dt": dt}
+            g.close()
+    line = {"form": "validation", "metric": "Error(t), energy norm relative to E_src",
+            "config": {"mesh": "23^3 hex x 6 Kuhn tets (73002) on [-0.5,0.5]^3, jitter 2% h", "N": 3,
+                       "source": "Ricker f_peak 2.5, t_s 0.5", "T": T, "times": times, "exclusion_radius": r_ex},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_seam_form(args):
+    """HABC overhead on a heterogeneous stand-in for the paper's SEAM run
+    (Sec. 4.2, Table 3): box [-1.75,1.75] x [-2,2] x [-0.75,0.75], 56 x 64 x 24
+    hexahedra x 6 = 516,096 tets (jitter 2% h), degree 3, three horizontal
+    layers (c, rho) = (3.5, 2.4), (2.5, 2.1), (1.5, 1.8) bottom to top, a fast
+    inclusion (c, rho) = (4.5, 2.6) touching the +x face, free surface (p = 0)
+    on top, HABC of order P = 0 (basic ABC), 3, 6 elsewhere, Ricker source
+    near the top.  Reports time per step and unknowns per P."""
+    import torch
+    import paper_1610_05023_b300 as dgh
+    from paper_1610_05023_b300 import workloads as W
+    torch.cuda.set_device(0)
+    VX, EToV = W.kuhn_mesh((56, 64, 24), (1.75, 2.0, 0.75), 0.02, seed=7000)
+    cen = VX[EToV].mean(axis=1)
+    z = cen[:, 2]
+    c = np.where(z < -0.25, 3.5, np.where(z < 0.25, 2.5, 1.5))
+    rho = np.where(z < -0.25, 2.4, np.where(z < 0.25, 2.1, 1.8))
+    inc = (cen[:, 0] > 1.0) & (np.abs(cen[:, 1]) < 0.5) & (z > -0.4) & (z < 0.1)
+    c[inc], rho[inc] = 4.5, 2.6
+    bc = (0, 0, 0, 0, 0, 1)
+    rows = {}
+    for P in (0, 3, 6):
+        st = torch.cuda.Stream()
+        g = dgh.Solver(VX, EToV, 3, P, bc=bc, c=c, rho=rho, stream=st)
+        g.add_point_source([0.0, 0.0, 0.6], 3.0, 0.4)
+        g.init_gaussian([0.0, 0.0, 0.6], 0.1, 0.0)
+        g.tune(steps=3)
+        g.step(args.warmup)
+        g.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.step(args.steps)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        info = g.info
+        rows["P=%d" % P] = {"ms_per_step": ms, "ndof": info["ndof"], "n_tris": info["n_tris"],
+                            "n_lines": info["n_lines"], "n_corners": info["n_corners"], "dt": info["dt"],
+                            "dof_updates_per_s": info["ndof"] * 5 / (ms * 1e-3)}
+        g.close()
+    base = rows["P=0"]
+    for r in rows.values():
+        r["time_overhead_vs_abc"] = r["ms_per_step"] / base["ms_per_step"] - 1.0
+        r["unknowns_overhead_vs_abc"] = r["ndof"] / base["ndof"] - 1.0
+    line = {"form": "seam", "metric": "time per step and unknowns, HABC vs basic ABC",
+            "config": {"mesh": "56 x 64 x 24 hex x 6 Kuhn tets (516096), [-1.75,1.75]x[-2,2]x[-0.75,0.75]",
+                       "N": 3, "bc": "free surface on +z, HABC elsewhere", "steps": args.steps},
+            "results": rows,
+            "paper_context": {"runtime_overhead_P3": 534.75 / 524.83 - 1.0,
+                              "runtime_overhead_P6": 547.72 / 524.83 - 1.0,
+                              "unknowns_overhead_P3": 96573304 / 94399120 - 1.0,
+                              "unknowns_overhead_P6": 98795296 / 94399120 - 1.0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,7 +597,7 @@ def main():
     ap.add_argument("--closure-eval-n", type=int, default=40)
     ap.add_argument("--closure-steps", type=int, default=4000)
     ap.add_argument("--closure-weights-out", default="", help="save the trained closure weights (.npy)")
-    ap.add_argument("--form", default="plain", choices=["plain", "batch", "precision", "closure"],
+    ap.add_argument("--form", default="plain", choices=["plain", "batch", "precision", "closure", "validation", "seam"],
                     help="batch: the batching form (48 independent problems); precision: the N = 6 layered "
                          "workload with the FP32 and tensor-core 3D kernels")
     args = ap.parse_args()
@@ -467,6 +612,10 @@ def main():
         return run_precision_form(args)
     if args.form == "closure":
         return run_closure_form(args)
+    if args.form == "validation":
+        return run_validation_form(args)
+    if args.form == "seam":
+        return run_seam_form(args)
 
     import torch
     import paper_1610_05023_b300 as dgh
@@ -524,6 +673,11 @@ def main():
     bytes_per_tet = 4 * (16 * Np + 16 * Nfp) + 100          # algorithmic bytes per tet per stage
     achieved = K * bytes_per_tet / (kt["k3d"] * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    # the FP32 compute bound: 12 Np^2 + 32 Np Nfp algorithmic flops per tet per stage
+    # against the probe-measured FP32 CUDA-core peak of this GPU
+    flops_per_tet = 12 * Np * Np + 32 * Np * Nfp
+    fp32_ach = K * flops_per_tet / (kt["k3d"] * 1e-3) / 1e12
+    fp32_scalar, fp32_packed = dgh.fp32_probe()
 
     # end to end through the public API: host initial state in, host fields out,
     # both in pinned host memory (allocated and filled outside the timed region)
@@ -559,6 +713,10 @@ def main():
                      "frac": achieved / peak, "traffic": K3D_TRAFFIC_BYTES if args.n == 48 else None,
                      "traffic_over_algorithmic": K3D_TRAFFIC_BYTES / (K * bytes_per_tet) if args.n == 48 else None,
                      "kernel": "k3d_stage<4>",
+                     "fp32": {"achieved_tflops": fp32_ach, "flops_per_tet": flops_per_tet,
+                              "peak_tflops": max(fp32_scalar, fp32_packed), "peak_kind": "measured (own FFMA probe)",
+                              "probe_ffma_tflops": fp32_scalar, "probe_ffma2_tflops": fp32_packed,
+                              "frac": fp32_ach / max(fp32_scalar, fp32_packed)},
                      "peak_kind": peak_kind, "bytes_per_tet": bytes_per_tet,
                      "launch_ms": kt["k3d"]},
         "kernel_ms": kt,

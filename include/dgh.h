@@ -83,7 +83,7 @@ typedef struct dgh_ctx dgh_ctx;
 /* Problem description (all pointers: host, read during dgh_create only). */
 typedef struct dgh_desc {
     int32_t        order;        /* N, 1..6                                     */
-    int32_t        habc_order;   /* P, 0..8 (common to all HABC faces)           */
+    int32_t        habc_order;   /* P, 0..12 (common to all HABC faces)          */
     int32_t        bc[6];        /* DGH_BC_* per domain face                     */
     int32_t        precision;    /* DGH_PREC_* (batches group problems by N, P and precision) */
     int32_t        reserved0;
@@ -209,6 +209,12 @@ int dgh_get_error_energy(dgh_ctx *ctx, const double *ref, size_t count, double *
  *  call, nothing needs clearing), so calls whose kernels overlap on the GPU
  *  -- e.g. on two streams at once -- race and must be serialised. */
 int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stream);
+
+/* FP32 CUDA-core throughput probe on the current device (the roofline's
+ * compute bound for the FP32 path): TFLOP/s of scalar FFMA and of packed
+ * FP32x2 FMA chains (8 independent chains per thread, all SMs, best of
+ * three timed launches).  Errors via dgh_last_error(NULL). */
+int dgh_fp32_probe(double *tflops_ffma, double *tflops_ffma2);
 
 /* Failure-detection self-test: a one-thread kernel waits, with the bounded
  * wait of the stage kernels and a limit of `limit` polls, on an mbarrier

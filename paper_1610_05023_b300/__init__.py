@@ -120,6 +120,7 @@ def load_library(path=LIB_PATH):
         "dgh_batch_get_launch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_Launch)]),
         "dgh_batch_tune": (ctypes.c_int, [P, ctypes.c_int, D, D]),
         "dgh_selftest_wait": (ctypes.c_int, [P, ctypes.c_int64]),
+        "dgh_fp32_probe": (ctypes.c_int, [D, D]),
         "dgh_clear_error": (ctypes.c_int, [P]),
         "dgh_closure_set_weights": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
         "dgh_closure_record": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
@@ -161,6 +162,14 @@ def _f32(a, shape=None):
 def _lib_check(rc):
     if rc != DGH_OK:
         raise DghError(rc, load_library().dgh_last_error(None).decode())
+
+
+def fp32_probe():
+    """Measured FP32 CUDA-core TFLOP/s (scalar FFMA, packed FP32x2 FMA) of the current device."""
+    lib = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _lib_check(lib.dgh_fp32_probe(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def closure_eval(w, X):

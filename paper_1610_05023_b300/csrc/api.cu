@@ -793,7 +793,7 @@ static int validate_desc(const dgh_desc *d) {
         return DGH_EINVAL;
     }
     if (d->order < 1 || d->order > 6 || d->habc_order < 0 || d->habc_order > MAXP) {
-        g_create_error = "order N must be 1..6 and HABC order P 0..8";
+        g_create_error = "order N must be 1..6 and HABC order P 0..12";
         return DGH_EUNSUPPORTED;
     }
     if (d->precision != DGH_PREC_FP32 && d->precision != DGH_PREC_BF16_TC && d->precision != DGH_PREC_FP16_TC &&
@@ -2290,7 +2290,7 @@ int dgh_closure_record(dgh_ctx *ctx, int shadow_order, int every, double fractio
         return DGH_ESTATE;
     }
     if (shadow_order < 1 || shadow_order > MAXP || every < 1 || !(fraction > 0.0 && fraction <= 1.0) || max_samples < 1) {
-        ctx->err = "record: shadow order 1..8, every >= 1, 0 < fraction <= 1, max_samples >= 1";
+        ctx->err = "record: shadow order 1..12, every >= 1, 0 < fraction <= 1, max_samples >= 1";
         return DGH_EINVAL;
     }
     if (ctx->P < 1 || ctx->T == 0) {
@@ -2556,6 +2556,74 @@ __global__ void k_selftest_wait(int *err, unsigned long long limit) {
 }
 
 }  // namespace
+
+namespace {
+
+// FP32 throughput probes: 8 independent FMA chains per thread (scalar or
+// packed FP32x2), enough CTAs to fill every SM; the result is stored only
+// under a condition that never holds, so the chains stay live.
+__global__ void __launch_bounds__(256) k_probe_ffma(float *out, int iters, float sink) {
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = threadIdx.x * 1e-7f + j;
+    const float b = 0.999999f, c = 1e-7f;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fmaf(a[j], b, c);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == sink) out[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) k_probe_ffma2(float *out, int iters, float sink) {
+    float2 a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = make_float2(threadIdx.x * 1e-7f + j, threadIdx.x * 2e-7f + j);
+    const float2 b = make_float2(0.999999f, 0.999998f), c = make_float2(1e-7f, 2e-7f);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = __ffma2_rn(a[j], b, c);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j].x + a[j].y;
+    if (s == sink) out[blockIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" int dgh_fp32_probe(double *tflops_ffma, double *tflops_ffma2) {
+    if (!tflops_ffma || !tflops_ffma2) return mlp_fail("fp32 probe: null output", DGH_EINVAL);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    DevScratch d;
+    float *out = d.get<float>(size_t(sms) * 64);
+    cudaEvent_t e0, e1;
+    if (!out || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return mlp_fail("fp32 probe: set-up failed", DGH_ECUDA);
+    const int blocks = sms * 8, iters = 1 << 14;
+    double best[2] = {0.0, 0.0};
+    for (int kind = 0; kind < 2; ++kind)
+        for (int rep = 0; rep < 4; ++rep) {   // first repetition warms up
+            cudaEventRecord(e0);
+            if (kind == 0) k_probe_ffma<<<blocks, 256>>>(out, iters, -1.f);
+            else k_probe_ffma2<<<blocks, 256>>>(out, iters, -1.f);
+            cudaEventRecord(e1);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double fma = double(blocks) * 256 * iters * 8 * (kind == 0 ? 1 : 2);
+            if (rep > 0) best[kind] = std::max(best[kind], 2.0 * fma / (ms * 1e-3) / 1e12);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return mlp_fail(std::string("fp32 probe: ") + cudaGetErrorString(e), DGH_ECUDA);
+    *tflops_ffma = best[0];
+    *tflops_ffma2 = best[1];
+    return DGH_OK;
+}
 
 extern "C" int dgh_selftest_wait(dgh_ctx *ctx, int64_t limit) {
     if (!ctx || limit < 1) return DGH_EINVAL;

@@ -32,7 +32,7 @@ struct Ord {
 
 constexpr int GEO2 = 28;   // per tri: drdx[4], 3 x (nx,ny,fscale,wm,zz,iz), rho c^2, 1/rho, Z, pad[3]
 constexpr int GEO1 = 16;   // per line: rx, fscale, rho c^2, 1/rho, Z, ZA, ZB, 2 x (wm,zz,iz), pad[3]
-constexpr int MAXP = 8;
+constexpr int MAXP = 12;
 constexpr int MAXSRC = 64;
 
 struct SrcParams {

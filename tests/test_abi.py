@@ -120,7 +120,7 @@ def test_plan_rejects_edge_inputs():
     assert code() == 0
     assert code(patch={"n_cells": 0}) == -1                     # empty mesh
     assert code(patch={"n_cells": (1 << 26) + 1}) == -7          # beyond the 32-bit connectivity encoding
-    assert code(P=9) == -7                                       # HABC order above 8
+    assert code(P=13) == -7                                      # HABC order above 12
     assert code(N=0) == -7
     assert code(precision=7) == -7                               # unknown precision code
     assert code(bc=(0, 0, 0, 0, 0, 5)) == -1                     # unknown boundary code

@@ -115,7 +115,7 @@ def test_parity_small_gaussian_all_levels():
     assert abs(g.info["time"] - t) < 1e-12
 
 
-@pytest.mark.parametrize("N,P", [(1, 1), (2, 2), (3, 1), (4, 3), (5, 2), (6, 2)])
+@pytest.mark.parametrize("N,P", [(1, 1), (2, 2), (3, 1), (4, 3), (5, 2), (6, 2), (2, 12), (3, 9)])
 def test_parity_orders_random_state(N, P):
     """Random smooth-in-time start of every level (all auxiliary paths active
     from step 0), 10 steps."""
