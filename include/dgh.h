@@ -235,8 +235,8 @@ int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size);
 /* ---------------------------------------------------------------- launch shapes
  * Launch shape of the stage kernels: the number of elements a CTA handles,
  * which the paper tunes per kernel as K_blk (Sec. 3.3, Tables 4-5), and the
- * number of persistent 3D CTAs.  tile2 = triangles per CTA of the 2D kernel,
- * tile1 = line cells per CTA of the 1D kernel, cta3_per_sm = persistent 3D
+ * number of persistent 3D CTAs.  tile2 = triangles per CTA of the 2D kernel
+ * (one thread per triangle and HABC set: tile2 * P <= thr2), tile1 = line cells per CTA of the 1D kernel, cta3_per_sm = persistent 3D
  * CTAs per SM (0 = as many as fit).  grid3/grid2/grid1 (CTAs per launch),
  * occ3 (3D CTAs that fit on one SM) and sms are derived, read only.  A 3D
  * CTA always handles 32-cell blocks (one cell per lane). */
@@ -250,8 +250,8 @@ int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *out);
 
 /* Sets tile2, tile1, cta3_per_sm, thr2 and thr1 (the other fields are ignored).  No
  * result changes: every element's arithmetic is the same whatever the shape.
- * DGH_EINVAL if a value is out of range or the tile does not fit in shared
- * memory (the previous shape is kept). */
+ * DGH_EINVAL if a value is out of range, tile2 * P > thr2, or a tile does not
+ * fit in shared memory (the previous shape is kept). */
 int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in);
 
 /* Autotuner: coordinate search over thr2, tile2, thr1, tile1 and cta3_per_sm, each

@@ -91,7 +91,7 @@ struct dgh_ctx {
     // launch shapes
     int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0, sms = 1;
     int cta3_per_sm = 0;              // tunable: persistent 3D CTAs per SM (0 = occupancy limit)
-    int thr2 = 256, thr1 = 256;       // tunable: threads per CTA of the 2D / 1D kernels
+    int thr2 = 128, thr1 = 256;       // tunable: threads per CTA of the 2D / 1D kernels
     int precision = DGH_PREC_FP32;    // arithmetic of the 3D contractions (DGH_PREC_*)
     uint8_t *tcops = nullptr;         // tensor-core operand images of D_r, D_s, D_t, LIFT (hi, then lo)
     unsigned long long *tile_ctr = nullptr;   // [11] block counters of the 3D launches of a step
@@ -516,6 +516,7 @@ struct Shapes {
         c->smem1 = P ? k1d_smem(N, P, c->tile1) : 0;
         c->smem0 = sizeof(float) * 3 * P * P;
         if ((int64_t)c->smem2 > c->smem_optin || (int64_t)c->smem1 > c->smem_optin) return DGH_EINVAL;
+        if (P && c->tile2 * P > c->thr2) return DGH_EINVAL;   // one thread per (triangle, set)
         const int sms = c->sms;
         const int per_sm = c->cta3_per_sm > 0 ? std::min(c->cta3_per_sm, std::max(c->occ3, 1)) : std::max(c->occ3, 1);
         const int64_t tiles3 = c->precision == DGH_PREC_FP32 ? c->K32 : (c->K32 + 3) / 4;
@@ -1176,7 +1177,8 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
     ctx->energy_blocks = 2 * 148;
     if ((rc = dalloc(ctx, ctx->partial, ctx->energy_blocks))) return fail(rc, "");
     // launch shapes
-    ctx->tile2 = std::max(1, 256 / std::max(1, P * Np2));
+    ctx->thr2 = 128;
+    ctx->tile2 = k2d_tile_max(P, ctx->thr2);
     ctx->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
     dispatchN<SetAttrs>(N, ctx);
     if ((rc = dispatchN<Shapes>(N, ctx))) return fail(DGH_EUNSUPPORTED, "2D/1D tile does not fit in shared memory");
@@ -1678,7 +1680,7 @@ int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in) {
         ctx->thr2 = h2;
         ctx->thr1 = h1;
         dispatchN<Shapes>(ctx->N, ctx);
-        ctx->err = "launch shape does not fit in shared memory";
+        ctx->err = "launch shape does not fit (shared memory, or tile2 * P > thr2)";
         return DGH_EINVAL;
     }
     drop_graphs(ctx);
@@ -1755,10 +1757,12 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
                 for (int v = 1; v <= 32 && v <= c->L; v *= 2) cand.push_back(v);
             if (param == 4)
                 for (int v = 0; v <= c->occ3; ++v) cand.push_back(v);
-            int keep = *slot;
+            if (param == 1 && c->T > 0) cand.push_back(k2d_tile_max(c->P, c->thr2));
+            int keep = *slot, keep_tile2 = c->tile2;
             for (int v : cand) {
                 if (v == keep) continue;
                 *slot = v;
+                if (param == 0) c->tile2 = k2d_tile_max(c->P, v);   // a 2D thread count comes with its largest tile
                 if (dispatchN<Shapes>(c->N, c) != DGH_OK) continue;
                 invalidate();
                 double ms = 0.0;
@@ -1766,9 +1770,11 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
                 if (ms < 0.99 * best) {
                     best = ms;
                     keep = v;
+                    keep_tile2 = c->tile2;
                 }
             }
             *slot = keep;
+            c->tile2 = param == 1 ? keep : keep_tile2;
             dispatchN<Shapes>(c->N, c);
             invalidate();
         }
@@ -2327,7 +2333,7 @@ int dgh_closure_record(dgh_ctx *ctx, int shadow_order, int every, double fractio
     h->every = every;
     h->threshold = fraction >= 1.0 ? 0xFFFFFFFFu : uint32_t(fraction * 4294967296.0);
     h->seed = seed;
-    h->tile2 = std::max(1, 256 / std::max(1, P * Np2));
+    h->tile2 = k2d_tile_max(P, 256);
     h->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
     h->smem2 = k2d_smem(N, P, h->tile2);
     h->smem1 = k1d_smem(N, P, h->tile1);

@@ -115,154 +115,276 @@ __device__ __forceinline__ double ricker_integral_d(double t, double f, double t
 namespace dgh {
 
 // ==================================================================== 2D
-// One block handles a tile of triangles; items are (tri, set, node).
+// One thread per (triangle, set) item: its p*, v1, v2 at the NP2 nodes live in
+// registers, the volume and lift operators are read as broadcast float4 rows
+// from shared memory, and every global array of a tile (fields, residuals,
+// traces) is a contiguous block moved by the whole CTA with 16-byte
+// asynchronous copies / vector stores.  A CTA handles tile_tris triangles at a
+// time (tile_tris * P <= blockDim.x).
+// Small-integer division s / P for s < 2^12, P <= 12: the fractional part of
+// (s + 0.5) / P lies in [0.5 / P, 1 - 0.5 / P], far from the float rounding.
+__device__ __forceinline__ int div_small(int s, float inv) { return __float2int_rz((float(s) + 0.5f) * inv); }
+
+// Asynchronous global -> shared copies (no register round trip): a tile's
+// loads are all in flight at once; cp_async_wait_all before the barrier.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Copies g[start, start + count) to s[sh, sh + count), sh = start mod 4, so
+// that global and shared addresses agree mod 16 bytes and the body moves
+// float4s (s is 16-byte aligned, with 4 floats of slack).  Returns sh.
+__device__ __forceinline__ int block_load_async(float *s, const float *g, int64_t start, int count, int tid, int nth) {
+    const int sh = (int)(start & 3);
+    const int head = min(count, (4 - sh) & 3);
+    const int body = (count - head) >> 2;
+    const int tail = count - head - 4 * body;
+    float *d = s + sh;
+    const float *src = g + start;
+    if (tid < head) cp_async4(d + tid, src + tid);
+    for (int i = tid; i < body; i += nth) cp_async16(d + head + 4 * i, src + head + 4 * i);
+    if (tid < tail) cp_async4(d + head + 4 * body + tid, src + head + 4 * body + tid);
+    return sh;
+}
+
+// The reverse of block_load_async: s[sh, sh + count) -> g[start, ...).
+__device__ __forceinline__ void block_store(float *g, const float *s, int64_t start, int count, int tid, int nth) {
+    const int sh = (int)(start & 3);
+    const int head = min(count, (4 - sh) & 3);
+    const int body = (count - head) >> 2;
+    const int tail = count - head - 4 * body;
+    const float *src = s + sh;
+    float *d = g + start;
+    if (tid < head) d[tid] = src[tid];
+    for (int i = tid; i < body; i += nth)
+        *reinterpret_cast<float4 *>(d + head + 4 * i) = *reinterpret_cast<const float4 *>(src + head + 4 * i);
+    if (tid < tail) d[head + 4 * body + tid] = src[head + 4 * body + tid];
+}
+
+template <int N>
+struct Cfg2 {
+    static constexpr int NP2 = Ord<N>::NP2, NFP2 = Ord<N>::NFP2, NE = 3 * NFP2;
+    static constexpr int NPP = (NP2 + 3) / 4 * 4;   // operator rows padded to float4
+    static constexpr int NEP = (NE + 3) / 4 * 4;
+    static constexpr int F = 3 * NP2;                 // (p*, v1, v2) of one item
+    static constexpr int TR = 6 * NFP2;               // traces of one item: [3 edges][p, v.n][Nfp2]
+};
+
+// Shared-memory carve-up of k2d_stage (float offsets; every array 16-byte aligned).
+struct Smem2 {
+    int dt, lt, cp, q, res, g, q0, trb, r, face, fm, total;
+    __host__ __device__ Smem2(int NP2, int NFP2, int P, int tile) {
+        auto al = [](int x) { return (x + 3) & ~3; };
+        const int NE = 3 * NFP2, NPP = al(NP2), NEP = al(NE), F = 3 * NP2;
+        dt = 0;
+        lt = dt + 2 * NP2 * NPP;
+        cp = lt + NP2 * NEP;
+        q = cp + 2 * 16;                       // c_a and 1 / (1 + c_a), a < MAXP
+        res = q + al(tile * P * F + 4);
+        g = res + al(tile * P * F + 4);
+        q0 = g + tile * GEO2;
+        trb = q0 + al(tile * NP2 + 4);
+        r = trb + al(tile * 2 * NP2);
+        face = r + al(tile * 2 * NP2);
+        fm = face + al(tile);
+        total = fm + al(NE);
+    }
+};
+
 template <int N, bool UPDATE>
 __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile_tris) {
-    using O = Ord<N>;
-    constexpr int NP2 = O::NP2, NFP2 = O::NFP2, NE = 3 * NFP2;
+    using C = Cfg2<N>;
+    constexpr int NP2 = C::NP2, NFP2 = C::NFP2, NE = C::NE, NPP = C::NPP, NEP = C::NEP, F = C::F, TR = C::TR;
     const int P = A.P;
-    extern __shared__ float sm[];
-    float *sD = sm;                                   // 2*NP2*NP2
-    float *sL = sD + 2 * NP2 * NP2;                   // NE*NP2
-    float *sq = sL + NE * NP2;                        // tile*P*3*NP2 (p*, v1, v2)
-    float *sp = sq + tile_tris * P * 3 * NP2;         // tile*P*NP2 full p
-    float *sx = sp + tile_tris * P * NP2;             // tile*P*2*NE
-    float *sg = sx + tile_tris * P * 2 * NE;          // tile*GEO2
-    float *s0 = sg + tile_tris * GEO2;                // tile*NP2 q0
-    float *sn = s0 + tile_tris * NP2;                 // tile*P*3*NP2 new (p*, v1, v2)
-    float *sr = sn + tile_tris * P * 3 * NP2;         // tile*P*NP2 dp*/dt of this stage (closure features)
-    float *sres = sr + tile_tris * P * NP2;           // tile*P*3*NP2 residuals (update only)
-    float *sxin = sres + tile_tris * P * 3 * NP2;     // tile*P*NE*2 exterior (p, v.n) at the edge nodes (update only)
-    float *strb = sxin + tile_tris * P * NE * 2;      // tile*2*NP2 own 3D traces of the triangle
-    int *sfm = reinterpret_cast<int *>(strb + tile_tris * 2 * NP2);
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const float invP = 1.0f / float(P);
+    extern __shared__ float4 sm4[];
+    float *sm = reinterpret_cast<float *>(sm4);
+    const Smem2 L(NP2, NFP2, P, tile_tris);
+    float *sDT = sm + L.dt;                           // [2][n][m]: D[d][m][n] (output row n)
+    float *sLT = sm + L.lt;                           // [n][em]: LIFT[em][n]
+    float *scp = sm + L.cp;                           // c_a, then 1 / (1 + c_a)
+    float *sqb = sm + L.q;                            // fields of the tile (+ alignment shift), updated in place
+    float *srb = sm + L.res;                          // residuals of the tile (same shift), updated in place
+    float *sg = sm + L.g;                             // tile*GEO2
+    float *s0b = sm + L.q0;                           // q0 (+ shift)
+    float *strb = sm + L.trb;                         // tile*2*NP2 own 3D traces of the triangle
+    float *sr = sm + L.r;                             // tile*2*NP2 dp*/dt of sets 0, 1 (closure features)
+    int *sface = reinterpret_cast<int *>(sm + L.face);
+    int *sfm = reinterpret_cast<int *>(sm + L.fm);
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = (nth + 31) >> 5;
     if (UPDATE) {
-        for (int i = tid; i < 2 * NP2 * NP2; i += nth) sD[i] = A.D[i];
-        for (int i = tid; i < NE * NP2; i += nth) sL[i] = A.LIFT[i];
+        for (int i = tid; i < 2 * NP2 * NPP; i += nth) {
+            const int d = i / (NP2 * NPP), r = i % (NP2 * NPP), n = r / NPP, m = r % NPP;
+            sDT[i] = m < NP2 ? A.D[(d * NP2 + m) * NP2 + n] : 0.f;
+        }
+        for (int i = tid; i < NP2 * NEP; i += nth) {
+            const int n = i / NEP, em = i % NEP;
+            sLT[i] = em < NE ? A.LIFT[em * NP2 + n] : 0.f;
+        }
+    }
+    for (int i = tid; i < P; i += nth) {
+        scp[i] = A.cP[i];
+        scp[16 + i] = 1.0f / (1.0f + A.cP[i]);
     }
     for (int i = tid; i < NE; i += nth) sfm[i] = A.fmask[i];
     const int64_t ntiles = (A.T + tile_tris - 1) / tile_tris;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t t0 = tile * tile_tris;
         const int nt = (int)((A.T - t0) < tile_tris ? (A.T - t0) : tile_tris);
+        const int nitem = nt * P;
         __syncthreads();
-        // every global input of the tile in one phase (one memory round trip):
-        // fields, residuals, geometry, q0, the exterior states at the edge
-        // nodes (neighbour traces / edge characteristic) and the own 3D traces
-        for (int i = tid; i < nt * P * 3 * NP2; i += nth) {
-            sq[i] = A.q[t0 * P * 3 * NP2 + i];
-            if (UPDATE) sres[i] = A.res[t0 * P * 3 * NP2 + i];
-        }
-        for (int i = tid; i < nt * GEO2; i += nth) sg[i] = A.geo[t0 * GEO2 + i];
-        for (int i = tid; i < nt * NP2; i += nth) s0[i] = A.q0[t0 * NP2 + i];
+        // every global input of the tile in one phase: contiguous blocks by the
+        // whole CTA, the exterior states at the edge nodes by each item thread
+        const int shq = block_load_async(sqb, A.q, t0 * P * F, nitem * F, tid, nth);
+        if (UPDATE) block_load_async(srb, A.res, t0 * P * F, nitem * F, tid, nth);
+        const int sh0 = block_load_async(s0b, A.q0, t0 * NP2, nt * NP2, tid, nth);
+        block_load_async(sg, A.geo, t0 * GEO2, nt * GEO2, tid, nth);   // GEO2 = 28: no shift
+        if (A.tin3 && tid < nt) cp_async4(sface + tid, A.tri_face + t0 + tid);
         for (int i = tid; i < nt * 2 * NP2; i += nth) {
             const int t = i / (2 * NP2), r = i % (2 * NP2);
-            strb[i] = A.trb[(int64_t)A.tri_bface[t0 + t] * 2 * NP2 + r];
+            cp_async4(strb + i, A.trb + (int64_t)A.tri_bface[t0 + t] * 2 * NP2 + r);
         }
-        if (UPDATE) {
-            for (int i = tid; i < nt * P * NE; i += nth) {
-                const int t = i / (P * NE), r = i % (P * NE), a = r / NE, em = r % NE, e = em / NFP2, m = em % NFP2;
-                const int64_t tg = t0 + t;
+        float *sq = sqb + shq, *sres = srb + shq, *s0 = s0b + sh0;
+        const bool act = tid < nitem;
+        const int t = act ? div_small(tid, invP) : 0, a = tid - t * P;
+        float xp[NE], xv[NE];   // exterior (p, v.n) at the edge nodes
+        int ce[3];
+        if (UPDATE && act) {
+            const int64_t tg = t0 + t;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
                 const int c = A.conn[tg * 3 + e];
-                float pp = 0.f, vnp = 0.f;
+                ce[e] = c;
                 if (c >= 0) {
-                    const int nb = c >> 1;
-                    const int mm = (c & 1) ? (NFP2 - 1 - m) : m;
-                    const int tn = nb / 3, en = nb % 3;
+                    const int nb = c >> 1, tn = nb / 3, en = nb - 3 * tn;
                     const float *tr = A.tr_in + (((int64_t)tn * P + a) * 3 + en) * 2 * NFP2;
-                    pp = tr[mm];
-                    vnp = -tr[NFP2 + mm];
-                } else if (c != -2) {
-                    pp = 2.0f * A.qb[((tg * 3 + e) * P + a) * NFP2 + m];
+#pragma unroll
+                    for (int m = 0; m < NFP2; ++m) {
+                        const int mm = (c & 1) ? (NFP2 - 1 - m) : m;
+                        xp[e * NFP2 + m] = tr[mm];
+                        xv[e * NFP2 + m] = -tr[NFP2 + mm];
+                    }
+                } else {
+                    const float *qb = A.qb + ((tg * 3 + e) * P + a) * NFP2;
+#pragma unroll
+                    for (int m = 0; m < NFP2; ++m) {
+                        xp[e * NFP2 + m] = c != -2 ? 2.0f * qb[m] : 0.f;
+                        xv[e * NFP2 + m] = 0.f;
+                    }
                 }
-                sxin[2 * i] = pp;
-                sxin[2 * i + 1] = vnp;
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (UPDATE && act) {
+            const float *g = sg + t * GEO2;
+            float *qa = sq + tid * F;
+            float *ra = sres + tid * F;
+            const float *q0t = s0 + t * NP2;
+            float p[NP2], w1[NP2], w2[NP2];
+            const float g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
+#pragma unroll
+            for (int n = 0; n < NP2; ++n) {
+                p[n] = qa[n] + q0t[n];
+                const float v1 = qa[NP2 + n], v2 = qa[2 * NP2 + n];
+                w1[n] = g0 * v1 + g1 * v2;
+                w2[n] = g2 * v1 + g3 * v2;
+            }
+            // upwind flux differences at the edge nodes, scaled by the edge Fscale
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const float nx = g[4 + 6 * e], ny = g[5 + 6 * e], fs = g[6 + 6 * e];
+                const float wm = g[7 + 6 * e], zz = g[8 + 6 * e], iz = g[9 + 6 * e];
+#pragma unroll
+                for (int m = 0; m < NFP2; ++m) {
+                    const int em = e * NFP2 + m, n = sfm[em];
+                    const float pm = qa[n] + q0t[n];
+                    const float vnm = nx * qa[NP2 + n] + ny * qa[2 * NP2 + n];
+                    float pp = xp[em], vnp = xv[em];
+                    if (ce[e] == -2) {   // p = 0 edge: mirror state
+                        pp = -pm;
+                        vnp = vnm;
+                    }
+                    const float dP = wm * (pp - pm) + zz * (vnm - vnp);
+                    const float dVn = (1.0f - wm) * (vnp - vnm) + iz * (pm - pp);
+                    xv[em] = fs * dVn;
+                    xp[em] = fs * dP;
+                }
+            }
+            const float rc2 = g[22], irho = g[23];
+            const float cw = -rc2 * scp[16 + a];
+            const float nx0 = g[4], ny0 = g[5], nx1 = g[10], ny1 = g[11], nx2 = g[16], ny2 = g[17];
+#pragma unroll 1
+            for (int n = 0; n < NP2; ++n) {
+                const float4 *dr4 = reinterpret_cast<const float4 *>(sDT + n * NPP);
+                const float4 *ds4 = reinterpret_cast<const float4 *>(sDT + (NP2 + n) * NPP);
+                float div = 0.f, dpr = 0.f, dps = 0.f;
+#pragma unroll
+                for (int k = 0; k < NPP / 4; ++k) {
+                    const float4 r4 = dr4[k], s4 = ds4[k];
+                    const float rv[4] = {r4.x, r4.y, r4.z, r4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int m = 4 * k + j;
+                        if (m < NP2) {
+                            div += rv[j] * w1[m] + sv[j] * w2[m];
+                            dpr += rv[j] * p[m];
+                            dps += sv[j] * p[m];
+                        }
+                    }
+                }
+                const float4 *l4 = reinterpret_cast<const float4 *>(sLT + n * NEP);
+                float lvn = 0.f, lp0 = 0.f, lp1 = 0.f, lp2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < NEP / 4; ++k) {
+                    const float4 L4 = l4[k];
+                    const float lv[4] = {L4.x, L4.y, L4.z, L4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int em = 4 * k + j;
+                        if (em < NE) {
+                            lvn += lv[j] * xv[em];
+                            if (em < NFP2) lp0 += lv[j] * xp[em];
+                            else if (em < 2 * NFP2) lp1 += lv[j] * xp[em];
+                            else lp2 += lv[j] * xp[em];
+                        }
+                    }
+                }
+                float rhs[3];
+                rhs[0] = cw * (div + lvn);
+                rhs[1] = -irho * (g0 * dpr + g2 * dps + nx0 * lp0 + nx1 * lp1 + nx2 * lp2);
+                rhs[2] = -irho * (g1 * dpr + g3 * dps + ny0 * lp0 + ny1 * lp1 + ny2 * lp2);
+                if (a < 2) sr[t * 2 * NP2 + a * NP2 + n] = rhs[0];
+#pragma unroll
+                for (int fl = 0; fl < 3; ++fl) {
+                    const float rr = sc.a * ra[fl * NP2 + n] + sc.dt * rhs[fl];
+                    ra[fl * NP2 + n] = rr;
+                    qa[fl * NP2 + n] += sc.b * rr;
+                }
             }
         }
         __syncthreads();
-        if (UPDATE) {
-            for (int i = tid; i < nt * P * NP2; i += nth) {
-                const int t = i / (P * NP2), r = i % (P * NP2), a = r / NP2, n = r % NP2;
-                sp[i] = sq[(t * P + a) * 3 * NP2 + n] + s0[t * NP2 + n];
-            }
-            __syncthreads();
-            // edge flux differences
-            for (int i = tid; i < nt * P * NE; i += nth) {
-                const int t = i / (P * NE), r = i % (P * NE), a = r / NE, em = r % NE, e = em / NFP2, m = em % NFP2;
-                const int n = sfm[em];
-                const float *g = sg + t * GEO2;
-                const float *qa = sq + (t * P + a) * 3 * NP2;
-                const float nx = g[4 + 6 * e], ny = g[5 + 6 * e];
-                const float pm = sp[(t * P + a) * NP2 + n];
-                const float vnm = nx * qa[NP2 + n] + ny * qa[2 * NP2 + n];
-                const int64_t tg = t0 + t;
-                const int c = A.conn[tg * 3 + e];
-                float pp = sxin[2 * i], vnp = sxin[2 * i + 1];
-                if (c == -2) {   // p = 0 edge: mirror state
-                    pp = -pm;
-                    vnp = vnm;
-                }
-                const float fs = g[6 + 6 * e], wm = g[7 + 6 * e], zz = g[8 + 6 * e], iz = g[9 + 6 * e];
-                const float dP = wm * (pp - pm) + zz * (vnm - vnp);
-                const float dVn = (1.0f - wm) * (vnp - vnm) + iz * (pm - pp);
-                sx[(t * P + a) * 2 * NE + em] = fs * dVn;
-                sx[(t * P + a) * 2 * NE + NE + em] = fs * dP;
-            }
-            __syncthreads();
-            // volume + lift + update
-            for (int i = tid; i < nt * P * NP2; i += nth) {
-                const int t = i / (P * NP2), r = i % (P * NP2), a = r / NP2, n = r % NP2;
-                const float *g = sg + t * GEO2;
-                const float *qa = sq + (t * P + a) * 3 * NP2;
-                const float *pa = sp + (t * P + a) * NP2;
-                float div = 0.f, dpr = 0.f, dps = 0.f;
-                for (int m = 0; m < NP2; ++m) {
-                    const float dr = sD[m * NP2 + n], ds = sD[(NP2 + m) * NP2 + n];
-                    const float v1 = qa[NP2 + m], v2 = qa[2 * NP2 + m];
-                    div += dr * (g[0] * v1 + g[1] * v2) + ds * (g[2] * v1 + g[3] * v2);
-                    dpr += dr * pa[m];
-                    dps += ds * pa[m];
-                }
-                const float *xa = sx + (t * P + a) * 2 * NE;
-                float lvn = 0.f, lp[3] = {0.f, 0.f, 0.f};
-                for (int e = 0; e < 3; ++e)
-                    for (int m = 0; m < NFP2; ++m) {
-                        const float l = sL[(e * NFP2 + m) * NP2 + n];
-                        lvn += l * xa[e * NFP2 + m];
-                        lp[e] += l * xa[NE + e * NFP2 + m];
-                    }
-                const float rc2 = g[22], irho = g[23];
-                const float wa = 1.0f / (1.0f + A.cP[a]);
-                float rhs[3];
-                rhs[0] = -rc2 * wa * (div + lvn);
-                rhs[1] = -irho * (g[0] * dpr + g[2] * dps + g[4] * lp[0] + g[10] * lp[1] + g[16] * lp[2]);
-                rhs[2] = -irho * (g[1] * dpr + g[3] * dps + g[5] * lp[0] + g[11] * lp[1] + g[17] * lp[2]);
-                const int64_t base = ((t0 + t) * P + a) * 3 * NP2;
-                sr[(t * P + a) * NP2 + n] = rhs[0];
-                for (int fl = 0; fl < 3; ++fl) {
-                    const float rr = sc.a * sres[(t * P + a) * 3 * NP2 + fl * NP2 + n] + sc.dt * rhs[fl];
-                    A.res[base + fl * NP2 + n] = rr;
-                    const float qv = qa[fl * NP2 + n] + sc.b * rr;
-                    A.q[base + fl * NP2 + n] = qv;
-                    sn[(t * P + a) * 3 * NP2 + fl * NP2 + n] = qv;
-                }
-            }
-            __syncthreads();
-            for (int i = tid; i < nt * P * 3 * NP2; i += nth) sq[i] = sn[i];
-            __syncthreads();
-        }
         // face BC: r^+ from the new 3D traces, r^- = (1/M) sum c_a p*_a, q0 = r^- + r^+
         for (int i = tid; i < nt * NP2; i += nth) {
-            const int t = i / NP2, n = i % NP2;
-            const int64_t tg = t0 + t;
-            const float *tr = strb + t * 2 * NP2;   // own tet face traces (Nfp == Np2)
-            const float Z = sg[t * GEO2 + 24];
+            const int tt = i / NP2, n = i % NP2;
+            const int64_t tg = t0 + tt;
+            const float *tr = strb + tt * 2 * NP2;   // own tet face traces (Nfp == Np2)
+            const float Z = sg[tt * GEO2 + 24];
             const float rp = 0.5f * (tr[n] + Z * tr[NP2 + n]);
             float rm = 0.f;
-            for (int a = 0; a < P; ++a) rm += A.cP[a] * sq[(t * P + a) * 3 * NP2 + n];
+            const float *qn = sq + tt * P * F + n;
+#pragma unroll
+            for (int b = 0; b < MAXP; ++b)
+                if (b < P) rm += scp[b] * qn[b * F];
             rm *= A.invM;
             if (A.tin3) {
-                const int64_t gf = A.tri_face[tg], kc = gf >> 2;
+                const int64_t gf = sface[tt], kc = gf >> 2;
                 const int fc = (int)(gf & 3);
                 A.tin3[(((kc >> 5) * 4 + fc) * 2 * NP2 + n) * 32 + (kc & 31)] = 2.0f * rm;   // exterior p; n.u = 0
             }
@@ -272,34 +394,42 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
                 float *f = A.feat + (tg * NP2 + n) * 6;
                 f[0] = tr[n];
                 f[1] = tr[NP2 + n];
-                f[2] = P >= 1 ? sq[(t * P + 0) * 3 * NP2 + n] + q0 : 0.f;
-                f[3] = P >= 2 ? sq[(t * P + 1) * 3 * NP2 + n] + q0 : 0.f;
-                f[4] = (UPDATE && P >= 1) ? sr[(t * P + 0) * NP2 + n] : 0.f;
-                f[5] = (UPDATE && P >= 2) ? sr[(t * P + 1) * NP2 + n] : 0.f;
+                f[2] = P >= 1 ? sq[(tt * P + 0) * F + n] + q0 : 0.f;
+                f[3] = P >= 2 ? sq[(tt * P + 1) * F + n] + q0 : 0.f;
+                f[4] = (UPDATE && P >= 1) ? sr[tt * 2 * NP2 + n] : 0.f;
+                f[5] = (UPDATE && P >= 2) ? sr[tt * 2 * NP2 + NP2 + n] : 0.f;
             }
-            A.q0[tg * NP2 + n] = q0;
-            s0[t * NP2 + n] = q0;
+            s0[tt * NP2 + n] = q0;
         }
         __syncthreads();
-        // new 2D traces (full pressure, in-plane normal velocity)
-        for (int i = tid; i < nt * P * NE; i += nth) {
-            const int t = i / (P * NE), r = i % (P * NE), a = r / NE, em = r % NE, e = em / NFP2, m = em % NFP2;
-            const int n = sfm[em];
-            const float *g = sg + t * GEO2;
-            const float *qa = sq + (t * P + a) * 3 * NP2;
-            float *dst = A.tr_out + (((t0 + t) * P + a) * 3 + e) * 2 * NFP2;
-            dst[m] = qa[n] + s0[t * NP2 + n];
-            dst[NFP2 + m] = g[4 + 6 * e] * qa[NP2 + n] + g[5 + 6 * e] * qa[2 * NP2 + n];
+        // write-back: fields, residuals and q0 (contiguous blocks), new 2D
+        // traces (full pressure, in-plane normal velocity), one warp per item
+        // over its contiguous [3][2][Nfp2] block
+        if (UPDATE) {
+            block_store(A.q, sqb, t0 * P * F, nitem * F, tid, nth);
+            block_store(A.res, srb, t0 * P * F, nitem * F, tid, nth);
+        }
+        block_store(A.q0, s0b, t0 * NP2, nt * NP2, tid, nth);
+        for (int r = lane; r < TR; r += 32) {   // lane-constant part of the trace slot r
+            const int e = r / (2 * NFP2), k = r % (2 * NFP2), isp = k < NFP2;
+            const int n = sfm[e * NFP2 + (isp ? k : k - NFP2)];
+            const float *ge = sg + 4 + 6 * e;
+            float *gt = A.tr_out + t0 * P * TR + r;
+            for (int s = warp; s < nitem; s += nwarp) {
+                const int tt = div_small(s, invP);
+                const float *qa = sq + s * F + n;
+                gt[s * TR] = isp ? qa[0] + s0[tt * NP2 + n] : ge[tt * GEO2] * qa[NP2] + ge[tt * GEO2 + 1] * qa[2 * NP2];
+            }
         }
     }
 }
 
 inline size_t k2d_smem(int N, int P, int tile) {
-    const int NP2 = (N + 1) * (N + 2) / 2, NFP2 = N + 1, NE = 3 * NFP2;
-    return sizeof(float) * (2 * NP2 * NP2 + NE * NP2 +
-                            tile * (3 * P * 3 * NP2 + 2 * P * NP2 + 2 * P * 2 * NE + GEO2 + NP2 + 2 * NP2)) +
-           sizeof(int) * NE;
+    return sizeof(float) * (size_t)Smem2((N + 1) * (N + 2) / 2, N + 1, P, tile).total;
 }
+
+// Triangles per CTA of the 2D kernel: one thread per (triangle, set).
+inline int k2d_tile_max(int P, int thr) { return P > 0 ? (thr / P > 0 ? thr / P : 1) : 1; }
 
 // ==================================================================== 1D
 template <int N, bool UPDATE>

@@ -151,4 +151,6 @@ def test_set_launch_rejects_bad_shapes():
         g.set_launch(tile2=100000)   # shared memory of the 2D tile does not fit
     with pytest.raises(dgh.DghError):
         g.set_launch(thr2=48)
+    with pytest.raises(dgh.DghError):
+        g.set_launch(tile2=17, thr2=32)   # one thread per (triangle, set): 17 * 2 > 32
     assert g.launch == before
