@@ -446,6 +446,11 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
     float *sg = s0 + tile_lines * 2 * P * NP1;        // tile*GEO1
     float *sn = sg + tile_lines * GEO1;               // tile*S*2*NP1 new (p*, w)
     float *sH = sn + tile_lines * S * 2 * NP1;        // 2P*2P + 2P*S
+    float *srp = sH + 4 * P * P + 2 * P * S;          // tile*NP1*2P  r^+ of the 2D fields of faces A, B
+    float *sres = srp + tile_lines * NP1 * 2 * P;     // tile*S*2*NP1 residuals (update only)
+    float *sxe = sres + tile_lines * S * 2 * NP1;     // tile*S*2*2   exterior (p, w.n) at the two ends (update only)
+    int *smp = reinterpret_cast<int *>(sxe + tile_lines * S * 4);   // tile*6 line map
+    int *scn = smp + tile_lines * 6;                  // tile*2 end connectivity
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < NP1 * NP1; i += nth) sD[i] = A.D[i];
     for (int i = tid; i < 2 * NP1; i += nth) sL[i] = A.LIFT[i];
@@ -459,6 +464,38 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
         for (int i = tid; i < nl * S * 2 * NP1; i += nth) sq[i] = A.q[l0 * S * 2 * NP1 + i];
         for (int i = tid; i < nl * 2 * P * NP1; i += nth) s0[i] = A.q0[l0 * 2 * P * NP1 + i];
         for (int i = tid; i < nl * GEO1; i += nth) sg[i] = A.geo[l0 * GEO1 + i];
+        for (int i = tid; i < nl * 6; i += nth) smp[i] = A.lmap[l0 * 6 + i];
+        if (UPDATE) {
+            for (int i = tid; i < nl * S * 2 * NP1; i += nth) sres[i] = A.res[l0 * S * 2 * NP1 + i];
+            for (int i = tid; i < nl * 2; i += nth) scn[i] = A.conn[l0 * 2 + i];
+        }
+        __syncthreads();
+        // gathers through the index arrays (one more memory round trip): r^+ of
+        // the faces' new 2D traces at the line nodes, exterior states at the ends
+        for (int i = tid; i < nl * NP1 * 2 * P; i += nth) {
+            const int l = i / (NP1 * 2 * P), r = i % (NP1 * 2 * P), n = r / (2 * P), j = r % (2 * P);
+            const int side = j >= P, a = j - side * P;
+            const int *mp = smp + l * 6 + 3 * side;
+            const int m = mp[2] ? (N - n) : n;
+            const float Z = sg[l * GEO1 + 5 + side];
+            const float *tr = A.tr2 + (((int64_t)mp[0] * P + a) * 3 + mp[1]) * 2 * NP1;
+            srp[i] = 0.5f * (tr[m] + Z * tr[NP1 + m]);
+        }
+        if (UPDATE)
+            for (int i = tid; i < nl * S * 2; i += nth) {
+                const int l = i / (S * 2), r = i % (S * 2), s2 = r / 2, e = r % 2;
+                const int c = scn[l * 2 + e];
+                float pp = 0.f, wnp = 0.f;
+                if (c >= 0) {
+                    const float *tr = A.tr_in + ((int64_t)(c >> 1) * S + s2) * 4 + (c & 1) * 2;
+                    pp = tr[0];
+                    wnp = -tr[1];
+                } else if (c != -2) {
+                    pp = 2.0f * A.qb[((l0 + l) * 2 + e) * S + s2];
+                }
+                sxe[2 * i] = pp;
+                sxe[2 * i + 1] = wnp;
+            }
         __syncthreads();
         if (UPDATE) {
             // full p_ab = p*_ab + C_ba q0_A,a + C_ab q0_B,b
@@ -472,24 +509,15 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
             __syncthreads();
             for (int i = tid; i < nl * S * 2; i += nth) {
                 const int l = i / (S * 2), r = i % (S * 2), s = r / 2, e = r % 2;
-                const int64_t lg = l0 + l;
                 const float *g = sg + l * GEO1;
                 const int nd = e ? N : 0;
                 const float tau = e ? 1.0f : -1.0f;
                 const float pm = sp[(l * S + s) * NP1 + nd];
                 const float wnm = tau * sq[(l * S + s) * 2 * NP1 + NP1 + nd];
-                const int c = A.conn[lg * 2 + e];
-                float pp, wnp;
-                if (c >= 0) {
-                    const float *tr = A.tr_in + ((int64_t)(c >> 1) * S + s) * 4 + (c & 1) * 2;
-                    pp = tr[0];
-                    wnp = -tr[1];
-                } else if (c == -2) {
+                float pp = sxe[2 * i], wnp = sxe[2 * i + 1];
+                if (scn[l * 2 + e] == -2) {   // p = 0 end: mirror state
                     pp = -pm;
                     wnp = wnm;
-                } else {
-                    pp = 2.0f * A.qb[(lg * 2 + e) * S + s];
-                    wnp = 0.0f;
                 }
                 const float wm = g[7 + 3 * e], zz = g[8 + 3 * e], iz = g[9 + 3 * e];
                 const float dP = wm * (pp - pm) + zz * (wnm - wnp);
@@ -519,7 +547,7 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
                 rhs[1] = -g[3] * (g[0] * dp + lpp);
                 const int64_t base = ((l0 + l) * S + s) * 2 * NP1;
                 for (int fl = 0; fl < 2; ++fl) {
-                    const float rr = sc.a * A.res[base + fl * NP1 + n] + sc.dt * rhs[fl];
+                    const float rr = sc.a * sres[(l * S + s) * 2 * NP1 + fl * NP1 + n] + sc.dt * rhs[fl];
                     A.res[base + fl * NP1 + n] = rr;
                     const float qv = qs[fl * NP1 + n] + sc.b * rr;
                     A.q[base + fl * NP1 + n] = qv;
@@ -530,34 +558,23 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
             for (int i = tid; i < nl * S * 2 * NP1; i += nth) sq[i] = sn[i];
             __syncthreads();
         }
-        // edge BCs: one thread per (line, node)
-        for (int i = tid; i < nl * NP1; i += nth) {
-            const int l = i / NP1, n = i % NP1;
+        // edge BCs: one thread per (line, node, row) of the solution operator
+        for (int i = tid; i < nl * NP1 * 2 * P; i += nth) {
+            const int l = i / (NP1 * 2 * P), r = i % (NP1 * 2 * P), n = r / (2 * P), row = r % (2 * P);
             const int64_t lg = l0 + l;
-            const int *mp = A.lmap + lg * 6;
-            float rp[2 * MAXP];
-            for (int side = 0; side < 2; ++side) {
-                const int tri = mp[3 * side], e = mp[3 * side + 1], rev = mp[3 * side + 2];
-                const int m = rev ? (N - n) : n;
-                const float Z = sg[l * GEO1 + 5 + side];
-                for (int a = 0; a < P; ++a) {
-                    const float *tr = A.tr2 + (((int64_t)tri * P + a) * 3 + e) * 2 * NP1;
-                    rp[side * P + a] = 0.5f * (tr[m] + Z * tr[NP1 + m]);
-                }
-            }
-            const float *H1 = sH, *H2 = sH + 4 * P * P;
-            for (int row = 0; row < 2 * P; ++row) {
-                float x = 0.f;
-                for (int col = 0; col < 2 * P; ++col) x += H1[row * 2 * P + col] * rp[col];
-                for (int s = 0; s < S; ++s) x += H2[row * S + s] * sq[(l * S + s) * 2 * NP1 + n];
-                const int side = row / P, a = row % P;
-                const int tri = mp[3 * side], e = mp[3 * side + 1], rev = mp[3 * side + 2];
-                const int m = rev ? (N - n) : n;
-                A.qb2[(((int64_t)tri * 3 + e) * P + a) * NP1 + m] = x;
-                const float q0 = x + rp[row];
-                A.q0[(lg * 2 + side) * P * NP1 + a * NP1 + n] = q0;
-                s0[(l * 2 + side) * P * NP1 + a * NP1 + n] = q0;
-            }
+            const float *rp = srp + (l * NP1 + n) * 2 * P;
+            const float *H1 = sH + row * 2 * P, *H2 = sH + 4 * P * P + row * S;
+            const float *qn = sq + l * S * 2 * NP1 + n;
+            float x = 0.f;
+            for (int col = 0; col < 2 * P; ++col) x += H1[col] * rp[col];
+            for (int s2 = 0; s2 < S; ++s2) x += H2[s2] * qn[s2 * 2 * NP1];
+            const int side = row >= P, a = row - side * P;
+            const int *mp = smp + l * 6 + 3 * side;
+            const int m = mp[2] ? (N - n) : n;
+            A.qb2[(((int64_t)mp[0] * 3 + mp[1]) * P + a) * NP1 + m] = x;
+            const float q0 = x + rp[row];
+            A.q0[(lg * 2 + side) * P * NP1 + a * NP1 + n] = q0;
+            s0[(l * 2 + side) * P * NP1 + a * NP1 + n] = q0;
         }
         __syncthreads();
         // new 1D traces (full p_ab, tangential velocity along the outward end direction)
@@ -579,7 +596,8 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
 inline size_t k1d_smem(int N, int P, int tile) {
     const int NP1 = N + 1, S = P * P;
     return sizeof(float) * (NP1 * NP1 + 2 * NP1 + tile * (2 * S * 2 * NP1 + S * NP1 + S * 4 + 2 * P * NP1 + GEO1) +
-                            4 * P * P + 2 * P * S);
+                            4 * P * P + 2 * P * S + tile * NP1 * 2 * P + tile * S * 2 * NP1 + tile * S * 4) +
+           sizeof(int) * tile * 8;
 }
 
 // ==================================================================== 0D
