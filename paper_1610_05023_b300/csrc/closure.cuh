@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const f
             const int node = (int)(r % np2);
             const int64_t gf = tri_face[t], kc = gf >> 2;
             const int fc = (int)(gf & 3);
-            tin3[(((kc >> 5) * 4 + fc) * 2 * np2 + node) * 32 + (kc & 31)] = 2.0f * (rm[r] + y);
+            tin3[((((kc >> 5) * 4 + fc) * np2 + node) * 32 + (kc & 31)) * 2] = 2.0f * (rm[r] + y);
         }
     }
 }

@@ -46,14 +46,16 @@ struct Cfg3 {
     static constexpr int STAGE = QS + TI + GS + CS;    // one pipeline stage (4-byte words)
     static constexpr int SPW = (NF + NW - 1) / NW;     // face slots per warp
     static constexpr int NSTAGE = (N >= 6 || N == 3) ? 1 : 2;   // input pipeline depth (N = 6: no room for two; N = 3: one more CTA per SM instead)
-    static constexpr int SM_WORDS = NP * 3 * NW * CP + NF * NW * CP + NSTAGE * STAGE + 3 * NP * 32 + NF + 6 * NFP + NP * MAXSLOT;
+    static constexpr bool PQ = N == 4 || N == 5;      // (p, f_r, f_s, f_t) interleaved per lane: one float4 load per node
+    static constexpr int SF = (PQ ? 4 : 3) * NP * 32;  // contravariant fluxes (N = 3: spills at 4 CTAs per SM; N = 6: no room)
+    static constexpr int SM_WORDS = NP * 3 * NW * CP + NF * NW * CP + NSTAGE * STAGE + SF + NF + 6 * NFP + NP * MAXSLOT;
     static constexpr size_t SMEM = 16 + sizeof(float) * SM_WORDS;  // 16: two mbarriers
     static constexpr int MINB = N <= 3 ? 4 : N == 4 ? 2 : 1;
 };
 
 struct Args3 {
     float *q, *res;          // [K32][4][Np][32]
-    const float *tin;        // incoming traces read this stage  [K32][4][2][Nfp][32]
+    const float *tin;        // incoming traces read this stage  [K32][4][Nfp][32][2] (p, n.u) pairs
     float *tout;             // incoming traces written for the next stage
     float *trb;              // own traces of boundary faces [Fb][2][Nfp]
     const float *geo;        // [K32][GEO3][32]
@@ -147,8 +149,8 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
     float *sD = reinterpret_cast<float *>(smraw + 16);  // NP*3*NW*CP
     float *sL = sD + NP * 3 * NW * CP;                  // NF*NW*CP
     float *sS = sL + NF * NW * CP;                      // NSTAGE pipeline stages
-    float *sF = sS + G::NSTAGE * G::STAGE;              // [3][NP][32] contravariant fluxes
-    int *sFm = reinterpret_cast<int *>(sF + 3 * NP * 32);
+    float *sF = sS + G::NSTAGE * G::STAGE;              // [NP][32](p, f_r, f_s, f_t) (N = 4, 5), else [3][NP][32] fluxes
+    int *sFm = reinterpret_cast<int *>(sF + G::SF);
     int *sFp = sFm + NF;
     int *sNs = sFp + 6 * NFP;
     const int tid = threadIdx.x, nth = NW * 32;
@@ -220,27 +222,32 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
                     const int n = sFm[f * NFP + m];
                     const float pm = sQ[n * 32 + e];
                     const float unm = nx * sQ[(NP + n) * 32 + e] + ny * sQ[(2 * NP + n) * 32 + e] + nz * sQ[(3 * NP + n) * 32 + e];
-                    float *xp_slot = sTi + ((2 * f) * NFP + m) * 32 + e;       // p slot -> Fscale dP
-                    float *xu_slot = sTi + ((2 * f + 1) * NFP + m) * 32 + e;   // n.u slot -> Fscale dUn
-                    float pp = *xp_slot, unp = *xu_slot;
+                    float2 *x_slot = reinterpret_cast<float2 *>(sTi) + (f * NFP + m) * 32 + e;   // (p, n.u) -> Fscale (dP, dUn)
+                    const float2 xin = *x_slot;
+                    float pp = xin.x, unp = xin.y;
                     if (dir) {   // p = 0 face: mirror state
                         pp = -pm;
                         unp = unm;
                     }
                     const float dP = wm * (pp - pm) + zz * (unm - unp);
                     const float dUn = (1.0f - wm) * (unp - unm) + izs * (pm - pp);
-                    *xu_slot = fsc * dUn;
-                    *xp_slot = fsc * dP;
+                    *x_slot = make_float2(fsc * dP, fsc * dUn);
                 }
             }
         }
-        __syncthreads();
-        // ---------------- contravariant fluxes f_j = sum_i dr_j/dx_i u_i
+        // ---------------- contravariant fluxes f_j = sum_i dr_j/dx_i u_i (same phase:
+        // the flux terms are read only by the lift, after the volume term)
         for (int n = w; n < NP; n += NW) {
             const float u = sQ[(NP + n) * 32 + e], v = sQ[(2 * NP + n) * 32 + e], ww = sQ[(3 * NP + n) * 32 + e];
-            sF[n * 32 + e] = g[0] * u + g[1] * v + g[2] * ww;
-            sF[(NP + n) * 32 + e] = g[3] * u + g[4] * v + g[5] * ww;
-            sF[(2 * NP + n) * 32 + e] = g[6] * u + g[7] * v + g[8] * ww;
+            const float fr = g[0] * u + g[1] * v + g[2] * ww, fs = g[3] * u + g[4] * v + g[5] * ww,
+                        ft = g[6] * u + g[7] * v + g[8] * ww;
+            if (G::PQ) {
+                reinterpret_cast<float4 *>(sF)[n * 32 + e] = make_float4(sQ[n * 32 + e], fr, fs, ft);
+            } else {
+                sF[n * 32 + e] = fr;
+                sF[(NP + n) * 32 + e] = fs;
+                sF[(2 * NP + n) * 32 + e] = ft;
+            }
         }
         __syncthreads();
         // ---------------- volume term for the chunk of warp w
@@ -252,7 +259,19 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
         const float4 *D4 = reinterpret_cast<const float4 *>(sD) + w * (CP / 4);
 #pragma unroll 5
         for (int m = 0; m < NP; ++m) {
-            const float p = sQ[m * 32 + e], fr = sF[m * 32 + e], fs = sF[(NP + m) * 32 + e], ft = sF[(2 * NP + m) * 32 + e];
+            float p, fr, fs, ft;
+            if (G::PQ) {
+                const float4 v = reinterpret_cast<const float4 *>(sF)[m * 32 + e];
+                p = v.x;
+                fr = v.y;
+                fs = v.z;
+                ft = v.w;
+            } else {
+                p = sQ[m * 32 + e];
+                fr = sF[m * 32 + e];
+                fs = sF[(NP + m) * 32 + e];
+                ft = sF[(2 * NP + m) * 32 + e];
+            }
             const float2 p2 = make_float2(p, p), fr2 = make_float2(fr, fr), fs2 = make_float2(fs, fs), ft2 = make_float2(ft, ft);
             const float4 *Dm = D4 + m * 3 * NW * (CP / 4);
 #pragma unroll
@@ -306,7 +325,8 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
 #pragma unroll 5
             for (int m = 0; m < NFP; ++m) {
                 const int fm = f * NFP + m;
-                const float xu = sTi[((2 * f + 1) * NFP + m) * 32 + e], xp = sTi[((2 * f) * NFP + m) * 32 + e];
+                const float2 xpu = reinterpret_cast<const float2 *>(sTi)[(f * NFP + m) * 32 + e];
+                const float xu = xpu.y, xp = xpu.x;
                 const float2 xu2 = make_float2(xu, xu), xp2 = make_float2(xp, xp);
                 const float4 *Lm = L4 + fm * NW * (CP / 4);
 #pragma unroll
@@ -383,9 +403,7 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
                     const int64_t kn = nb >> 2;
                     const int fn = nb & 3;
                     const int mn = sFp[(cc & 7) * NFP + m];
-                    float *d = A.tout + (((kn >> 5) * 4 + fn) * 2 * NFP) * 32 + (kn & 31);
-                    d[mn * 32] = qn[0];
-                    d[(NFP + mn) * 32] = -un;
+                    reinterpret_cast<float2 *>(A.tout)[(((kn >> 5) * 4 + fn) * NFP + mn) * 32 + (kn & 31)] = make_float2(qn[0], -un);
                 } else {         // boundary face: own trace for the face HABC solver
                     const int64_t b = (-1 - cc) >> 1;
                     A.trb[b * 2 * NFP + m] = qn[0];
@@ -399,7 +417,9 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
             s_blk[st] = b;
             if (b < ntiles) issue_tile<N>(A, sS + st * G::STAGE, &bar[st], b);
         }
-        __syncthreads();
+        // With two stages, s_blk[st] is next read two iterations later, after
+        // the barrier of the iteration in between; one stage needs a barrier.
+        if (G::NSTAGE == 1) __syncthreads();
     }
 }
 
@@ -430,9 +450,7 @@ __global__ void __launch_bounds__(128) k3d_traces(const float *q, const float *g
         const int64_t kn = nb >> 2;
         const int fn = nb & 3;
         const int mn = fperm[(cc & 7) * NFP + m];
-        float *d = tout + (((kn >> 5) * 4 + fn) * 2 * NFP) * 32 + (kn & 31);
-        d[mn * 32] = p;
-        d[(NFP + mn) * 32] = -un;
+        reinterpret_cast<float2 *>(tout)[(((kn >> 5) * 4 + fn) * NFP + mn) * 32 + (kn & 31)] = make_float2(p, -un);
     } else {
         const int64_t b = (-1 - cc) >> 1;
         trb[b * 2 * NFP + m] = p;

@@ -277,8 +277,9 @@ __global__ void __launch_bounds__(256, 1) k3d_tc(Args3 A, StageCoef sc, const ui
                     const int n = ok ? sFm[f * NFP + m] : 0;
 #pragma unroll
                     for (int fl = 0; fl < 4; ++fl) v[6 * k + fl] = ok ? qb[(fl * NP + n) * 32 + lane] : 0.f;
-                    v[6 * k + 4] = ok ? tb[((2 * f) * NFP + m) * 32 + lane] : 0.f;
-                    v[6 * k + 5] = ok ? tb[((2 * f + 1) * NFP + m) * 32 + lane] : 0.f;
+                    const float2 pu = ok ? reinterpret_cast<const float2 *>(tb)[(f * NFP + m) * 32 + lane] : make_float2(0.f, 0.f);
+                    v[6 * k + 4] = pu.x;
+                    v[6 * k + 5] = pu.y;
                 }
             }
         };
@@ -482,9 +483,8 @@ __global__ void __launch_bounds__(256, 1) k3d_tc(Args3 A, StageCoef sc, const ui
                                 const int64_t kn = nb >> 2;
                                 const int fn = nb & 3;
                                 const int mn = sFp[(cc & 7) * NFP + m];
-                                float *d = tout + (((kn >> 5) * 4 + fn) * 2 * NFP) * 32 + (kn & 31);
-                                d[mn * 32] = qn[0];
-                                d[(NFP + mn) * 32] = -un;
+                                reinterpret_cast<float2 *>(tout)[(((kn >> 5) * 4 + fn) * NFP + mn) * 32 + (kn & 31)] =
+                                    make_float2(qn[0], -un);
                             } else {
                                 const int64_t b = (-1 - cc) >> 1;
                                 trb[b * 2 * NFP + m] = qn[0];

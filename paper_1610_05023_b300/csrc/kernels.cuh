@@ -56,7 +56,7 @@ struct Args2 {
     const int *conn;        // >=0: (t'*3+e')<<1 | flip ; -1: HABC edge (qb2) ; -2: Dirichlet edge
     const float *qb;        // [T][3][P][Nfp2]  incoming 2D characteristic at domain-edge nodes
     float *q0;              // [T][Np2]         r^- + r^+ of the 3D field at the triangle nodes
-    float *tin3;            // out: 3D incoming traces [K32][4][2][Nfp][32], exterior state (2 r^-, 0); NULL: not written
+    float *tin3;            // out: 3D incoming traces [K32][4][Nfp][32][2], exterior state (2 r^-, 0); NULL: not written
     float *feat;            // out (optional): closure features per triangle node [T][Np2][6]
     float *rm_out;          // out (optional): r^- per triangle node [T][Np2]
     const float *trb;       // own 3D traces of the boundary faces [Fb][2][Nfp]
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
             if (A.tin3) {
                 const int64_t gf = sface[tt], kc = gf >> 2;
                 const int fc = (int)(gf & 3);
-                A.tin3[(((kc >> 5) * 4 + fc) * 2 * NP2 + n) * 32 + (kc & 31)] = 2.0f * rm;   // exterior p; n.u = 0
+                A.tin3[((((kc >> 5) * 4 + fc) * NP2 + n) * 32 + (kc & 31)) * 2] = 2.0f * rm;   // exterior p; n.u = 0
             }
             const float q0 = rm + rp;
             if (A.rm_out) A.rm_out[tg * NP2 + n] = rm;
