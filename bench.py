@@ -33,7 +33,7 @@ METRIC = "DOF-updates/s per RK stage"
 SEED = 2000
 # dram__bytes_read.sum + dram__bytes_write.sum of k3d_stage<4> for one full stage (interior and
 # boundary-cell launches) of this workload, from one ncu capture of this build (one pass)
-K3D_TRAFFIC_BYTES = 2119630592 + 85365504
+K3D_TRAFFIC_BYTES = 2092811264 + 71113984
 
 
 def build_inputs(n=48):
