@@ -387,6 +387,12 @@ struct Launch2 {
         sc.c_dt = 0.0;
         sc.time = c->d_time;
         Args2 A = args2(c, cur, update, shadow);
+        // the kernel moves these arrays with 16-byte copies from 16-byte aligned bases
+        if ((reinterpret_cast<uintptr_t>(A.q) | reinterpret_cast<uintptr_t>(A.res) | reinterpret_cast<uintptr_t>(A.q0) |
+             reinterpret_cast<uintptr_t>(A.geo)) & 15u) {
+            c->err = "2D level arrays are not 16-byte aligned";
+            return DGH_EINVAL;
+        }
         const int grid = shadow ? c->sh->grid2 : c->grid2, tile = shadow ? c->sh->tile2 : c->tile2;
         const int thr = shadow ? 256 : c->thr2;
         const size_t smem = shadow ? c->sh->smem2 : c->smem2;
