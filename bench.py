@@ -338,11 +338,42 @@ def _closure_runs(dgh, W, n_runs, n_hex, T, every, fraction, seed):
         yield r, rows
 
 
+def _closure_closed_loop_runs(dgh, W, w, n_runs, n_hex, T, every, fraction, seed):
+    """Closed-loop training data: n_runs seeded runs of the same kind as
+    _closure_runs, but with HABC P = 2 and the closure w in the loop, and a
+    P = 8 shadow chain; the rows are (features of the P = 2 chain, r^-_8 -
+    r^-_2) along the trajectory the closure produces.  Rows with a non-finite
+    value are dropped.  Returns the rows."""
+    out = []
+    for r in range(n_runs):
+        u = [float(W.hashed_uniform(seed, r, j)[0]) for j in range(6)]
+        x = [(2.0 * u[a] - 1.0) * 0.6 for a in range(3)]
+        VX, EToV = W.kuhn_mesh(n_hex, 1.0, 0.02, seed=seed + r)
+        g = dgh.Solver(VX, EToV, 4, 2, dt=dgh.plan(VX, EToV, 4, 8)["dt"])
+        g.closure_set_weights(w)
+        g.closure_record(shadow_order=8, every=every, fraction=fraction, max_samples=1 << 22, seed=seed + r)
+        if u[3] < 0.5:
+            g.init_gaussian(x, 0.08 + 0.07 * u[4])
+        else:
+            f0 = 2.0 + 4.0 * u[4]
+            g.add_point_source(x, f0, 1.25 / f0)
+            g.init_gaussian(x, 0.1, 0.0)
+        g.step(int(math.ceil(T / g.info["dt"])))
+        rows = g.closure_samples()
+        g.close()
+        out.append(rows[np.all(np.isfinite(rows), axis=1)])
+    return np.concatenate(out)
+
+
 def run_closure_form(args):
-    """Learned closure: record, train, evaluate.  Evaluation on the 40^3 x 6
-    unjittered cube (N = 4, c = rho = 1, Gaussian pulse of width 0.12 at
-    (0.35, -0.25, 0.30), t in [0, 1.5]): plain P = 2, P = 2 with the closure
-    (MLP(x) - MLP(0), and the homogeneous form), plain P = 8, against a
+    """Learned closure: record, train, evaluate.
+    Training: open-loop rows (a P = 8 run with a P = 2 shadow chain), then
+    closed-loop rounds that add the rows of P = 2 runs with the current
+    closure in the loop and a P = 8 shadow, retraining after each round.
+    Evaluation on the 40^3 x 6 unjittered cube (N = 4, c = rho = 1, Gaussian
+    pulse of width 0.12 at (0.35, -0.25, 0.30), t in [0, 1.5]): plain P = 2,
+    P = 2 with the open-loop closure (MLP(x) - MLP(0), and the homogeneous
+    form), P = 2 with the closed-loop closure, plain P = 8, against a
     large-domain reference whose inner mesh is the same cube (its boundary is
     too far for reflections to return by t = 1.5).
     Error(t)^2 = energy of the difference in the cube / initial energy."""
@@ -368,6 +399,17 @@ def run_closure_form(args):
                                                seed=CLOSURE_SEED)
     mse_hv = float(np.mean((dgh.closure_eval(wh, Xva) - Yva) ** 2))
     mse_mv = float(np.mean((dgh.closure_eval(w, Xva) - Yva) ** 2))
+    # closed-loop rounds (dataset aggregation): record along the trajectories
+    # of P = 2 with the current closure against a P = 8 shadow, add the rows
+    # to the training set, retrain
+    wc, agg, rounds = w, np.concatenate([Xtr, Ytr[:, None]], axis=1), []
+    for k in range(args.closure_rounds):
+        Dk = _closure_closed_loop_runs(dgh, W, wc, args.closure_round_runs, args.closure_train_n, 2.5, 20, 0.01,
+                                       CLOSURE_SEED + 1000 * (k + 1))
+        agg = np.concatenate([agg, Dk])
+        wc, _, mse_k = dgh.mlp_train(agg[:, :6], agg[:, 6], steps=args.closure_steps, batch=8192, lr=1e-3,
+                                     seed=CLOSURE_SEED)
+        rounds.append({"rows": int(Dk.shape[0]), "target_var": float(np.var(Dk[:, 6])), "train_mse": mse_k})
     t2 = time.perf_counter()
 
     # ---- evaluation
@@ -388,7 +430,8 @@ def run_closure_form(args):
     nst = int(math.ceil(T / dt))
     nst += (-nst) % nck
     dt = T / nst
-    arms = {"P2": (2, None), "P2_closure": (2, w), "P2_closure_homogeneous": (2, wh), "P8": (8, None)}
+    arms = {"P2": (2, None), "P2_closure": (2, w), "P2_closure_homogeneous": (2, wh),
+            "P2_closure_closed_loop": (2, wc), "P8": (8, None)}
     solvers = {}
     for name, (P, wts) in arms.items():
         g = dgh.Solver(VXs, EToVs, 4, P, dt=dt)
@@ -423,6 +466,8 @@ def run_closure_form(args):
     line = {"form": "closure", "metric": "reflection error (energy norm, relative)",
             "config": {"train": "%d runs, %d^3 x 6 tets, N = 4, P = 8, shadow P = 2, T = 2.5, every 20 steps, "
                                 "1%% of the face nodes" % (n_runs, args.closure_train_n),
+                       "closed_loop": "%d rounds of %d runs, P = 2 with the closure, shadow P = 8"
+                                      % (args.closure_rounds, args.closure_round_runs),
                        "eval": "%d^3 x 6 tets (unjittered), N = 4, Gaussian width %.2f at %s, T = %.1f, "
                                "reference %d^3 x 6 tets" % (n, sigma, x0, T, n + 2 * pad), "dt": dt},
             "samples": {"train": int(Xtr.shape[0]), "val": int(Xva.shape[0])},
@@ -430,12 +475,13 @@ def run_closure_form(args):
                          "val_mse_of_correction": mse_mv, "val_mse_homogeneous": mse_hv,
                          "homogeneous_fit_mse_relative_target": mse_h,
                          "target_var_val": float(np.var(Yva)), "first_batches_mse": float(np.mean(hist[:20])),
-                         "last_batches_mse": float(np.mean(hist[-20:]))},
+                         "last_batches_mse": float(np.mean(hist[-20:])),
+                         "closed_loop_rounds": rounds},
             "errors": summary, "times": times, "error_curves": errs,
             "seconds": {"record": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}
     print(json.dumps(line), flush=True)
     if args.closure_weights_out:
-        np.save(args.closure_weights_out, w)
+        np.save(args.closure_weights_out, wc)
 
 
 def _ricker(t, f, ts):
@@ -596,7 +642,9 @@ def main():
     ap.add_argument("--closure-train-n", type=int, default=24)
     ap.add_argument("--closure-eval-n", type=int, default=40)
     ap.add_argument("--closure-steps", type=int, default=4000)
-    ap.add_argument("--closure-weights-out", default="", help="save the trained closure weights (.npy)")
+    ap.add_argument("--closure-weights-out", default="", help="save the closed-loop closure weights (.npy)")
+    ap.add_argument("--closure-rounds", type=int, default=5, help="closed-loop retraining rounds")
+    ap.add_argument("--closure-round-runs", type=int, default=24, help="closed-loop runs per round")
     ap.add_argument("--form", default="plain", choices=["plain", "batch", "precision", "closure", "validation", "seam"],
                     help="batch: the batching form (48 independent problems); precision: the N = 6 layered "
                          "workload with the FP32 and tensor-core 3D kernels")

@@ -356,7 +356,11 @@ int dgh_closure_set_weights(dgh_ctx *ctx, const float *w, size_t n);
  * on every step that is a multiple of `every` (at its first stage) the rows
  * (x of the shadow chain, r^-_this - r^-_shadow) of a hashed fraction of the
  * boundary face nodes into a device buffer of max_samples rows (further rows
- * are dropped).  The shadow chain never changes this context's solution. */
+ * are dropped).  With the closure enabled on this context (a low order here,
+ * a high shadow order), the rows are closed-loop instead: (x of this chain,
+ * r^-_shadow - r^-_this), the correction the shadow order implies on the
+ * trajectory the closure produces.  The shadow chain never changes this
+ * context's solution. */
 int dgh_closure_record(dgh_ctx *ctx, int shadow_order, int every, double fraction, int64_t max_samples, uint64_t seed);
 
 /* Copies up to max_rows recorded rows [row][7] (6 features, target) into out

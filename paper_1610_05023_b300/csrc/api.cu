@@ -464,8 +464,13 @@ int launch_shadow(dgh_ctx *c, int cur, int stage, bool update, cudaStream_t st, 
         dgh_ctx::Shadow *h = c->sh;
         const int64_t rows = c->T * c->Np2;
         const int blocks = (int)std::min<int64_t>((rows + 255) / 256, int64_t(4) * c->sms);
-        k_record_samples<<<blocks, 256, 0, st>>>(h->feat, h->rm, h->rm_main, rows, c->d_step, h->every, h->threshold,
-                                                 h->seed, h->samples, h->count, h->max_samples);
+        // With the closure on, the rows are closed-loop: this chain's features
+        // and r^-_shadow - r^-_this, the correction that the shadow order
+        // implies on the trajectory the closure itself produces.
+        const bool cl = c->cl_on;
+        k_record_samples<<<blocks, 256, 0, st>>>(cl ? c->cl_feat : h->feat, cl ? c->cl_rm : h->rm, cl ? h->rm : h->rm_main,
+                                                 rows, c->d_step, h->every, h->threshold, h->seed, h->samples, h->count,
+                                                 h->max_samples);
     }
     return DGH_OK;
 }

@@ -138,6 +138,32 @@ def test_recorder_lower_order_shadow_and_sampling():
 
 
 @pytest.mark.gpu
+def test_closed_loop_recorder_rows_match_open_loop_rows_at_the_first_step():
+    """With the closure on, the recorder takes this chain's features and
+    r^-_shadow - r^-_this (closed-loop rows).  Here the correction is zero and
+    only the first step is recorded, where every chain still sees the initial
+    state: a P = 2 context with a P = 6 shadow must then record the same rows
+    as a P = 6 context with a P = 2 shadow (open-loop rows: the shadow's
+    features, r^-_this - r^-_shadow).  Same hashed node selection, so the
+    same set of rows."""
+    w = _weights(16).astype(np.float32)
+    w[C.NPARAM - C.NH - 1:] = 0.0      # w3 = 0, b3 = 0: MLP == 0
+    a, b = _solver(2), _solver(6)
+    a.closure_set_weights(w)
+    a.closure_record(shadow_order=6, every=1, fraction=1.0, max_samples=1 << 20, seed=3)
+    b.closure_record(shadow_order=2, every=1, fraction=1.0, max_samples=1 << 20, seed=3)
+    for g in (a, b):
+        g.init_gaussian([0.3, 0.2, -0.1], 0.3)
+        g.step(1)
+    Sa, Sb = a.closure_samples(), b.closure_samples()
+    T, Np2 = a.info["n_tris"], a.info["Np2"]
+    assert Sa.shape == Sb.shape == (T * Np2, 7)
+    Sa, Sb = Sa[np.lexsort(Sa.T[::-1])], Sb[np.lexsort(Sb.T[::-1])]
+    assert np.abs(Sa[:, 6]).max() > 0          # the orders differ at the first stage already
+    assert np.allclose(Sa, Sb, rtol=1e-6, atol=1e-6 * np.abs(Sb).max())
+
+
+@pytest.mark.gpu
 def test_closure_zero_output_is_bit_identical_and_output_changes_solution():
     w = _weights(11).astype(np.float32)
     o3 = C.NPARAM - C.NH - 1
@@ -181,3 +207,56 @@ def test_homogeneous_form_is_degree_one_and_zero_at_zero():
     s = np.linalg.norm(Xt, axis=1)
     yr = scales[C.NIN] * s * C.forward(wb, Xt / s[:, None])
     assert np.linalg.norm(y1 - yr) <= 1e-5 * np.linalg.norm(yr)
+
+
+@pytest.mark.gpu
+def test_closed_loop_closure_reflects_less_than_plain_p2():
+    """What the trained network gains over the method without it: on the
+    evaluation problem of the closure form (40^3 x 6 unjittered tets, N = 4,
+    Gaussian pulse of width 0.12 at (0.35, -0.25, 0.30), t in [0, 1.5]), the
+    energy-norm error against a large-domain run (80^3 x 6 tets, whose
+    boundary cannot reflect back in time) after the wave reaches the faces is
+    lower with the closed-loop-trained closure than with plain P = 2.  The
+    weights are the ones bench.py --form closure wrote (tests/data)."""
+    import math
+    import os
+    w = np.load(os.path.join(os.path.dirname(__file__), "data", "closure_closed_loop_w.npy"))
+    assert w.shape == (C.NPARAM,)
+    n, T, sigma, x0 = 40, 1.5, 0.12, [0.35, -0.25, 0.30]
+    h = 2.0 / n
+    pad = int(math.ceil((T / 2 + 2 * sigma) / h))
+    VXs, EToVs = W.kuhn_mesh(n, 1.0, 0.0, seed=0)
+    VXl, EToVl = W.kuhn_mesh(n + 2 * pad, 1.0 + pad * h, 0.0, seed=0)
+    key = lambda c: [tuple(v) for v in np.round(c / (h / 64.0)).astype(np.int64)]
+    where = {k: i for i, k in enumerate(key(VXl[EToVl].mean(axis=1)))}
+    inner = np.array([where[k] for k in key(VXs[EToVs].mean(axis=1))])
+    ref = dgh.Solver(VXl, EToVl, 4, 0)
+    dt = min(ref.info["dt"], dgh.plan(VXs, EToVs, 4, 8)["dt"])
+    ref.close()
+    nck = 15
+    nst = int(math.ceil(T / dt))
+    nst += (-nst) % nck
+    dt = T / nst
+    plain = dgh.Solver(VXs, EToVs, 4, 2, dt=dt)
+    closed = dgh.Solver(VXs, EToVs, 4, 2, dt=dt)
+    closed.closure_set_weights(w)
+    ref = dgh.Solver(VXl, EToVl, 4, 0, dt=dt)
+    for g in (plain, closed, ref):
+        g.init_gaussian(x0, sigma)
+    E0 = plain.energy()
+    t_hit = 1.0 - max(abs(v) for v in x0) - 2 * sigma
+    worst = {"plain": 0.0, "closed": 0.0}
+    for ck in range(1, nck + 1):
+        ref.step(nst // nck)
+        qr = ref.get_state(3)[inner]
+        for name, g in (("plain", plain), ("closed", closed)):
+            g.step(nst // nck)
+            e = math.sqrt(max(g.error_energy(qr), 0.0) / E0)
+            assert math.isfinite(e)
+            if ck * T / nck >= t_hit:
+                worst[name] = max(worst[name], e)
+    for g in (plain, closed, ref):
+        g.close()
+    assert worst["plain"] > 1e-3                       # plain P = 2 reflects visibly here
+    assert worst["closed"] < 0.8 * worst["plain"], worst
+
