@@ -43,6 +43,37 @@ __device__ __forceinline__ float mlp_forward(const float *w, const float (&x)[ML
     return y;
 }
 
+// The same forward pass for inference, arranged for throughput: the hidden
+// activations as (h[k], h[k+1]) register pairs, each W2 row read as float4s
+// (w 16-byte aligned), packed FP32x2 FMAs over the even and odd k of a row.
+__device__ __forceinline__ float mlp_forward_fast(const float *w, const float (&x)[MLP_IN]) {
+    float2 h[MLP_H / 2];
+#pragma unroll
+    for (int j = 0; j < MLP_H; ++j) {
+        float z = w[MLP_OB1 + j];
+#pragma unroll
+        for (int i = 0; i < MLP_IN; ++i) z += w[MLP_OW1 + j * MLP_IN + i] * x[i];
+        if (j & 1) h[j >> 1].y = tanhf(z);
+        else h[j >> 1].x = tanhf(z);
+        asm volatile("" ::: "memory");   // one activation at a time (register pressure)
+    }
+    float y = w[MLP_OB3];
+    const float4 *w2 = reinterpret_cast<const float4 *>(w + MLP_OW2);
+#pragma unroll 1
+    for (int j = 0; j < MLP_H; ++j) {
+        float2 z2 = make_float2(0.f, 0.f);   // (sum over even k, sum over odd k)
+#pragma unroll
+        for (int k4 = 0; k4 < MLP_H / 4; ++k4) {
+            const float4 a = w2[j * (MLP_H / 4) + k4];
+            z2 = __ffma2_rn(make_float2(a.x, a.y), h[2 * k4], z2);
+            z2 = __ffma2_rn(make_float2(a.z, a.w), h[2 * k4 + 1], z2);
+        }
+        y += w[MLP_OW3 + j] * tanhf(w[MLP_OB2 + j] + (z2.x + z2.y));
+    }
+    return y;
+}
+static_assert(MLP_OW2 % 4 == 0 && MLP_H % 4 == 0, "W2 rows must be float4-aligned");
+
 // Inference: the correction y = MLP(feat) - MLP(0) for n feature rows (the
 // fields enter linearly, so no fields must give no correction; MLP(0) is
 // evaluated by the same code with the same weights, so y(0) = 0 exactly).
@@ -56,21 +87,21 @@ __device__ __forceinline__ float mlp_forward(const float *w, const float (&x)[ML
 __global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const float *scales, const float *feat,
                                                        const float *rm, int64_t n, int np2, const int *tri_face,
                                                        float *tin3, float *y_out) {
-    __shared__ float sw[MLP_NPARAM];
+    __shared__ __align__(16) float sw[MLP_NPARAM];
     __shared__ float y0, ssc[MLP_IN + 1];
     for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sw[i] = wts[i];
     if (threadIdx.x <= MLP_IN) ssc[threadIdx.x] = scales ? scales[threadIdx.x] : 1.f;
     __syncthreads();
     if (threadIdx.x == 0) {
         const float z[MLP_IN] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        y0 = scales ? 0.f : mlp_forward(sw, z);
+        y0 = scales ? 0.f : mlp_forward_fast(sw, z);
     }
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         float x[MLP_IN];
 #pragma unroll
         for (int i = 0; i < MLP_IN; ++i) x[i] = feat[r * MLP_IN + i];
-        float y;
+        float amp = 1.f, off = y0;   // y = amp * MLP(x') - off
         if (scales) {
             float s2 = 0.f;
 #pragma unroll
@@ -79,17 +110,14 @@ __global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const f
                 s2 += x[i] * x[i];
             }
             const float sn = sqrtf(s2);
-            if (sn > 1e-30f) {
-                const float inv = 1.0f / sn;
+            const float inv = sn > 1e-30f ? 1.0f / sn : 0.f;
 #pragma unroll
-                for (int i = 0; i < MLP_IN; ++i) x[i] *= inv;
-                y = ssc[MLP_IN] * sn * mlp_forward(sw, x);
-            } else {
-                y = 0.f;
-            }
-        } else {
-            y = mlp_forward(sw, x) - y0;
+            for (int i = 0; i < MLP_IN; ++i) x[i] *= inv;
+            amp = sn > 1e-30f ? ssc[MLP_IN] * sn : 0.f;
+            off = 0.f;
         }
+        const float m = mlp_forward_fast(sw, x);
+        const float y = amp == 0.f ? 0.f : amp * m - off;
         if (y_out) y_out[r] = y;
         if (tin3) {
             const int64_t t = r / np2;
