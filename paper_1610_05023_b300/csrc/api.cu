@@ -100,7 +100,7 @@ struct dgh_ctx {
     // learned closure (inference on this context's chain)
     bool cl_on = false;
     bool cl_homog = false;            // homogeneous form: 7 scales follow the weights
-    float *cl_w = nullptr;            // MLP weights (BF16-rounded, stored FP32) [MLP_NPARAM] (+ 7 FP32 scales)
+    float *cl_w = nullptr;            // MLP weights (BF16-rounded, stored FP32) [MLP_NPARAM], 7 FP32 scales, MLP(0)
     float *cl_feat = nullptr;         // [T][Np2][6]
     float *cl_rm = nullptr;           // [T][Np2] r^- of this chain
     // shadow chain of another HABC order driven one-way by the 3D traces (sample recording)
@@ -403,7 +403,8 @@ struct Launch2 {
         if (!shadow && c->cl_on) {   // learned closure: exterior state 2 (r^- + MLP(features))
             const int64_t rows = c->T * c->Np2;
             const int blocks = (int)std::min<int64_t>((rows + 255) / 256, int64_t(4) * c->sms);
-            k_closure_apply<<<blocks, 256, 0, st>>>(c->cl_w, c->cl_homog ? c->cl_w + MLP_NPARAM : nullptr, c->cl_feat,
+            k_closure_apply<<<blocks, 256, 0, st>>>(c->cl_w, c->cl_homog ? c->cl_w + MLP_NPARAM : nullptr,
+                                                    c->cl_w + CL_MLP0, c->cl_feat,
                                                     c->cl_rm, rows, c->Np2, c->tri_face,
                                                     update ? c->tin3[cur ^ 1] : c->tin3[cur], nullptr);
         }
@@ -2289,10 +2290,12 @@ int dgh_closure_set_weights(dgh_ctx *ctx, const float *w, size_t n) {
     std::vector<float> wb(n);   // BF16 weights (FP32 arithmetic); the scales of the homogeneous form stay FP32
     for (size_t i = 0; i < n; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
     int rc = DGH_OK;
-    if (!ctx->cl_w && ((rc = dalloc(ctx, ctx->cl_w, size_t(MLP_NPARAM + MLP_IN + 1))) || (rc = dalloc(ctx, ctx->cl_feat, size_t(ctx->T) * ctx->Np2 * MLP_IN)) ||
+    if (!ctx->cl_w && ((rc = dalloc(ctx, ctx->cl_w, size_t(CL_MLP0 + 1))) || (rc = dalloc(ctx, ctx->cl_feat, size_t(ctx->T) * ctx->Np2 * MLP_IN)) ||
                        (rc = dalloc(ctx, ctx->cl_rm, size_t(ctx->T) * ctx->Np2))))
         return rc;
     CK(cudaMemcpy(ctx->cl_w, wb.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    k_mlp_zero<<<1, 256, 0, ctx->stream>>>(ctx->cl_w, ctx->cl_w + CL_MLP0);   // once per weight set
+    CK(cudaGetLastError());
     ctx->cl_on = true;
     ctx->cl_homog = n != size_t(MLP_NPARAM);
     ctx->dirty = true;   // the exterior state is rebuilt with the closure before the next step
@@ -2430,11 +2433,13 @@ int dgh_closure_eval(const float *w, size_t nw, const float *X, int64_t n, float
     for (size_t i = 0; i < nw; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
     DevScratch d;
     float *dw = d.get<float>(nw), *dX = d.get<float>(size_t(n) * MLP_IN), *dy = d.get<float>(size_t(n));
-    if (!dw || !dX || !dy) return mlp_fail("closure eval: device allocation failed", DGH_ENOMEM);
+    float *d0 = d.get<float>(1);
+    if (!dw || !dX || !dy || !d0) return mlp_fail("closure eval: device allocation failed", DGH_ENOMEM);
     cudaMemcpy(dw, wb.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
+    k_mlp_zero<<<1, 256>>>(dw, d0);
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    k_closure_apply<<<blocks, 256>>>(dw, nw == size_t(MLP_NPARAM) ? nullptr : dw + MLP_NPARAM, dX, nullptr, n, 1,
+    k_closure_apply<<<blocks, 256>>>(dw, nw == size_t(MLP_NPARAM) ? nullptr : dw + MLP_NPARAM, d0, dX, nullptr, n, 1,
                                      nullptr, nullptr, dy);
     cudaError_t e = cudaMemcpy(y, dy, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return mlp_fail(std::string("closure eval: ") + cudaGetErrorString(e), DGH_ECUDA);

@@ -21,6 +21,7 @@ constexpr int MLP_OW1 = 0, MLP_OB1 = MLP_OW1 + MLP_H * MLP_IN, MLP_OW2 = MLP_OB1
               MLP_OB2 = MLP_OW2 + MLP_H * MLP_H, MLP_OW3 = MLP_OB2 + MLP_H, MLP_OB3 = MLP_OW3 + MLP_H;
 constexpr int MLP_NPARAM = MLP_OB3 + 1;   // 4673
 constexpr int SAMPLE_W = MLP_IN + 1;      // recorded sample: 6 features, target
+constexpr int CL_MLP0 = MLP_NPARAM + MLP_IN + 1;   // device weight block: weights, 7 scales, then MLP(0)
 
 // forward pass of one sample with the weights in shared memory
 __device__ __forceinline__ float mlp_forward(const float *w, const float (&x)[MLP_IN]) {
@@ -74,9 +75,21 @@ __device__ __forceinline__ float mlp_forward_fast(const float *w, const float (&
 }
 static_assert(MLP_OW2 % 4 == 0 && MLP_H % 4 == 0, "W2 rows must be float4-aligned");
 
+// MLP(0) with the inference code and the weights in shared memory, as
+// k_closure_apply evaluates every row (one block; the value goes to *y0).
+__global__ void k_mlp_zero(const float *wts, float *y0) {
+    __shared__ __align__(16) float sw[MLP_NPARAM];
+    for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sw[i] = wts[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float z[MLP_IN] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        *y0 = mlp_forward_fast(sw, z);
+    }
+}
+
 // Inference: the correction y = MLP(feat) - MLP(0) for n feature rows (the
-// fields enter linearly, so no fields must give no correction; MLP(0) is
-// evaluated by the same code with the same weights, so y(0) = 0 exactly).
+// fields enter linearly, so no fields must give no correction; MLP(0) comes
+// from k_mlp_zero, the same code with the same weights, so y(0) = 0 exactly).
 // When tin3 is given, the corrected exterior state 2 (r^- + y) of every
 // boundary face node of the chain goes to the 3D incoming traces (rows =
 // triangle nodes t * NP2 + node).
@@ -84,18 +97,14 @@ static_assert(MLP_OW2 % 4 == 0 && MLP_H % 4 == 0, "W2 rows must be float4-aligne
 // sigma_y): x~ = x / sigma, s = |x~|, y = sigma_y s MLP(x~ / s), 0 at s = 0 --
 // the correction is then of degree one in the fields, as the linear wave
 // equation requires, and the network sees only the direction of x.
-__global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const float *scales, const float *feat,
-                                                       const float *rm, int64_t n, int np2, const int *tri_face,
-                                                       float *tin3, float *y_out) {
+__global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const float *scales, const float *mlp0,
+                                                       const float *feat, const float *rm, int64_t n, int np2,
+                                                       const int *tri_face, float *tin3, float *y_out) {
     __shared__ __align__(16) float sw[MLP_NPARAM];
-    __shared__ float y0, ssc[MLP_IN + 1];
+    __shared__ float ssc[MLP_IN + 1];
     for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sw[i] = wts[i];
     if (threadIdx.x <= MLP_IN) ssc[threadIdx.x] = scales ? scales[threadIdx.x] : 1.f;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const float z[MLP_IN] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        y0 = scales ? 0.f : mlp_forward_fast(sw, z);
-    }
+    const float y0 = scales ? 0.f : mlp0[0];   // MLP(0) (not used by the homogeneous form)
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         float x[MLP_IN];

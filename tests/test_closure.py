@@ -190,6 +190,20 @@ def test_closure_zero_output_is_bit_identical_and_output_changes_solution():
 
 
 @pytest.mark.gpu
+def test_closure_gives_no_correction_at_zero_fields():
+    """MLP(0) is evaluated once per weight set by the inference code itself,
+    so a field-free run stays exactly zero under a closure with arbitrary
+    weights (a correction of even one ulp at zero fields would inject a
+    nonzero exterior state)."""
+    g = _solver(2)
+    g.closure_set_weights(_weights(17).astype(np.float32))
+    g.init_gaussian([0.3, 0.2, -0.1], 0.3, 0.0)
+    g.step(20)
+    for lv in (3, 2, 1):
+        assert np.all(g.get_state(lv) == 0.0)
+
+
+@pytest.mark.gpu
 def test_homogeneous_form_is_degree_one_and_zero_at_zero():
     w = _weights(13).astype(np.float32)
     rng = np.random.default_rng(14)
