@@ -23,31 +23,11 @@ constexpr int MLP_NPARAM = MLP_OB3 + 1;   // 4673
 constexpr int SAMPLE_W = MLP_IN + 1;      // recorded sample: 6 features, target
 constexpr int CL_MLP0 = MLP_NPARAM + MLP_IN + 1;   // device weight block: weights, 7 scales, then MLP(0)
 
-// forward pass of one sample with the weights in shared memory
+// Forward pass of one sample with the weights in shared memory, arranged for
+// throughput: the hidden activations as (h[k], h[k+1]) register pairs, each
+// W2 row read as float4s (w 16-byte aligned), packed FP32x2 FMAs over the even
+// and odd k of a row.
 __device__ __forceinline__ float mlp_forward(const float *w, const float (&x)[MLP_IN]) {
-    float h1[MLP_H];
-#pragma unroll
-    for (int j = 0; j < MLP_H; ++j) {
-        float z = w[MLP_OB1 + j];
-#pragma unroll
-        for (int i = 0; i < MLP_IN; ++i) z += w[MLP_OW1 + j * MLP_IN + i] * x[i];
-        h1[j] = tanhf(z);
-    }
-    float y = w[MLP_OB3];
-#pragma unroll 4
-    for (int j = 0; j < MLP_H; ++j) {
-        float z = w[MLP_OB2 + j];
-#pragma unroll
-        for (int k = 0; k < MLP_H; ++k) z += w[MLP_OW2 + j * MLP_H + k] * h1[k];
-        y += w[MLP_OW3 + j] * tanhf(z);
-    }
-    return y;
-}
-
-// The same forward pass for inference, arranged for throughput: the hidden
-// activations as (h[k], h[k+1]) register pairs, each W2 row read as float4s
-// (w 16-byte aligned), packed FP32x2 FMAs over the even and odd k of a row.
-__device__ __forceinline__ float mlp_forward_fast(const float *w, const float (&x)[MLP_IN]) {
     float2 h[MLP_H / 2];
 #pragma unroll
     for (int j = 0; j < MLP_H; ++j) {
@@ -83,7 +63,7 @@ __global__ void k_mlp_zero(const float *wts, float *y0) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const float z[MLP_IN] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        *y0 = mlp_forward_fast(sw, z);
+        *y0 = mlp_forward(sw, z);
     }
 }
 
@@ -125,7 +105,7 @@ __global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const f
             amp = sn > 1e-30f ? ssc[MLP_IN] * sn : 0.f;
             off = 0.f;
         }
-        const float m = mlp_forward_fast(sw, x);
+        const float m = mlp_forward(sw, x);
         const float y = amp == 0.f ? 0.f : amp * m - off;
         if (y_out) y_out[r] = y;
         if (tin3) {
