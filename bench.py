@@ -143,6 +143,24 @@ def cpu_oracle_sample(seconds_budget=20.0):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def replica_time_max(seconds, world, device=None):
+    """Whole-job time of N replicas: the maximum over ranks of each rank's
+    own duration (all-reduce MAX over the default process group; a CPU
+    tensor under gloo, a device tensor under NCCL)."""
+    if world <= 1:
+        return float(seconds)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_replica, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the job time."""
+    return max(world, 1) * units_per_replica / seconds
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -707,12 +725,8 @@ def main():
     end.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ndof * 5 * args.steps / (ms * 1e-3)
+    ms = replica_time_max(start.elapsed_time(end), world, device="cuda")
+    value = replica_throughput(ndof * 5 * args.steps, world, ms * 1e-3)
 
     # per-kernel durations (events around each launch, direct launches)
     kt = g.time_kernels(20)
@@ -740,7 +754,7 @@ def main():
     g.step(e2e_steps)
     g.get_state(3, out=out)
     t1 = time.perf_counter()
-    e2e_value = world * ndof * 5 * e2e_steps / (t1 - t0)
+    e2e_value = replica_throughput(ndof * 5 * e2e_steps, world, replica_time_max(t1 - t0, world, device="cuda"))
     state_bytes = q3.size * 8      # FP64 host arrays copied as they are (converted on the device)
 
     parts3 = 2 if info["n_tris"] > 0 else 1      # interior cells, then cells with HABC faces
