@@ -452,11 +452,17 @@ class Solver:
         self._check(self._lib.dgh_closure_set_weights(self._h, _fptr(w), w.size))
 
     def closure_record(self, shadow_order=2, every=1, fraction=1.0, max_samples=1 << 20, seed=0):
+        """Add a shadow HABC chain of order shadow_order driven one-way by this
+        solver's 3D traces and record training rows on every `every`-th step
+        from a hashed fraction of the boundary face nodes (dgh_closure_record)."""
         self._check(self._lib.dgh_closure_record(self._h, int(shadow_order), int(every), float(fraction),
                                                  int(max_samples), int(seed)))
 
     def closure_samples(self, max_rows=None):
-        """Recorded rows [n][7]: 6 features, target (r^-_this - r^-_shadow)."""
+        """Recorded rows [n][7]: 6 features and the target.  Open-loop rows
+        (closure off): the shadow chain's features, r^-_this - r^-_shadow.
+        Closed-loop rows (closure on): this chain's features, r^-_shadow -
+        r^-_this."""
         cnt = ctypes.c_int64()
         self._check(self._lib.dgh_closure_samples(self._h, None, 0, ctypes.byref(cnt)))
         n = cnt.value if max_rows is None else min(cnt.value, int(max_rows))
