@@ -4,12 +4,12 @@
 //
 // B300 design
 //  * Cell-interleaved layouts: q, res [K/32][field][node][32]; the incoming
-//    face traces of every cell [K/32][face][p|n.u][Nfp][32]; geometry
-//    [K/32][GEO3][32]; connectivity [K/32][4][32].  A 32-cell block of each
-//    is one contiguous chunk.
+//    face traces of every cell [K/32][face][Nfp][32][p, n.u] (one 8-byte pair
+//    per face node and cell); geometry [K/32][GEO3][32]; connectivity
+//    [K/32][4][32].  A 32-cell block of each is one contiguous chunk.
 //  * Traces are pushed, not pulled: after its update a cell writes (p, -n.u)
 //    of each face straight into the incoming slots of the neighbour (in the
-//    neighbour's face-node order), with fire-and-forget stores.  The next stage
+//    neighbour's face-node order), with fire-and-forget 8-byte stores.  The next stage
 //    then reads its own incoming traces as one contiguous block -- no
 //    dependent gathers on the critical path.  Boundary faces write their own
 //    traces to a per-boundary-face array read by the 2D (face HABC) kernel,
