@@ -446,7 +446,8 @@ void launch0(dgh_ctx *c, int cur_traces, cudaStream_t st = nullptr, bool shadow 
     A.Hc = shadow ? c->sh->Hc : c->Hc;
     A.P = shadow ? c->sh->P : c->P;
     A.C = c->C;
-    k0d_stage<<<c->C, 128, shadow ? c->sh->smem0 : c->smem0, st>>>(A);
+    const int R = 3 * A.P * A.P;
+    k0d_stage<<<dim3(c->C, (R + K0D_ROWS - 1) / K0D_ROWS), 256, shadow ? c->sh->smem0 : c->smem0, st>>>(A);
 }
 
 // The shadow chain of one stage (2D, 1D, 0D of the shadow order; no

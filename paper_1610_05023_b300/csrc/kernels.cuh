@@ -601,7 +601,13 @@ inline size_t k1d_smem(int N, int P, int tile) {
 }
 
 // ==================================================================== 0D
-__global__ void k0d_stage(Args0 A) {
+// One CTA per (corner, block of K0D_ROWS rows of the 3P^2 x 3P^2 solution
+// operator): the CTA forms the corner's r^+ (3P^2 values) in shared memory,
+// then each warp takes rows two at a time -- coalesced row loads, shuffle
+// sums -- so that the operator (746 KB at P = 12) streams through many SMs.
+constexpr int K0D_ROWS = 32;
+
+__global__ void __launch_bounds__(256) k0d_stage(Args0 A) {
     const int c = blockIdx.x;
     const int P = A.P, S = P * P, R = 3 * S;
     extern __shared__ float rp[];
@@ -613,12 +619,28 @@ __global__ void k0d_stage(Args0 A) {
         rp[i] = 0.5f * (tr[0] + A.cornerZ[c * 3 + slot] * tr[1]);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-        float x = 0.f;
-        for (int j = 0; j < R; ++j) x += A.Hc[i * R + j] * rp[j];
-        const int slot = i / S, s = i % S;
-        const int l = cd[2 * slot], e = cd[2 * slot + 1];
-        A.qb1[((int64_t)l * 2 + e) * S + s] = x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int r0 = blockIdx.y * K0D_ROWS, r1 = min(R, r0 + K0D_ROWS);
+    for (int i = r0 + 2 * warp; i < r1; i += 2 * nwarp) {
+        const bool two = i + 1 < r1;
+        const float *h0 = A.Hc + (int64_t)i * R, *h1 = h0 + R;
+        float x0 = 0.f, x1 = 0.f;
+        for (int j = lane; j < R; j += 32) {
+            const float r = rp[j];
+            x0 += h0[j] * r;
+            if (two) x1 += h1[j] * r;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x0 += __shfl_xor_sync(0xffffffffu, x0, o);
+            x1 += __shfl_xor_sync(0xffffffffu, x1, o);
+        }
+        if (lane == 0)
+            for (int k = 0; k < (two ? 2 : 1); ++k) {
+                const int row = i + k, slot = row / S, s = row % S;
+                const int l = cd[2 * slot], e = cd[2 * slot + 1];
+                A.qb1[((int64_t)l * 2 + e) * S + s] = k ? x1 : x0;
+            }
     }
 }
 
