@@ -60,7 +60,7 @@ extern "C" {
 #define DGH_EINVAL       -1   /* invalid argument (null pointer, bad size, bad mesh) */
 #define DGH_ENOMEM       -2   /* device or host allocation failed */
 #define DGH_ECUDA        -3   /* CUDA runtime error (launch or asynchronous) */
-#define DGH_EUNSTABLE    -4   /* non-finite values detected by a check */
+#define DGH_EUNSTABLE    -4   /* non-finite energy, or energy above the watchdog bound (dgh_set_watchdog) */
 #define DGH_ETIMEOUT     -5   /* a bounded device-side wait gave up (reported by dgh_sync) */
 #define DGH_ESTATE       -6   /* call not valid in the current state */
 #define DGH_EUNSUPPORTED -7   /* feature / order not compiled in */
@@ -165,8 +165,21 @@ int dgh_set_time(dgh_ctx *ctx, double t);
  * Errors: DGH_EINVAL if xs lies outside the mesh. */
 int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double t_s, double amp);
 
-/* Advances nsteps LSERK4 steps on the context's stream (asynchronous). */
+/* Advances nsteps LSERK4 steps on the context's stream (asynchronous unless
+ * the watchdog is on).  With the watchdog on, returns DGH_EUNSTABLE after the
+ * first checked step whose energy fails the check; the steps up to and
+ * including it have been taken. */
 int dgh_step(dgh_ctx *ctx, int64_t nsteps);
+
+/* Energy watchdog.  The Pade HABC has a known slow error growth over long
+ * times (Sec. 4.1); this guards long runs against it and against non-finite
+ * values.  With every > 0, dgh_step computes the 3D energy (as dgh_get_energy)
+ * after every step whose step count is a multiple of `every` and stops with
+ * DGH_EUNSTABLE if it is not finite, or if energy_limit > 0 and the energy
+ * exceeds energy_limit (the message in dgh_last_error gives the step and the
+ * energy).  Each check synchronises the stream.  every = 0 turns it off.
+ * DGH_EINVAL if every < 0 or energy_limit is not finite. */
+int dgh_set_watchdog(dgh_ctx *ctx, int64_t every, double energy_limit);
 
 /* Profiling aid: advances nsteps steps with direct launches (no graph),
  * bracketing every kernel launch with CUDA events on the context's stream.

@@ -25,6 +25,7 @@ PREC_SPLIT_BF16 = 3
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ETIMEOUT", -6: "ESTATE",
            -7: "EUNSUPPORTED"}
 DGH_ETIMEOUT = -5
+DGH_EUNSTABLE = -4
 
 
 class DghError(RuntimeError):
@@ -95,6 +96,7 @@ def load_library(path=LIB_PATH):
         "dgh_set_time": (ctypes.c_int, [P, ctypes.c_double]),
         "dgh_add_point_source": (ctypes.c_int, [P, D, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "dgh_step": (ctypes.c_int, [P, ctypes.c_int64]),
+        "dgh_set_watchdog": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_double]),
         "dgh_sync": (ctypes.c_int, [P]),
         "dgh_time_kernels": (ctypes.c_int, [P, ctypes.c_int64, D]),
         "dgh_get_energy": (ctypes.c_int, [P, D]),
@@ -385,6 +387,12 @@ class Solver:
 
     def set_time(self, t):
         self._check(self._lib.dgh_set_time(self._h, float(t)))
+
+    def set_watchdog(self, every, energy_limit=0.0):
+        """Energy watchdog (dgh_set_watchdog): every `every` steps, step()
+        raises DghError (EUNSTABLE) if the 3D energy is not finite or exceeds
+        energy_limit (> 0).  every = 0 turns it off."""
+        self._check(self._lib.dgh_set_watchdog(self._h, int(every), float(energy_limit)))
 
     def add_point_source(self, xs, f_peak, t_s, amp=1.0):
         x = np.ascontiguousarray(xs, dtype=np.float64)

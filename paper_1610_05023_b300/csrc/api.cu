@@ -54,6 +54,8 @@ struct dgh_ctx {
     int M = 1;
     double dt = 0.0, t0 = 0.0;
     int64_t step_count = 0;
+    int64_t wd_every = 0;     // energy watchdog: check every wd_every steps (0 = off)
+    double wd_limit = 0.0;    // energy bound (<= 0: finiteness only)
     int cur = 0;              // trace buffer holding the current traces
     bool dirty = true;        // boundary algebra must be recomputed
     std::vector<DevBuf> bufs;
@@ -1472,8 +1474,31 @@ int dgh_step(dgh_ctx *ctx, int64_t nsteps) {
         }
         ctx->cur ^= 1;   // 5 stages: odd number of trace swaps
         ctx->step_count++;
+        if (ctx->wd_every > 0 && ctx->step_count % ctx->wd_every == 0) {
+            double E = 0.0;
+            int rc = dgh_get_energy(ctx, &E);
+            if (rc) return rc;
+            if (!std::isfinite(E) || (ctx->wd_limit > 0.0 && E > ctx->wd_limit)) {
+                char msg[160];
+                std::snprintf(msg, sizeof msg, "watchdog: energy %.6e at step %lld (limit %.6e)", E,
+                              (long long)ctx->step_count, ctx->wd_limit);
+                ctx->err = msg;
+                return DGH_EUNSTABLE;
+            }
+        }
     }
     CK(cudaGetLastError());
+    return DGH_OK;
+}
+
+int dgh_set_watchdog(dgh_ctx *ctx, int64_t every, double energy_limit) {
+    if (!ctx) return DGH_EINVAL;
+    if (every < 0 || !std::isfinite(energy_limit)) {
+        ctx->err = "watchdog: every >= 0 and a finite energy limit";
+        return DGH_EINVAL;
+    }
+    ctx->wd_every = every;
+    ctx->wd_limit = energy_limit;
     return DGH_OK;
 }
 

@@ -43,6 +43,7 @@ def test_error_paths_without_gpu(lib):
     h = ctypes.c_void_p()
     assert L.dgh_create(None, None, ctypes.byref(h)) == -1
     assert b"invalid" in L.dgh_last_error(None)
+    assert L.dgh_set_watchdog(None, 1, 0.0) == -1
     VX, EToV = W.kuhn_mesh(1)
     d, keep = dgh._make_desc(VX, EToV, 9, 0, (0,) * 6, 1.0, 1.0, 0.0, 1.0)
     assert L.dgh_create(ctypes.byref(d), None, ctypes.byref(h)) == -7
