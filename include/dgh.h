@@ -64,6 +64,7 @@ extern "C" {
 #define DGH_ETIMEOUT     -5   /* a bounded device-side wait gave up (reported by dgh_sync) */
 #define DGH_ESTATE       -6   /* call not valid in the current state */
 #define DGH_EUNSUPPORTED -7   /* feature / order not compiled in */
+#define DGH_EBOUNDS      -8   /* checked build: an index outside its array, access skipped (reported by dgh_sync) */
 
 /* Boundary condition of a domain face. */
 #define DGH_BC_HABC       0   /* Pade HABC of order P (P = 0: basic ABC, Sec. 3.2) */
@@ -190,6 +191,12 @@ int dgh_time_kernels(dgh_ctx *ctx, int64_t nsteps, double out_ms[5]);
 
 /* Waits for the context's stream; reports asynchronous CUDA errors. */
 int dgh_sync(dgh_ctx *ctx);
+
+/* 1 in the checked build (libdgh_checked.so, compiled with -DDGH_CHECKED),
+ * else 0.  In the checked build the stage kernels test every index they
+ * gather through or push to against its array; a violation skips the access
+ * and dgh_sync returns DGH_EBOUNDS.  Results are otherwise identical. */
+int dgh_is_checked_build(void);
 
 /* Discrete energy of the 3D fields,
  * E = sum_k |J_k| [p^T M p / (2 rho c^2) + (rho/2) sum_i u_i^T M u_i],

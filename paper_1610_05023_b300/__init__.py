@@ -13,6 +13,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdgh.so")
+CHECKED_LIB_PATH = os.path.join(_HERE, "libdgh_checked.so")   # index-checked build (tests)
 
 DGH_OK = 0
 BC_HABC = 0
@@ -23,9 +24,10 @@ PREC_FP16_TC = 2
 PREC_SPLIT_BF16 = 3
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ETIMEOUT", -6: "ESTATE",
-           -7: "EUNSUPPORTED"}
+           -7: "EUNSUPPORTED", -8: "EBOUNDS"}
 DGH_ETIMEOUT = -5
 DGH_EUNSTABLE = -4
+DGH_EBOUNDS = -8
 
 
 class DghError(RuntimeError):
@@ -98,6 +100,7 @@ def load_library(path=LIB_PATH):
         "dgh_step": (ctypes.c_int, [P, ctypes.c_int64]),
         "dgh_set_watchdog": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_double]),
         "dgh_sync": (ctypes.c_int, [P]),
+        "dgh_is_checked_build": (ctypes.c_int, []),
         "dgh_time_kernels": (ctypes.c_int, [P, ctypes.c_int64, D]),
         "dgh_get_energy": (ctypes.c_int, [P, D]),
         "dgh_get_error_energy": (ctypes.c_int, [P, D, ctypes.c_size_t, D]),

@@ -197,6 +197,8 @@ Args3 args3(dgh_ctx *c, int cur) {
     A.geo = c->geo3;
     A.conn = c->conn3;
     A.err = c->d_err;
+    A.kcells = c->K32 * 32;
+    A.nbfaces = c->Fb;
     A.blk_begin = 0;
     A.blk_end = c->K32;
     A.D = c->D3;
@@ -249,6 +251,9 @@ Args2 args2(dgh_ctx *c, int cur, bool update, bool shadow = false) {
     A.invM = 1.0f / float(c->M);
     A.P = c->P;
     A.T = c->T;
+    A.err = c->d_err;
+    A.kcells = c->K32 * 32;
+    A.nbfaces = c->Fb;
     return A;
 }
 
@@ -291,6 +296,8 @@ Args1 args1(dgh_ctx *c, int cur, bool update, bool shadow = false) {
     A.invM = 1.0f / float(c->M);
     A.P = c->P;
     A.L = c->L;
+    A.err = c->d_err;
+    A.T = c->T;
     return A;
 }
 
@@ -448,6 +455,8 @@ void launch0(dgh_ctx *c, int cur_traces, cudaStream_t st = nullptr, bool shadow 
     A.Hc = shadow ? c->sh->Hc : c->Hc;
     A.P = shadow ? c->sh->P : c->P;
     A.C = c->C;
+    A.err = c->d_err;
+    A.L = c->L;
     const int R = 3 * A.P * A.P;
     k0d_stage<<<dim3(c->C, (R + K0D_ROWS - 1) / K0D_ROWS), 256, shadow ? c->sh->smem0 : c->smem0, st>>>(A);
 }
@@ -1560,11 +1569,23 @@ int dgh_sync(dgh_ctx *ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
     int err = 0;
     CK(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err == 2) {
+        ctx->err = "checked build: an index outside its array (the access was skipped)";
+        return DGH_EBOUNDS;
+    }
     if (err) {
         ctx->err = "a device-side wait timed out (stage kernel aborted)";
         return DGH_ETIMEOUT;
     }
     return DGH_OK;
+}
+
+int dgh_is_checked_build(void) {
+#ifdef DGH_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int dgh_get_energy(dgh_ctx *ctx, double *E) {

@@ -68,6 +68,7 @@ struct Args3 {
     int *err;                // device error word (bounded waits)
     int64_t blk_begin;       // 32-cell blocks [blk_begin, blk_end) handled by this launch
     int64_t blk_end;
+    int64_t kcells, nbfaces;       // bounds of pushed cell and boundary-face ids (checked build)
     unsigned long long *tile_ctr;  // zeroed before the launch; CTAs claim blocks from it
     int max_tiles;                 // blocks per CTA at most (CTAs retire regularly so that
                                    // concurrent kernels of the HABC chain get SMs)
@@ -403,11 +404,14 @@ __global__ void __launch_bounds__(Cfg3<N>::NW * 32, Cfg3<N>::MINB) k3d_stage(Arg
                     const int64_t kn = nb >> 2;
                     const int fn = nb & 3;
                     const int mn = sFp[(cc & 7) * NFP + m];
-                    reinterpret_cast<float2 *>(A.tout)[(((kn >> 5) * 4 + fn) * NFP + mn) * 32 + (kn & 31)] = make_float2(qn[0], -un);
+                    if (DGH_IN_RANGE(A.err, kn, A.kcells))
+                        reinterpret_cast<float2 *>(A.tout)[(((kn >> 5) * 4 + fn) * NFP + mn) * 32 + (kn & 31)] = make_float2(qn[0], -un);
                 } else {         // boundary face: own trace for the face HABC solver
                     const int64_t b = (-1 - cc) >> 1;
-                    A.trb[b * 2 * NFP + m] = qn[0];
-                    A.trb[b * 2 * NFP + NFP + m] = un;
+                    if (DGH_IN_RANGE(A.err, b, A.nbfaces)) {
+                        A.trb[b * 2 * NFP + m] = qn[0];
+                        A.trb[b * 2 * NFP + NFP + m] = un;
+                    }
                 }
             }
         }

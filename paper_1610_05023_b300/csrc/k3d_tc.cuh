@@ -483,12 +483,15 @@ __global__ void __launch_bounds__(256, 1) k3d_tc(Args3 A, StageCoef sc, const ui
                                 const int64_t kn = nb >> 2;
                                 const int fn = nb & 3;
                                 const int mn = sFp[(cc & 7) * NFP + m];
-                                reinterpret_cast<float2 *>(tout)[(((kn >> 5) * 4 + fn) * NFP + mn) * 32 + (kn & 31)] =
-                                    make_float2(qn[0], -un);
+                                if (DGH_IN_RANGE(A.err, kn, A.kcells))
+                                    reinterpret_cast<float2 *>(tout)[(((kn >> 5) * 4 + fn) * NFP + mn) * 32 + (kn & 31)] =
+                                        make_float2(qn[0], -un);
                             } else {
                                 const int64_t b = (-1 - cc) >> 1;
-                                trb[b * 2 * NFP + m] = qn[0];
-                                trb[b * 2 * NFP + NFP + m] = un;
+                                if (DGH_IN_RANGE(A.err, b, A.nbfaces)) {
+                                    trb[b * 2 * NFP + m] = qn[0];
+                                    trb[b * 2 * NFP + NFP + m] = un;
+                                }
                             }
                         }
                     }

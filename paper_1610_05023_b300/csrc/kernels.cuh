@@ -35,6 +35,22 @@ constexpr int GEO1 = 16;   // per line: rx, fscale, rho c^2, 1/rho, Z, ZA, ZB, 2
 constexpr int MAXP = 12;
 constexpr int MAXSRC = 64;
 
+// Checked build (compiled with -DDGH_CHECKED): every index that a stage
+// kernel gathers through or pushes to is tested against its array; a
+// violation writes 2 into the device error word and the access is skipped
+// (the host reports DGH_EBOUNDS).  In the normal build the test is compiled
+// out.  This stands in for a memory checker that this platform lacks.
+#ifdef DGH_CHECKED
+__device__ __forceinline__ bool in_range_checked(int *err, int64_t i, int64_t n) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicExch(err, 2);
+    return false;
+}
+#define DGH_IN_RANGE(err, i, n) ::dgh::in_range_checked((err), (int64_t)(i), (int64_t)(n))
+#else
+#define DGH_IN_RANGE(err, i, n) true
+#endif
+
 struct SrcParams {
     int n;
     int64_t cell[MAXSRC];
@@ -69,6 +85,8 @@ struct Args2 {
     float invM;
     int P;
     int64_t T;
+    int *err;               // device error word (checked build)
+    int64_t kcells, nbfaces;   // bounds of tri_face cells and tri_bface (checked build)
 };
 
 struct Args1 {
@@ -90,6 +108,8 @@ struct Args1 {
     float invM;
     int P;
     int64_t L;
+    int *err;               // device error word (checked build)
+    int64_t T;              // bound of the triangle ids in lmap (checked build)
 };
 
 struct Args0 {
@@ -100,6 +120,8 @@ struct Args0 {
     const float *Hc;        // [3P^2][3P^2]
     int P;
     int C;
+    int *err;               // device error word (checked build)
+    int64_t L;              // bound of the line ids in corner (checked build)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -248,7 +270,8 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
         if (A.tin3 && tid < nt) cp_async4(sface + tid, A.tri_face + t0 + tid);
         for (int i = tid; i < nt * 2 * NP2; i += nth) {
             const int t = i / (2 * NP2), r = i % (2 * NP2);
-            cp_async4(strb + i, A.trb + (int64_t)A.tri_bface[t0 + t] * 2 * NP2 + r);
+            const int bf = A.tri_bface[t0 + t];
+            if (DGH_IN_RANGE(A.err, bf, A.nbfaces)) cp_async4(strb + i, A.trb + (int64_t)bf * 2 * NP2 + r);
         }
         float *sq = sqb + shq, *sres = srb + shq, *s0 = s0b + sh0;
         const bool act = tid < nitem;
@@ -262,7 +285,8 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
                 const int c = A.conn[tg * 3 + e];
                 ce[e] = c;
                 if (c >= 0) {
-                    const int nb = c >> 1, tn = nb / 3, en = nb - 3 * tn;
+                    const int nb = c >> 1, tn0 = nb / 3, en = nb - 3 * tn0;
+                    const int tn = DGH_IN_RANGE(A.err, tn0, A.T) ? tn0 : 0;
                     const float *tr = A.tr_in + (((int64_t)tn * P + a) * 3 + en) * 2 * NFP2;
 #pragma unroll
                     for (int m = 0; m < NFP2; ++m) {
@@ -386,7 +410,8 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
             if (A.tin3) {
                 const int64_t gf = sface[tt], kc = gf >> 2;
                 const int fc = (int)(gf & 3);
-                A.tin3[((((kc >> 5) * 4 + fc) * NP2 + n) * 32 + (kc & 31)) * 2] = 2.0f * rm;   // exterior p; n.u = 0
+                if (DGH_IN_RANGE(A.err, kc, A.kcells))
+                    A.tin3[((((kc >> 5) * 4 + fc) * NP2 + n) * 32 + (kc & 31)) * 2] = 2.0f * rm;   // exterior p; n.u = 0
             }
             const float q0 = rm + rp;
             if (A.rm_out) A.rm_out[tg * NP2 + n] = rm;
@@ -478,7 +503,8 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
             const int *mp = smp + l * 6 + 3 * side;
             const int m = mp[2] ? (N - n) : n;
             const float Z = sg[l * GEO1 + 5 + side];
-            const float *tr = A.tr2 + (((int64_t)mp[0] * P + a) * 3 + mp[1]) * 2 * NP1;
+            const int tri = DGH_IN_RANGE(A.err, mp[0], A.T) ? mp[0] : 0;
+            const float *tr = A.tr2 + (((int64_t)tri * P + a) * 3 + mp[1]) * 2 * NP1;
             srp[i] = 0.5f * (tr[m] + Z * tr[NP1 + m]);
         }
         if (UPDATE)
@@ -486,7 +512,7 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
                 const int l = i / (S * 2), r = i % (S * 2), s2 = r / 2, e = r % 2;
                 const int c = scn[l * 2 + e];
                 float pp = 0.f, wnp = 0.f;
-                if (c >= 0) {
+                if (c >= 0 && DGH_IN_RANGE(A.err, c >> 1, A.L)) {
                     const float *tr = A.tr_in + ((int64_t)(c >> 1) * S + s2) * 4 + (c & 1) * 2;
                     pp = tr[0];
                     wnp = -tr[1];
@@ -571,7 +597,7 @@ __global__ void __launch_bounds__(256) k1d_stage(Args1 A, StageCoef sc, int tile
             const int side = row >= P, a = row - side * P;
             const int *mp = smp + l * 6 + 3 * side;
             const int m = mp[2] ? (N - n) : n;
-            A.qb2[(((int64_t)mp[0] * 3 + mp[1]) * P + a) * NP1 + m] = x;
+            if (DGH_IN_RANGE(A.err, mp[0], A.T)) A.qb2[(((int64_t)mp[0] * 3 + mp[1]) * P + a) * NP1 + m] = x;
             const float q0 = x + rp[row];
             A.q0[(lg * 2 + side) * P * NP1 + a * NP1 + n] = q0;
             s0[(l * 2 + side) * P * NP1 + a * NP1 + n] = q0;
@@ -614,7 +640,8 @@ __global__ void __launch_bounds__(256) k0d_stage(Args0 A) {
     const int *cd = A.corner + c * 6;
     for (int i = threadIdx.x; i < R; i += blockDim.x) {
         const int slot = i / S, s = i % S;
-        const int l = cd[2 * slot], e = cd[2 * slot + 1];
+        const int l0 = cd[2 * slot], e = cd[2 * slot + 1];
+        const int l = DGH_IN_RANGE(A.err, l0, A.L) ? l0 : 0;
         const float *tr = A.tr1 + ((int64_t)l * S + s) * 4 + e * 2;
         rp[i] = 0.5f * (tr[0] + A.cornerZ[c * 3 + slot] * tr[1]);
     }
@@ -639,7 +666,7 @@ __global__ void __launch_bounds__(256) k0d_stage(Args0 A) {
             for (int k = 0; k < (two ? 2 : 1); ++k) {
                 const int row = i + k, slot = row / S, s = row % S;
                 const int l = cd[2 * slot], e = cd[2 * slot + 1];
-                A.qb1[((int64_t)l * 2 + e) * S + s] = k ? x1 : x0;
+                if (DGH_IN_RANGE(A.err, l, A.L)) A.qb1[((int64_t)l * 2 + e) * S + s] = k ? x1 : x0;
             }
     }
 }

@@ -37,6 +37,16 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_checked_build_exports_the_same_symbols(lib):
+    """The index-checked variant (DGH_CHECKED) is the same ABI."""
+    path = build.build(checked=True)
+    chk = ctypes.CDLL(path)
+    for n in sorted(declared_symbols()):
+        assert hasattr(chk, n), n
+    assert chk.dgh_is_checked_build() == 1
+    assert lib.dgh_is_checked_build() == 0
+
+
 def test_error_paths_without_gpu(lib):
     dgh.load_library()
     L = dgh._lib
