@@ -313,6 +313,7 @@ class Solver:
             raise DghError(rc, lib.dgh_last_error(None).decode())
         self._h = h
         self._lib = lib
+        self.precision = int(precision)
         self.N, self.P = int(N), int(P)
 
     # ------------------------------------------------------------ helpers
@@ -498,11 +499,54 @@ class Solver:
         o.thr1 = cur["thr1"] if thr1 is None else int(thr1)
         self._check(self._lib.dgh_set_launch(self._h, ctypes.byref(o)))
 
-    def tune(self, steps=5):
-        """Autotune the launch shape (results unchanged); returns (ms/step before, after)."""
+    def tune(self, steps=5, cache=None):
+        """Autotune the launch shape (results unchanged); returns (ms/step
+        before, after).  With cache (a JSON file path), a shape stored for the
+        same key (tune_cache_key) is applied instead of searching, and a new
+        search result is stored."""
+        key = tune_cache_key(self.info, self.precision) if cache else None
+        if cache:
+            hit = tune_cache_load(cache).get(key)
+            if hit is not None:
+                self.set_launch(**{k: hit[k] for k in TUNABLE})
+                return hit["ms_before"], hit["ms_after"]
         a, b = ctypes.c_double(), ctypes.c_double()
         self._check(self._lib.dgh_tune(self._h, int(steps), ctypes.byref(a), ctypes.byref(b)))
+        if cache:
+            L = self.launch
+            tune_cache_store(cache, key, dict({k: L[k] for k in TUNABLE}, ms_before=a.value, ms_after=b.value))
         return a.value, b.value
+
+
+TUNABLE = ("tile2", "tile1", "cta3_per_sm", "thr2", "thr1")
+
+
+def tune_cache_key(info, precision):
+    """Key of a tuned launch shape in a tuning cache: the orders, the
+    precision mode and the sizes of every level (a cache file belongs to one
+    machine and build)."""
+    return "N%d_P%d_prec%d_K%d_T%d_L%d_C%d" % (info["order"], info["habc_order"], int(precision), info["n_cells"],
+                                               info["n_tris"], info["n_lines"], info["n_corners"])
+
+
+def tune_cache_load(path):
+    """The cache {key: shape}; empty when the file does not exist."""
+    import json
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
+def tune_cache_store(path, key, shape):
+    """Adds or replaces one entry (written to a temporary file, then renamed)."""
+    import json
+    data = tune_cache_load(path)
+    data[key] = shape
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 class Batch:
