@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dgh.h"
 #include "kernels.cuh"
 #include "setup.h"
@@ -18,6 +20,14 @@
 using namespace dgh;
 
 namespace {
+
+// NVTX range over one API call, so that a profiler's timeline groups the
+// kernels of a call under its name (no cost without an attached tool).
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+};
+
 
 // Carpenter & Kennedy (1994) 5-stage 2N-storage RK4 coefficients.
 const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
@@ -1226,6 +1236,7 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
 extern "C" {
 
 int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
+    ApiRange nvtx_range("dgh_create");
     if (!out) {
         g_create_error = "out is NULL";
         return DGH_EINVAL;
@@ -1369,6 +1380,7 @@ int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp
 }
 
 int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count) {
+    ApiRange nvtx_range("dgh_set_state");
     if (!ctx || (!in && count)) return DGH_EINVAL;
     size_t n;
     if (level_count(ctx, level, n) || n != count) {
@@ -1383,6 +1395,7 @@ int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count) {
 }
 
 int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count) {
+    ApiRange nvtx_range("dgh_get_state");
     if (!ctx || (!out && count)) return DGH_EINVAL;
     size_t n;
     if (level_count(ctx, level, n) || n != count) {
@@ -1464,6 +1477,7 @@ int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double
 }
 
 int dgh_step(dgh_ctx *ctx, int64_t nsteps) {
+    ApiRange nvtx_range("dgh_step");
     if (!ctx || nsteps < 0) return DGH_EINVAL;
     if (ctx->dirty) {
         int rc = run_closure(ctx);
@@ -1853,6 +1867,7 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
 }  // namespace
 
 extern "C" int dgh_tune(dgh_ctx *ctx, int steps, double *ms_before, double *ms_after) {
+    ApiRange nvtx_range("dgh_tune");
     if (!ctx || steps < 1) return DGH_EINVAL;
     const int64_t sc0 = ctx->step_count;
     int rc = tune_contexts(
@@ -2167,6 +2182,7 @@ int dgh_batch_count(const dgh_batch *b, int *n_problems, int *n_groups) {
 }
 
 int dgh_batch_step(dgh_batch *b, int64_t nsteps) {
+    ApiRange nvtx_range("dgh_batch_step");
     if (!b || nsteps < 0) return DGH_EINVAL;
     for (dgh_ctx *u : b->groups)
         if (u->dirty) {
@@ -2303,6 +2319,7 @@ int dgh_batch_get_launch(const dgh_batch *b, int group, dgh_launch *o) {
 }
 
 int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after) {
+    ApiRange nvtx_range("dgh_batch_tune");
     if (!b || steps < 1) return DGH_EINVAL;
     const int64_t sc0 = b->step_count;
     std::vector<int64_t> gsc;
@@ -2515,6 +2532,7 @@ int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n,
 
 int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
                   double *final_mse) {
+    ApiRange nvtx_range("dgh_mlp_train");
     if (!X || !Y || n < 2 || !cfg || !w_out || cfg->steps < 0 || cfg->batch < 1 || !(cfg->lr > 0.f))
         return mlp_fail("mlp train: invalid arguments", DGH_EINVAL);
     int sms = 1, rc = mlp_setup(sms);
