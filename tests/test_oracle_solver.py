@@ -146,6 +146,41 @@ def test_gaussian_pulse_exact_solution():
     assert errs[1] < 0.03 and errs[1] < errs[0] / 6, errs
 
 
+def _gaussian_exact_at(m, t, sigma, x0):
+    """The free-space spherical pulse of _gaussian_exact, centred at x0."""
+    class Shifted:
+        pass
+    sm = Shifted()
+    sm.x, sm.K, sm.ref3 = m.x - np.asarray(x0, dtype=float), m.K, m.ref3
+    return _gaussian_exact(sm, t, sigma)
+
+
+def test_free_surface_matches_the_method_of_images():
+    """A p = 0 face (Sec. 2.4) acts as a mirror with a sign change: in the
+    half-space the exact field of a pulse at x0 is the free-space field of x0
+    minus that of its mirror image x0' (method of images).  Pulse 0.45 from
+    the +z face, compared at t = 0.35, when a large part of it has reflected
+    while the other faces are still out of reach.  The image solution must be
+    matched far better than the free-space field alone."""
+    sigma, T, N, n = 0.25, 0.35, 3, 8
+    x0, xi = [0.0, 0.0, 0.55], [0.0, 0.0, 1.45]     # +z face at z = 1
+    m = make(n, N, 0, bc=[BC_HABC] * 5 + [BC_DIRICHLET], jitter=0.02, seed=5)
+    s = Solver(m)
+    Y = s.zero_state()
+    Y["q3"] = _gaussian_exact_at(m, 0.0, sigma, x0) - _gaussian_exact_at(m, 0.0, sigma, xi)
+    E0 = s.energy(Y)
+    nst = int(math.ceil(T / m.dt_rule()))
+    Y, _, _ = s.run(Y, 0.0, T / nst, nst)
+    img = _gaussian_exact_at(m, T, sigma, x0) - _gaussian_exact_at(m, T, sigma, xi)
+    free = _gaussian_exact_at(m, T, sigma, x0)
+
+    def err(ref):
+        return math.sqrt(s.energy({"q3": Y["q3"] - ref, "q2": Y["q2"], "q1": Y["q1"]}) / E0)
+
+    e_img, e_free = err(img), err(free)
+    assert e_img < 0.03 and e_free > 8 * e_img, (e_img, e_free)
+
+
 @pytest.mark.parametrize("bc", [BC_HABC, BC_DIRICHLET])
 def test_energy_non_increasing(bc):
     """Upwind DG with the basic ABC (HABC of order 0) or p = 0: the discrete
