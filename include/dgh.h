@@ -155,6 +155,25 @@ int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count);
  * p_ab = p*_ab + C_ba Q_A,a + C_ab Q_B,b (eq. proc:pij0Star). */
 int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count);
 
+/* Initial state from 3D fields: q3d [K][4][Np] in canonical order (as
+ * dgh_get_state level 3); every auxiliary field, the time and the step count
+ * are set to zero, as by dgh_init_gaussian.  DGH_EINVAL on a size mismatch. */
+int dgh_init_fields(dgh_ctx *ctx, const double *q3d, size_t count);
+
+/* Changes the material: c, rho per cell (count = number of cells, positive
+ * and finite).  The set-up that depends on it (impedances, upwind
+ * coefficients of every level, time step unless the description fixed dt) is
+ * rebuilt; the fields of all levels, the time, the step count, the point
+ * sources, the launch shape and the watchdog carry over (the handle stays
+ * valid).  A learned closure and a recording shadow chain are removed.  On
+ * an error the context is unchanged.  DGH_ESTATE for a batch group. */
+int dgh_set_material(dgh_ctx *ctx, const double *c, const double *rho, size_t count);
+
+/* Horizontal layers, bottom to top: layer l holds the cells whose centroid
+ * has z < z_top[l] (z_top increasing, nlayers - 1 values); the last layer
+ * takes the rest.  Then as dgh_set_material. */
+int dgh_set_material_layers(dgh_ctx *ctx, int nlayers, const double *z_top, const double *c, const double *rho);
+
 /* Sets the simulated time (the step count is unchanged). */
 int dgh_set_time(dgh_ctx *ctx, double t);
 

@@ -96,6 +96,9 @@ def load_library(path=LIB_PATH):
         "dgh_get_state": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
         "dgh_get_fields": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
         "dgh_set_time": (ctypes.c_int, [P, ctypes.c_double]),
+        "dgh_init_fields": (ctypes.c_int, [P, D, ctypes.c_size_t]),
+        "dgh_set_material": (ctypes.c_int, [P, D, D, ctypes.c_size_t]),
+        "dgh_set_material_layers": (ctypes.c_int, [P, ctypes.c_int, D, D, D]),
         "dgh_add_point_source": (ctypes.c_int, [P, D, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "dgh_step": (ctypes.c_int, [P, ctypes.c_int64]),
         "dgh_set_watchdog": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_double]),
@@ -391,6 +394,30 @@ class Solver:
 
     def set_time(self, t):
         self._check(self._lib.dgh_set_time(self._h, float(t)))
+
+    def init_fields(self, q3):
+        """Initial state from 3D fields [K][4][Np] (canonical order); auxiliary
+        fields, time and step count to zero."""
+        q = np.ascontiguousarray(q3, dtype=np.float64)
+        self._check(self._lib.dgh_init_fields(self._h, _dptr(q), q.size))
+
+    def set_material(self, c, rho):
+        """New material (c, rho per cell); the state carries over."""
+        K = self.info["n_cells"]
+        cc = np.ascontiguousarray(np.broadcast_to(np.asarray(c, np.float64), (K,)))
+        rr = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, np.float64), (K,)))
+        self._check(self._lib.dgh_set_material(self._h, _dptr(cc), _dptr(rr), K))
+
+    def set_material_layers(self, z_top, c, rho):
+        """Horizontal layers bottom to top: layer l holds cell centroids with
+        z < z_top[l]; len(c) = len(rho) = len(z_top) + 1."""
+        z = np.ascontiguousarray(z_top, dtype=np.float64)
+        cc = np.ascontiguousarray(c, dtype=np.float64)
+        rr = np.ascontiguousarray(rho, dtype=np.float64)
+        if cc.size != z.size + 1 or rr.size != cc.size:
+            raise ValueError("need len(c) == len(rho) == len(z_top) + 1")
+        self._check(self._lib.dgh_set_material_layers(self._h, int(cc.size), _dptr(z) if z.size else None,
+                                                      _dptr(cc), _dptr(rr)))
 
     def set_watchdog(self, every, energy_limit=0.0):
         """Energy watchdog (dgh_set_watchdog): every `every` steps, step()

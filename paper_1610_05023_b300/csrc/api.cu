@@ -63,6 +63,8 @@ struct dgh_ctx {
     int C = 0;
     int M = 1;
     double dt = 0.0, t0 = 0.0;
+    double cfl = 1.0;                 // time-step rule factor of the description
+    bool dt_fixed = false;            // dt given in the description (kept by dgh_set_material)
     int64_t step_count = 0;
     int64_t wd_every = 0;     // energy watchdog: check every wd_every steps (0 = off)
     double wd_limit = 0.0;    // energy bound (<= 0: finiteness only)
@@ -1255,7 +1257,9 @@ int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
         dgh_destroy(ctx);
         return rc;
     }
-    ctx->dt = d->dt > 0.0 ? d->dt : dt_rule(ctx->mesh, d->cfl > 0.0 ? d->cfl : 1.0);
+    ctx->cfl = d->cfl > 0.0 ? d->cfl : 1.0;
+    ctx->dt_fixed = d->dt > 0.0;
+    ctx->dt = d->dt > 0.0 ? d->dt : dt_rule(ctx->mesh, ctx->cfl);
     rc = build_context(ctx, {0, ctx->mesh.K});
     if (rc) {
         g_create_error = ctx->err;
@@ -1377,6 +1381,105 @@ int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp
     ctx->dirty = true;
     CK(cudaStreamSynchronize(ctx->stream));
     return DGH_OK;
+}
+
+int dgh_init_fields(dgh_ctx *ctx, const double *q3d, size_t count) {
+    if (!ctx || !q3d) return DGH_EINVAL;
+    size_t n;
+    level_count(ctx, 3, n);
+    if (count != n) {
+        ctx->err = "state size mismatch";
+        return DGH_EINVAL;
+    }
+    const double x0[3] = {0.0, 0.0, 0.0};
+    int rc = dgh_init_gaussian(ctx, x0, 1.0, 0.0);   // every level and the clock to zero
+    if (rc) return rc;
+    return dgh_set_state(ctx, 3, q3d, count);
+}
+
+int dgh_set_material(dgh_ctx *ctx, const double *c, const double *rho, size_t count) {
+    if (!ctx || !c || !rho) return DGH_EINVAL;
+    if (count != size_t(ctx->mesh.K)) {
+        ctx->err = "material: one (c, rho) per cell";
+        return DGH_EINVAL;
+    }
+    if (ctx->no_overlap || ctx->part_blk0.size() > 2) {
+        ctx->err = "material: not for a batch group";
+        return DGH_ESTATE;
+    }
+    for (size_t k = 0; k < count; ++k)
+        if (!(c[k] > 0.0) || !(rho[k] > 0.0) || !std::isfinite(c[k]) || !std::isfinite(rho[k])) {
+            ctx->err = "material: c and rho must be positive and finite";
+            return DGH_EINVAL;
+        }
+    // the state (all levels, time, step count) moves through a checkpoint blob
+    size_t sz = 0;
+    int rc = dgh_save_state(ctx, nullptr, &sz);
+    if (rc) return rc;
+    std::vector<char> blob(sz);
+    if ((rc = dgh_save_state(ctx, blob.data(), &sz))) return rc;
+    dgh_ctx *n = new dgh_ctx();
+    n->stream = ctx->stream;
+    n->device = ctx->device;
+    n->N = ctx->N;
+    n->P = ctx->P;
+    n->precision = ctx->precision;
+    n->mesh = ctx->mesh;
+    n->mesh.c.assign(c, c + count);
+    n->mesh.rho.assign(rho, rho + count);
+    n->ref3 = ctx->ref3;
+    n->ref2 = ctx->ref2;
+    n->ref1 = ctx->ref1;
+    n->habc = ctx->habc;
+    n->cfl = ctx->cfl;
+    n->dt_fixed = ctx->dt_fixed;
+    n->dt = ctx->dt_fixed ? ctx->dt : dt_rule(n->mesh, ctx->cfl);
+    n->t0 = ctx->t0;
+    auto give_up = [&](int code) {
+        ctx->err = n->err;
+        dgh_destroy(n);
+        return code;
+    };
+    if ((rc = build_context(n, {0, n->mesh.K}))) return give_up(rc);
+    // sources, launch shapes and the watchdog carry over; the closure and a
+    // recording shadow chain do not (set them again)
+    n->src = ctx->src;
+    if (ctx->src.n > 0 && cudaMemcpy(n->srcvec, ctx->srcvec, sizeof(float) * MAXSRC * ctx->Np,
+                                     cudaMemcpyDeviceToDevice) != cudaSuccess)
+        return give_up(DGH_ECUDA);
+    n->tile2 = ctx->tile2;
+    n->tile1 = ctx->tile1;
+    n->cta3_per_sm = ctx->cta3_per_sm;
+    n->thr2 = ctx->thr2;
+    n->thr1 = ctx->thr1;
+    if (dispatchN<Shapes>(n->N, n) != DGH_OK) return give_up(DGH_EINVAL);
+    n->wd_every = ctx->wd_every;
+    n->wd_limit = ctx->wd_limit;
+    if ((rc = dgh_load_state(n, blob.data(), sz))) return give_up(rc);
+    std::swap(*ctx, *n);   // the handle keeps its address; n now holds the old context
+    dgh_destroy(n);
+    return DGH_OK;
+}
+
+int dgh_set_material_layers(dgh_ctx *ctx, int nlayers, const double *z_top, const double *c, const double *rho) {
+    if (!ctx || nlayers < 1 || !c || !rho || (nlayers > 1 && !z_top)) return DGH_EINVAL;
+    for (int l = 0; l + 2 < nlayers; ++l)
+        if (!(z_top[l] < z_top[l + 1])) {
+            ctx->err = "material layers: z_top must increase";
+            return DGH_EINVAL;
+        }
+    const HostMesh &m = ctx->mesh;
+    std::vector<double> cc(size_t(m.K)), rr(size_t(m.K));
+    for (int64_t k = 0; k < m.K; ++k) {
+        double z = 0.0;
+        for (int v = 0; v < 4; ++v) z += m.VX[size_t(m.EToV[size_t(k) * 4 + v]) * 3 + 2];
+        z *= 0.25;
+        int l = 0;
+        while (l < nlayers - 1 && z_top[l] <= z) ++l;   // layer l holds z < z_top[l]
+        cc[size_t(k)] = c[l];
+        rr[size_t(k)] = rho[l];
+    }
+    return dgh_set_material(ctx, cc.data(), rr.data(), cc.size());
 }
 
 int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count) {
