@@ -431,6 +431,12 @@ int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n,
 int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
                   double *final_mse);
 
+/* Trains the closure on the rows this context has recorded
+ * (dgh_closure_record): the same training as dgh_mlp_train on their
+ * features and targets.  DGH_ESTATE without recording or with fewer than 2
+ * rows. */
+int dgh_closure_train(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist, double *final_mse);
+
 #ifdef __cplusplus
 }
 #endif

@@ -143,6 +143,7 @@ def load_library(path=LIB_PATH):
                                              ctypes.POINTER(ctypes.c_float)]),
         "dgh_mlp_train": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
                                          ctypes.POINTER(_TrainCfg), ctypes.POINTER(ctypes.c_float), D, D]),
+        "dgh_closure_train": (ctypes.c_int, [P, ctypes.POINTER(_TrainCfg), ctypes.POINTER(ctypes.c_float), D, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -496,6 +497,16 @@ class Solver:
         from a hashed fraction of the boundary face nodes (dgh_closure_record)."""
         self._check(self._lib.dgh_closure_record(self._h, int(shadow_order), int(every), float(fraction),
                                                  int(max_samples), int(seed)))
+
+    def closure_train(self, steps=2000, batch=4096, lr=1e-3, seed=1, beta1=0.9, beta2=0.999, eps=1e-8):
+        """Train the closure on this solver's recorded rows (dgh_closure_train);
+        returns (weights, minibatch MSE history, final MSE) like mlp_train."""
+        cfg = _TrainCfg(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(seed))
+        w = np.empty(MLP_NPARAM, np.float32)
+        hist = np.empty(max(int(steps), 1))
+        fin = ctypes.c_double()
+        self._check(self._lib.dgh_closure_train(self._h, ctypes.byref(cfg), _fptr(w), _dptr(hist), ctypes.byref(fin)))
+        return w, hist[:int(steps)], fin.value
 
     def closure_samples(self, max_rows=None):
         """Recorded rows [n][7]: 6 features and the target.  Open-loop rows

@@ -2546,6 +2546,27 @@ int dgh_closure_samples(dgh_ctx *ctx, float *out, int64_t max_rows, int64_t *cou
     return DGH_OK;
 }
 
+int dgh_closure_train(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist, double *final_mse) {
+    if (!ctx || !cfg || !w_out) return DGH_EINVAL;
+    int64_t n = 0;
+    int rc = dgh_closure_samples(ctx, nullptr, 0, &n);
+    if (rc) return rc;
+    if (n < 2) {
+        ctx->err = "closure train: fewer than 2 recorded rows";
+        return DGH_ESTATE;
+    }
+    std::vector<float> rows(static_cast<size_t>(n) * SAMPLE_W), X(static_cast<size_t>(n) * MLP_IN),
+        Y(static_cast<size_t>(n));
+    if ((rc = dgh_closure_samples(ctx, rows.data(), n, &n))) return rc;
+    for (int64_t r = 0; r < n; ++r) {
+        for (int i = 0; i < MLP_IN; ++i) X[size_t(r) * MLP_IN + i] = rows[size_t(r) * SAMPLE_W + i];
+        Y[size_t(r)] = rows[size_t(r) * SAMPLE_W + MLP_IN];
+    }
+    rc = dgh_mlp_train(X.data(), Y.data(), n, cfg, w_out, loss_hist, final_mse);
+    if (rc) ctx->err = dgh_last_error(nullptr);
+    return rc;
+}
+
 }  // extern "C"
 
 namespace {

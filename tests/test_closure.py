@@ -164,6 +164,23 @@ def test_closed_loop_recorder_rows_match_open_loop_rows_at_the_first_step():
 
 
 @pytest.mark.gpu
+def test_closure_train_on_recorded_rows_equals_mlp_train():
+    """dgh_closure_train trains on the context's recorded rows exactly as
+    dgh_mlp_train on the same rows read back (fixed-order reductions)."""
+    g = _solver(6)
+    g.closure_record(shadow_order=2, every=2, fraction=0.5, max_samples=1 << 20, seed=4)
+    g.init_gaussian([0.3, 0.2, -0.1], 0.3)
+    g.step(40)
+    S = g.closure_samples()
+    w1, h1, f1 = g.closure_train(steps=50, batch=256, lr=1e-3, seed=5)
+    w2, h2, f2 = dgh.mlp_train(S[:, :6], S[:, 6], steps=50, batch=256, lr=1e-3, seed=5)
+    assert np.array_equal(w1, w2) and np.array_equal(h1, h2) and f1 == f2
+    fresh = _solver(2)
+    with pytest.raises(dgh.DghError):
+        fresh.closure_train(steps=5)               # nothing recorded
+
+
+@pytest.mark.gpu
 def test_closure_zero_output_is_bit_identical_and_output_changes_solution():
     w = _weights(11).astype(np.float32)
     o3 = C.NPARAM - C.NH - 1
