@@ -1,7 +1,8 @@
 """The index-checked build (libdgh_checked.so, -DDGH_CHECKED) in place of a
 memory checker: every index that a stage kernel gathers through or pushes to
 is tested against its array.  A child process runs a spread of configurations
-under the checked library; dgh_sync must report no violation (DGH_EBOUNDS),
+under the checked library (single problems, a batch of uneven problems, a
+recording shadow chain); dgh_sync must report no violation (DGH_EBOUNDS),
 and every level must be bit-identical to the normal build.  No index is
 corrupted on purpose: the checks guard the set-up code, not a planted fault."""
 import os
@@ -41,6 +42,31 @@ def run_cases(steps=12):
         for lv in (3, 2, 1):
             out["c%d_l%d" % (i, lv)] = g.get_state(lv)
         g.close()
+    # a batch of uneven problems (one union context per (N, P) group)
+    probs = []
+    for j, (n, N, P) in enumerate([(2, 3, 2), (3, 4, 2), (2, 3, 2)]):
+        VX, EToV = W.kuhn_mesh(n, 1.0, 0.03, seed=80 + j)
+        g = dgh.Solver(VX, EToV, N, P)
+        g.add_point_source([0.1 * j, 0.0, 0.1], 3.0, 0.3)
+        g.init_gaussian([0.0, 0.1, 0.0], 0.3, 0.0)
+        probs.append(g)
+    b = dgh.Batch(probs)
+    b.step(steps)
+    b.sync()
+    for j in range(len(probs)):
+        for lv in (3, 2, 1):
+            out["b%d_l%d" % (j, lv)] = b.get_state(j, lv)
+    b.close()
+    # the closure's recording shadow chain (its own 2D, 1D and 0D launches)
+    VX, EToV = W.kuhn_mesh(2, 1.0, 0.03, seed=90)
+    g = dgh.Solver(VX, EToV, 3, 4)
+    g.closure_record(shadow_order=2, every=3, fraction=1.0, max_samples=1 << 18, seed=9)
+    g.init_gaussian([0.2, -0.1, 0.15], 0.3)
+    g.step(steps)
+    g.sync()
+    S = g.closure_samples()
+    out["shadow_rows"] = S[np.lexsort(S.T[::-1])]
+    g.close()
     return out
 
 
