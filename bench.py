@@ -32,7 +32,7 @@ WORKLOAD = {"workload": "cube48_N4_P6_gaussian", "mesh": "48^3 hex x 6 Kuhn tets
 METRIC = "DOF-updates/s per RK stage"
 SEED = 2000
 # dram__bytes_read.sum + dram__bytes_write.sum of k3d_stage<4> for one full stage (interior and
-# boundary-cell launches) of this workload, from one ncu capture of this build (one pass)
+# boundary-cell launches) of this workload, from one ncu capture of the current kernel (one pass)
 K3D_TRAFFIC_BYTES = 2092811264 + 71113984
 
 
