@@ -8,7 +8,10 @@ so the checks are properties that hold at any size:
   stream bit for bit (each cell's arithmetic does not depend on scheduling);
 * with the basic ABC (P = 0) the discrete energy never increases;
 * against the exact solution of a Gaussian pulse in free space the error is
-  at least 10 times below the oracle's own error on a 6x coarser mesh.
+  at least 10 times below the oracle's own error on a 6x coarser mesh;
+* sampled cells: one step of the full-size run, from its own state, equals
+  the oracle's step of a block of hexes cut out around them (patch_sampling:
+  the cells are far enough inside the block that the cut cannot reach them).
 """
 import math
 
@@ -107,3 +110,47 @@ def test_fullsize_gaussian_pulse_against_exact_solution(mesh48):
     err8 = math.sqrt(o.energy(d) / E0)
     print("energy-norm error vs exact: 48^3 GPU %.3e, 8^3 oracle %.3e" % (err48, err8))
     assert err48 <= 0.1 * err8
+
+
+def test_fullsize_one_step_matches_oracle_on_sampled_cells(mesh48):
+    """Sec. 3.2 / Appendix A at full size: the GPU state after 40 steps is
+    stepped once more on the GPU (tuned shapes, graph replay) and once by the
+    FP64 oracle on two 12^3-hex blocks (at the pulse and on its flank); the
+    2^3 central hexes (48 tets, 6,720 values each) must agree per field.
+    Bounds: the state within 1e-6 relative (the FP32 contract is 1e-5), the
+    one-step increment within 1e-4 of its own norm; measured on a B300 at most
+    9.2e-8 and 1.4e-5."""
+    import torch
+    from oracle.mesh import BC_HABC
+    from oracle.solver import Solver
+    from patch_sampling import patch_and_centre, patch_mesh
+    VX, EToV, x0 = mesh48
+    s = torch.cuda.Stream()
+    g = dgh.Solver(VX, EToV, 4, 6, stream=s)
+    g.init_gaussian(x0, 0.1)
+    g.tune(steps=2)
+    g.step(40)
+    g.sync()
+    Yk = g.get_state(3)
+    t, dt = g.info["time"], g.info["dt"]
+    g.step(1)
+    g.sync()
+    Yk1 = g.get_state(3)
+    g.close()
+    c = np.floor((np.asarray(x0) + 1.0) / (2.0 / N48)).astype(int)
+    for centre in (c, c - 3):
+        tets, cen, pos = patch_and_centre(N48, centre)
+        o = Solver(patch_mesh(VX, EToV, tets, 4, BC_HABC))
+        Y = o.zero_state()
+        Y["q3"][:] = Yk[tets]
+        res = {k: np.zeros_like(v) for k, v in Y.items()}
+        o.step(Y, res, t, dt)
+        ref, gpu, start = Y["q3"][pos], Yk1[cen], Yk[cen]
+        for f in range(4):
+            e_state = np.linalg.norm(gpu[:, f] - ref[:, f]) / np.linalg.norm(ref[:, f])
+            d_ref = ref[:, f] - start[:, f]
+            e_incr = np.linalg.norm((gpu[:, f] - start[:, f]) - d_ref) / np.linalg.norm(d_ref)
+            where = tuple(int(v) for v in centre)
+            print("block at hex %s field %d: state %.2e, one-step increment %.2e" % (where, f, e_state, e_incr))
+            assert e_state <= 1e-6, (where, f, e_state)
+            assert e_incr <= 1e-4, (where, f, e_incr)

@@ -1,0 +1,52 @@
+"""The sampling argument of the full-size GPU check, on the oracle alone: one
+LSERK4 step of a block of hexes cut out of the 48^3 benchmark mesh leaves the
+cells MARGIN = 5 hexes inside the block independent of what happens at the cut
+(the cut condition, the block size).  MARGIN is the plain bound: one step
+carries a change at most four face hops (five stages), and each hop moves at
+most one hex.  Kuhn tetrahedra are slower: a tet has one face on a low side and
+one on a high side of its hex, on different axes, so moving one hex along an
+axis takes three hops and a margin of 2 is already enough, while a margin of 1
+is not (the negative control)."""
+import numpy as np
+
+from oracle.mesh import BC_DIRICHLET, BC_HABC
+from oracle.solver import Solver
+from paper_1610_05023_b300 import workloads as W
+from patch_sampling import MARGIN, hex_tets, patch_and_centre, patch_mesh
+
+N48 = 48
+
+
+def _one_step(VX, EToV, tets, bc, x0, dt=5e-4):
+    m = patch_mesh(VX, EToV, tets, 4, bc)
+    o = Solver(m)
+    Y = o.gaussian_state(x0, 0.1)
+    Y["q3"][:, 1] = 0.3 * Y["q3"][:, 0]          # a velocity field as well
+    Y["q3"][:, 3] = -0.2 * Y["q3"][:, 0]
+    res = {k: np.zeros_like(v) for k, v in Y.items()}
+    o.step(Y, res, 0.0, dt)
+    return Y["q3"]
+
+
+def test_sampled_cells_do_not_see_the_cut_within_one_step():
+    VX, EToV = W.kuhn_mesh(N48, 1.0, 0.02, seed=2000)
+    x0 = W.seeded_point(2000, [0.70, 0.65, 0.60], 0.05)
+    c = np.floor((np.asarray(x0) + 1.0) / (2.0 / N48)).astype(int)
+    tets, cen, pos = patch_and_centre(N48, c)
+    abc = _one_step(VX, EToV, tets, BC_HABC, x0)[pos]
+    dirichlet = _one_step(VX, EToV, tets, BC_DIRICHLET, x0)[pos]
+    # a larger block: the same compared cells, now MARGIN + 2 hexes from the cut
+    big = hex_tets(N48, c - MARGIN - 2, 2 + 2 * (MARGIN + 2))
+    larger = _one_step(VX, EToV, big, BC_HABC, x0)[np.searchsorted(big, cen)]
+    scale = np.abs(abc).max()
+    assert scale > 0.5
+    # the per-cell arithmetic is the same in all three runs: equal up to the
+    # summation order of the library matrix products (bitwise in practice)
+    assert np.abs(abc - dirichlet).max() <= 1e-14 * scale
+    assert np.abs(abc - larger).max() <= 1e-14 * scale
+    # one hex from the cut the cut condition does reach them; two are enough
+    for margin, seen in ((1, True), (2, False)):
+        near = hex_tets(N48, c - margin, 2 + 2 * margin)
+        p2 = np.searchsorted(near, cen)
+        d = np.abs(_one_step(VX, EToV, near, BC_HABC, x0)[p2] - _one_step(VX, EToV, near, BC_DIRICHLET, x0)[p2])
+        assert (d.max() > 1e-6 * scale) == seen, (margin, d.max())
