@@ -62,8 +62,10 @@ def patch_and_centre(n, centre_hex, inner=2):
     return tets, cen, pos
 
 
-def patch_mesh(VX, EToV, tets, N, bc_code):
-    """The oracle mesh of a block (P = 0, the same code on all six sides)."""
+def patch_mesh(VX, EToV, tets, N, bc_code, c=1.0, rho=1.0):
+    """The oracle mesh of a block (P = 0, the same code on all six sides);
+    c and rho are scalars or per-tet arrays of the whole mesh."""
     E = EToV[tets]
     v = VX[E].reshape(-1, 3)
-    return PatchMesh(VX, E, N, 0, [bc_code] * 6, 1.0, 1.0, lo=v.min(0), hi=v.max(0))
+    pick = lambda a: np.asarray(a, float)[tets] if np.ndim(a) else float(a)
+    return PatchMesh(VX, E, N, 0, [bc_code] * 6, pick(rho), pick(c), lo=v.min(0), hi=v.max(0))

@@ -140,3 +140,65 @@ def test_batch_groups_by_precision():
     b.step(10)
     assert _rel(batch.get_state(0, 3), a.get_state(3)) <= 2e-6
     assert _rel(batch.get_state(1, 3), b.get_state(3)) <= 2e-5
+
+
+# one step from a smooth state at full size, per precision: bounds on the
+# state and on the one-step increment (relative L2 per field), about three
+# times the largest values measured on a B300 (state / increment: FP32 6.1e-8 /
+# 1.9e-5, split BF16 1.1e-6 / 2.6e-4, FP16 5.9e-5 / 1.5e-2, BF16 7.3e-4 / 0.17)
+FULL_TOL = {dgh.PREC_FP32: (2e-7, 6e-5), dgh.PREC_SPLIT_BF16: (3e-6, 8e-4),
+            dgh.PREC_FP16_TC: (2e-4, 5e-2), dgh.PREC_BF16_TC: (2e-3, 0.5)}
+
+
+def test_precision_fullsize_one_step_on_sampled_cells():
+    """The precision form's workload at full size: 32^3 x 6 = 196,608 tets,
+    N = 6, three layers (c, rho) = (1, 1), (1.5, 1.2), (2, 1.5), HABC P = 4,
+    each precision on its own stream as in the benchmark.  From one smooth
+    state (two Gaussian pulses with a velocity field), one step of every
+    precision against the FP64 oracle's step of 12^3-hex blocks cut out
+    around two sampled 2^3-hex groups: one inside the top layer, one across
+    the interface z = 1/3 (heterogeneous upwind flux, Sec. 2.3)."""
+    import torch
+    from patch_sampling import patch_and_centre, patch_mesh
+    n, N = 32, 6
+    h = 2.0 / n
+    VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=3000)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.0, 1.5, 2.0], [1.0, 1.2, 1.5])
+    centres = [np.array([20, 12, 25]), np.array([8, 18, 20])]   # hexes 20 | 21 straddle z = 1/3
+    g = dgh.Solver(VX, EToV, N, 4, c=c, rho=rho)
+    x = g.nodes(3)
+    dt = g.info["dt"]
+    g.close()
+    Y0 = np.zeros((x.shape[0], 4, x.shape[1]))
+    for cc in centres:
+        Y0[:, 0] += np.exp(-np.sum((x - (-1.0 + (cc + 1) * h)) ** 2, axis=2) / 0.1 ** 2)
+    Y0[:, 1], Y0[:, 2], Y0[:, 3] = 0.3 * Y0[:, 0], -0.2 * Y0[:, 0], 0.25 * Y0[:, 0]
+    Y0 = Y0.astype(np.float32).astype(np.float64)        # the values the GPU holds
+    ref = []
+    for cc in centres:
+        tets, cen, pos = patch_and_centre(n, cc)
+        o = Solver(patch_mesh(VX, EToV, tets, N, BC_HABC, c, rho))
+        Y = o.zero_state()
+        Y["q3"][:] = Y0[tets]
+        res = {k: np.zeros_like(v) for k, v in Y.items()}
+        o.step(Y, res, 0.0, dt)
+        ref.append((cen, Y["q3"][pos]))
+    assert np.unique(c[ref[1][0]]).size == 2            # the second group spans two layers
+    for prec in (dgh.PREC_FP32, dgh.PREC_SPLIT_BF16, dgh.PREC_FP16_TC, dgh.PREC_BF16_TC):
+        st = torch.cuda.Stream()
+        g = dgh.Solver(VX, EToV, N, 4, c=c, rho=rho, stream=st, precision=prec)
+        assert g.info["dt"] == dt
+        g.set_state(3, Y0)
+        g.step(1)
+        g.sync()
+        q3 = g.get_state(3)
+        g.close()
+        tol_s, tol_i = FULL_TOL[prec]
+        for (cen, r), cc in zip(ref, centres):
+            for f in range(4):
+                e_s = _rel(q3[cen, f], r[:, f])
+                e_i = _rel(q3[cen, f] - Y0[cen, f], r[:, f] - Y0[cen, f])
+                where = tuple(int(v) for v in cc)
+                print("precision %d block at hex %s field %d: state %.2e, one-step increment %.2e" % (prec, where, f, e_s, e_i))
+                assert e_s <= tol_s, (prec, where, f, e_s)
+                assert e_i <= tol_i, (prec, where, f, e_i)
