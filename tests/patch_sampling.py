@@ -12,8 +12,9 @@ block gets there cannot reach them within one step.  A CPU test checks this by
 swapping the cut condition and the block size.
 """
 import numpy as np
+from scipy.spatial import cKDTree
 
-from oracle.mesh import TET_FACE_VERTS, CuboidMesh
+from oracle.mesh import BC_DIRICHLET, BC_HABC, TET_FACE_VERTS, CuboidMesh
 
 MARGIN = 5     # hexes between the compared cells and the cut (one step = 5 stages)
 
@@ -34,6 +35,9 @@ class PatchMesh(CuboidMesh):
         self.bface_k, self.bface_f = k, f
         self.bface_index = np.full((self.K, 4), -1, np.int64)
         self.bface_index[k, f] = np.arange(len(bf))
+        # the later plane tests (edges and corners of the domain faces) meet
+        # the jittered cut too: a tenth of a hex (h^3 = 6 tets x 4/3 |J|)
+        self.tol = 0.1 * float(np.cbrt(8.0 * np.mean(np.abs(self.J))))
 
 
 def hex_tets(n, lo, size):
@@ -62,10 +66,66 @@ def patch_and_centre(n, centre_hex, inner=2):
     return tets, cen, pos
 
 
-def patch_mesh(VX, EToV, tets, N, bc_code, c=1.0, rho=1.0):
-    """The oracle mesh of a block (P = 0, the same code on all six sides);
-    c and rho are scalars or per-tet arrays of the whole mesh."""
+def patch_mesh(VX, EToV, tets, N, bc_code, c=1.0, rho=1.0, P=0):
+    """The oracle mesh of a block; bc_code is one code for all six sides or
+    six codes (-x, +x, -y, +y, -z, +z); c and rho are scalars or per-tet
+    arrays of the whole mesh."""
     E = EToV[tets]
     v = VX[E].reshape(-1, 3)
     pick = lambda a: np.asarray(a, float)[tets] if np.ndim(a) else float(a)
-    return PatchMesh(VX, E, N, 0, [bc_code] * 6, pick(rho), pick(c), lo=v.min(0), hi=v.max(0))
+    bc = list(bc_code) if np.ndim(bc_code) else [bc_code] * 6
+    return PatchMesh(VX, E, N, P, bc, pick(rho), pick(c), lo=v.min(0), hi=v.max(0))
+
+
+# ------------------------------------------------------------ corner blocks
+# A block at the (+, +, +) corner of the domain keeps three real domain faces
+# (the HABC, with its face, edge and corner levels) and three cut faces (p = 0
+# there: no auxiliary fields on the cut and on its edges).  The sampled cells
+# are the inner^3 hexes at the corner, size - inner hexes from the cut; the
+# auxiliary levels couple only co-located nodes across levels and face or line
+# neighbours within a level, so the cut reaches them no faster than the cells.
+CORNER_BC = (BC_DIRICHLET, BC_HABC) * 3
+
+
+def corner_block(n, size=12, inner=2):
+    """(block tet ids, sampled tet ids, their positions in the block)."""
+    tets = hex_tets(n, np.full(3, n - size), size)
+    cen = hex_tets(n, np.full(3, n - inner), inner)
+    pos = np.searchsorted(tets, cen)
+    assert np.array_equal(tets[pos], cen)
+    return tets, cen, pos
+
+
+def tri_nodes(m):
+    """[K^tri, Np2, 3] node coordinates of a mesh's triangles in the order of
+    its face-level state (the owning tet face's nodes)."""
+    return m.x[m.tri_k[:, None], m.ref3.Fmask[m.tri_f]]
+
+
+def line_nodes(m):
+    """[K^lin, Np1, 3] node coordinates of a mesh's line cells in the order
+    of its edge-level state (ascending along the edge)."""
+    X = np.empty((m.Klin, m.ref1.Np, 3))
+    for l in range(m.Klin):
+        X[l, :, m.lin_axis[l]] = m.x1[l]
+        for d in (m.lin_A[l], m.lin_B[l]):
+            X[l, :, d // 2] = m.hi[d // 2] if d % 2 else m.lo[d // 2]
+    return X
+
+
+def match_rows(sub, full, tol=1e-12):
+    """For each cell of sub ([M, n, 3] node coordinates) the index of the cell
+    of full with the same nodes in the same order."""
+    d, j = cKDTree(full.mean(axis=1)).query(sub.mean(axis=1))
+    assert np.all(d < 1e-9), d.max()
+    assert np.abs(full[j] - sub).max() < tol
+    return j
+
+
+def sampled_aux(m, tets, cen):
+    """Triangles and line cells of a block mesh that belong to the sampled
+    tets (a line cell through its face-A triangle)."""
+    on = np.isin(tets[m.tri_k], cen)
+    tri = np.nonzero(on)[0]
+    lin = np.nonzero(on[m.lin_triA])[0] if m.Klin else np.zeros(0, np.int64)
+    return tri, lin

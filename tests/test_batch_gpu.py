@@ -154,3 +154,50 @@ def test_set_launch_rejects_bad_shapes():
     with pytest.raises(dgh.DghError):
         g.set_launch(tile2=17, thr2=32)   # one thread per (triangle, set): 17 * 2 > 32
     assert g.launch == before
+
+
+def test_batch_fullsize_48_problems():
+    """The batching form's workload at full size: the 48 seeded problems the
+    benchmark times (n ~ U{8..24}, N ~ U{3,4,5}, P ~ U{2,4,6}, Ricker point
+    source, each at its own time step; 1.58 M tets), batched with the shapes
+    the autotuner picks.  Each problem also starts from a Gaussian pulse of
+    width 0.3 at its source point, so that every level carries data from the
+    first step.  After 20 steps every problem equals the same problem run
+    alone (<= 2e-6 per field), and two 8^3-hex problems, the one with the
+    highest HABC order and the one with the highest degree, equal their FP64
+    oracle runs (<= 2e-5)."""
+    import torch
+    probs = W.batch_problems(4000)
+    seq = torch.cuda.Stream()
+    solvers, meshes = [], []
+    for p in probs:
+        VX, EToV = W.kuhn_mesh(p["n"], 1.0, 0.02, seed=p["mesh_seed"])
+        s = dgh.Solver(VX, EToV, p["N"], p["P"], stream=seq)
+        s.add_point_source(p["xs"], p["f0"], p["t_s"])
+        s.init_gaussian(p["xs"], 0.3)
+        solvers.append(s)
+        meshes.append((VX, EToV))
+    b = dgh.Batch(solvers)
+    b.tune(steps=3)
+    nst = 20
+    b.step(nst)
+    b.sync()
+    n_min = min(p["n"] for p in probs)
+    smallest = [i for i, p in enumerate(probs) if p["n"] == n_min]
+    checked = {max(smallest, key=lambda i: (probs[i]["P"], -probs[i]["N"])),
+               max(smallest, key=lambda i: (probs[i]["N"], -probs[i]["P"]))}
+    assert len(checked) == 2
+    for i, (p, s) in enumerate(zip(probs, solvers)):
+        s.step(nst)
+        got = _levels(lambda lv: b.get_state(i, lv), p["P"])
+        _compare(got, _levels(s.get_state, p["P"]), 2e-6)
+        assert b.info(i)["step_count"] == nst
+        if i in checked:
+            VX, EToV = meshes[i]
+            o = Solver(CuboidMesh(VX, EToV, p["N"], p["P"], [BC_HABC] * 6, 1.0, 1.0))
+            o.add_point_source(p["xs"], p["f0"], p["t_s"])
+            Yr, _, _ = o.run(o.gaussian_state(p["xs"], 0.3), 0.0, s.info["dt"], nst)
+            _compare(got, {3: Yr["q3"], 2: Yr["q2"], 1: Yr["q1"]}, 2e-5)
+    b.close()
+    for s in solvers:
+        s.close()

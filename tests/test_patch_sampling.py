@@ -50,3 +50,48 @@ def test_sampled_cells_do_not_see_the_cut_within_one_step():
         p2 = np.searchsorted(near, cen)
         d = np.abs(_one_step(VX, EToV, near, BC_HABC, x0)[p2] - _one_step(VX, EToV, near, BC_DIRICHLET, x0)[p2])
         assert (d.max() > 1e-6 * scale) == seen, (margin, d.max())
+
+
+def _corner_step(VX, EToV, size, bc, x0):
+    from patch_sampling import corner_block, line_nodes, patch_mesh, sampled_aux, tri_nodes
+    tets, cen, pos = corner_block(N48, size=size)
+    m = patch_mesh(VX, EToV, tets, 4, bc, P=6)
+    o = Solver(m)
+    Y = o.zero_state()
+    w = lambda x: np.exp(-np.sum((x - x0) ** 2, axis=-1) / 0.15 ** 2)
+    Y["q3"][:, 0] = w(m.x)
+    Y["q3"][:, 1], Y["q3"][:, 2], Y["q3"][:, 3] = 0.3 * Y["q3"][:, 0], -0.2 * Y["q3"][:, 0], 0.25 * Y["q3"][:, 0]
+    x2, x1 = tri_nodes(m), line_nodes(m)
+    for i in range(m.P):
+        for f, a in enumerate((1.0, 0.3, -0.2)):
+            Y["q2"][:, i, f] = (1 + 0.1 * i) * a * w(x2)
+    for s in range(m.P ** 2):
+        for f, a in enumerate((1.0, 0.4)):
+            Y["q1"][:, s, f] = (1 + 0.05 * s) * a * w(x1)
+    res = {k: np.zeros_like(v) for k, v in Y.items()}
+    o.step(Y, res, 0.0, 5e-4)
+    tri, lin = sampled_aux(m, tets, cen)
+    return {"q3": Y["q3"][pos], "q2": Y["q2"][tri], "q1": Y["q1"][lin], "x2": x2[tri], "x1": x1[lin]}
+
+
+def test_corner_block_levels_do_not_see_the_cut_within_one_step():
+    """The same at a domain corner with the HABC (P = 6) on the three domain
+    faces: the sampled corner hexes' cells, face triangles and edge line cells
+    after one step do not depend on the cut (p = 0 there, or the HABC with its
+    own auxiliary fields, which renumbers every level) or on the block size.
+    The triangles and line cells are matched across the block meshes by node
+    coordinates (patch_sampling.match_rows), as the GPU check matches them to
+    the full mesh."""
+    from patch_sampling import CORNER_BC, match_rows
+    VX, EToV = W.kuhn_mesh(N48, 1.0, 0.02, seed=2000)
+    x0 = np.array([0.9, 0.9, 0.9])
+    a = _corner_step(VX, EToV, 12, CORNER_BC, x0)
+    runs = [_corner_step(VX, EToV, 12, BC_HABC, x0), _corner_step(VX, EToV, 14, CORNER_BC, x0)]
+    assert len(a["q2"]) == 3 * 4 * 2 and len(a["q1"]) == 3 * 2    # 3 faces x 2x2 hex faces x 2 tris; 3 edges x 2 lines
+    for key in ("q3", "q2", "q1"):
+        assert np.abs(a[key]).max() > 0.1, key
+    for b in runs:
+        j2, j1 = match_rows(a["x2"], b["x2"]), match_rows(a["x1"], b["x1"])
+        for key, got in (("q3", b["q3"]), ("q2", b["q2"][j2]), ("q1", b["q1"][j1])):
+            scale = np.abs(a[key]).max()
+            assert np.abs(got - a[key]).max() <= 1e-14 * scale, key
