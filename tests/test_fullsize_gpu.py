@@ -11,7 +11,9 @@ so the checks are properties that hold at any size:
   at least 10 times below the oracle's own error on a 6x coarser mesh;
 * sampled cells: one step of the full-size run, from its own state, equals
   the oracle's step of a block of hexes cut out around them (patch_sampling:
-  the cells are far enough inside the block that the cut cannot reach them).
+  the cells are far enough inside the block that the cut cannot reach them),
+  in the interior and at a domain corner, where the face, edge and corner
+  levels of the HABC are sampled too.
 """
 import math
 
@@ -154,3 +156,54 @@ def test_fullsize_one_step_matches_oracle_on_sampled_cells(mesh48):
             print("block at hex %s field %d: state %.2e, one-step increment %.2e" % (where, f, e_state, e_incr))
             assert e_state <= 1e-6, (where, f, e_state)
             assert e_incr <= 1e-4, (where, f, e_incr)
+
+
+def test_fullsize_habc_corner_one_step_matches_oracle(mesh48):
+    """The HABC chain at full size (Algorithms 1-5: face, edge and corner
+    levels, P = 6): a pulse at (0.9, 0.9, 0.9) is run 40 steps on the GPU
+    (tuned shapes, graph replay), then stepped once more on the GPU and once
+    by the FP64 oracle on the 12^3-hex block at the (+, +, +) corner, started
+    from the GPU's state on every level.  Compared: the 2^3 corner hexes'
+    48 tets, their 24 face triangles and 6 edge line cells (the corner system
+    couples the three edges' end nodes), per field: the state within 1e-6
+    relative, the one-step increment within 5e-5; measured on a B300 at most
+    1.2e-7 and 4.8e-6."""
+    import torch
+    from oracle.solver import Solver
+    from patch_sampling import (CORNER_BC, corner_block, line_nodes, match_rows, patch_mesh, sampled_aux,
+                                tri_nodes)
+    VX, EToV, _ = mesh48
+    s = torch.cuda.Stream()
+    g = dgh.Solver(VX, EToV, 4, 6, stream=s)
+    g.init_gaussian([0.9, 0.9, 0.9], 0.1)
+    g.tune(steps=2)
+    g.step(40)
+    g.sync()
+    Yk = {lv: g.get_state(lv) for lv in (3, 2, 1)}
+    t, dt = g.info["time"], g.info["dt"]
+    x2, x1 = g.nodes(2), g.nodes(1)
+    g.step(1)
+    g.sync()
+    Yk1 = {lv: g.get_state(lv) for lv in (3, 2, 1)}
+    g.close()
+    tets, cen, pos = corner_block(N48)
+    m = patch_mesh(VX, EToV, tets, 4, CORNER_BC, P=6)
+    tmap, lmap = match_rows(tri_nodes(m), x2), match_rows(line_nodes(m), x1)
+    o = Solver(m)
+    Y = o.zero_state()
+    Y["q3"][:], Y["q2"][:], Y["q1"][:] = Yk[3][tets], Yk[2][tmap], Yk[1][lmap]
+    res = {k: np.zeros_like(v) for k, v in Y.items()}
+    o.step(Y, res, t, dt)
+    tri, lin = sampled_aux(m, tets, cen)
+    assert (len(tri), len(lin)) == (24, 6)
+    cases = [(3, Y["q3"][pos], Yk1[3][cen], Yk[3][cen]),
+             (2, Y["q2"][tri], Yk1[2][tmap[tri]], Yk[2][tmap[tri]]),
+             (1, Y["q1"][lin], Yk1[1][lmap[lin]], Yk[1][lmap[lin]])]
+    for lv, ref, gpu, start in cases:
+        for f in range(ref.shape[-2]):
+            r, gg, st = ref[..., f, :], gpu[..., f, :], start[..., f, :]
+            e_state = np.linalg.norm(gg - r) / np.linalg.norm(r)
+            e_incr = np.linalg.norm((gg - st) - (r - st)) / np.linalg.norm(r - st)
+            print("corner block level %d field %d: state %.2e, one-step increment %.2e" % (lv, f, e_state, e_incr))
+            assert e_state <= 1e-6, (lv, f, e_state)
+            assert e_incr <= 5e-5, (lv, f, e_incr)
