@@ -14,6 +14,8 @@ refelem   nodal reference line / triangle / tetrahedron (Sec. 3.2)
 mesh      volume, surface and line meshes of a cuboid (Sec. 3.2, Table 1)
 habc      Pade coefficients and the face / edge / corner algebra (Sec. 2, 3.1)
 solver    DG right-hand sides, LSERK4, sources, energy (Sec. 3.2, Sec. 4.1)
+closure   the learned closure's MLP (forward, gradient, finite differences)
+          and the closed time step (ClosureSolver); not from the paper
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the
 numerical fluxes of the 2D / 1D auxiliary systems (the paper only says "the
