@@ -17,8 +17,9 @@ solver    DG right-hand sides, LSERK4, sources, energy (Sec. 3.2, Sec. 4.1)
 closure   the learned closure's MLP (forward, gradient, finite differences)
           and the closed time step (ClosureSolver); not from the paper
 
-Parity status: every function is pinned by a ``-m "not gpu"`` test except the
+Parity status: every function is pinned by a ``-m "not gpu"`` test.  The
 numerical fluxes of the 2D / 1D auxiliary systems (the paper only says "the
-same numerical scheme", Sec. 3.1 item 1): those are "parity unpinned" beyond
-the behavioural pins (free stream, energy, symmetry, reflection ordering).
+same numerical scheme", Sec. 3.1 item 1; read as the upwind flux with the 3D
+impedance rho c) are pinned by the exact energy rate of the semi-discrete
+face and edge systems, a quadratic form of the interface jumps.
 """
