@@ -327,3 +327,46 @@ def test_reflection_falls_with_habc_order():
         errs.append(math.sqrt(s.energy(d) / E0))
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     assert errs[0] > 10 * errs[3], errs
+
+
+def test_volume_energy_rate_is_the_upwind_dissipation_across_materials():
+    """Sec. 3.2 upwind flux with cell-wise materials (reading E18): the
+    semi-discrete 3D energy E = sum_k int p^2 / (2 rho c^2) + rho |u|^2 / 2
+    changes at exactly -sum over interior faces of
+    int ([p]^2 + Z- Z+ [u.n]^2) / (Z- + Z+), Z = rho c of each side (the
+    exact Riemann flux; summation by parts of the nodal operators).  Three
+    layers give faces with impedance jumps; the fields are random and
+    discontinuous and zero on cells with a boundary face.  The same sum with
+    an impedance of 1 everywhere must miss."""
+    VX, EToV = W.kuhn_mesh(4, 1.0, 0.03, seed=83)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.0, 1.5, 2.0], [1.0, 1.2, 1.5])
+    m = CuboidMesh(VX, EToV, 3, 0, [BC_HABC] * 6, rho, c)
+    o = Solver(m)
+    ref, K, Nfp = m.ref3, m.K, m.ref3.Nfp
+    inner = np.all(m.EToE >= 0, axis=1)
+    q3 = np.random.default_rng(7).normal(size=(K, 4, ref.Np)) * inner[:, None, None]
+    rhs = o._rhs3(q3, np.zeros((len(m.bfaces), Nfp)), 0.0)
+    J = np.abs(m.J)
+    Mr = np.einsum("nj,kfj->kfn", ref.M, rhs)
+    dE = np.sum(J * (np.sum(q3[:, 0] * Mr[:, 0], -1) / (m.rho * m.c ** 2)
+                     + m.rho * np.sum(q3[:, 1:] * Mr[:, 1:], axis=(-1, -2))))
+    E = ref.M @ ref.LIFT                       # face mass blocks (Np x 4 Nfp)
+    Z = m.rho * m.c
+    diss, diss1, jumps = 0.0, 0.0, 0
+    for k in range(K):
+        for f in range(4):
+            k2 = m.EToE[k, f]
+            if k2 < 0:
+                continue
+            own = ref.Fmask[f]
+            nb = ref.Fmask[m.EToF[k, f]][m.nbr_perm[k, f]]
+            Ef = E[own][:, f * Nfp:(f + 1) * Nfp] * J[k] * m.Fscale[k, f]
+            jp = q3[k, 0, own] - q3[k2, 0, nb]
+            ju = m.n[k, f] @ (q3[k, 1:][:, own] - q3[k2, 1:][:, nb])
+            pp, uu = jp @ Ef @ jp, ju @ Ef @ ju
+            diss += 0.5 * (pp + Z[k] * Z[k2] * uu) / (Z[k] + Z[k2])   # each face seen from both sides
+            diss1 += 0.5 * (pp + uu) / 2.0
+            jumps += Z[k] != Z[k2]
+    assert jumps > 0
+    assert abs(dE + diss) <= 1e-12 * diss
+    assert abs(dE + diss1) > 1e-2 * diss
