@@ -129,3 +129,26 @@ def sampled_aux(m, tets, cen):
     tri = np.nonzero(on)[0]
     lin = np.nonzero(on[m.lin_triA])[0] if m.Klin else np.zeros(0, np.int64)
     return tri, lin
+
+
+def block_step(VX, EToV, tets, N, P, bc_code, Yk, x2, x1, t, dt, c=1.0, rho=1.0, sources=()):
+    """One oracle step of a block from a full-mesh state Yk = {3: q3, 2: q2,
+    1: q1} (canonical layouts; x2, x1: the full mesh's triangle and line node
+    coordinates, to match the block's).  sources: (x_s, f_peak, t_s) Ricker
+    point sources.  Returns (block mesh, stepped state, triangle map, line
+    map, the block's oracle solver)."""
+    from oracle.solver import Solver
+    m = patch_mesh(VX, EToV, tets, N, bc_code, c=c, rho=rho, P=P)
+    o = Solver(m)
+    for xs, f, ts in sources:
+        o.add_point_source(xs, f, ts)
+    Y = o.zero_state()
+    Y["q3"][:] = Yk[3][tets]
+    tmap = match_rows(tri_nodes(m), x2) if m.Ktri else np.zeros(0, np.int64)
+    lmap = match_rows(line_nodes(m), x1) if m.Klin else np.zeros(0, np.int64)
+    if m.Ktri:
+        Y["q2"][:] = Yk[2][tmap]
+    if m.Klin:
+        Y["q1"][:] = Yk[1][lmap]
+    o.step(Y, {k: np.zeros_like(v) for k, v in Y.items()}, t, dt)
+    return m, Y, tmap, lmap, o
