@@ -157,25 +157,29 @@ def test_dof_count_matches_table3():
 #   dE/dt = - sum over interior interfaces of int [p]^2 / (2 Z) + Z [v.n]^2 / 2
 # when the interfaces use the upwind flux with impedance Z (summation by
 # parts of the nodal operators plus the flux algebra; the integrals are
-# exact).  Reading E15 takes Z = rho c of the 3D medium, so with rho c != 1
-# the identity pins the auxiliary fluxes' signs, factors, lift and
-# neighbour matching against that reading; Z = 1 must miss it.  The fields
-# are random and discontinuous, and zero on the cells that touch a domain
-# edge (resp. corner), so that only interior interfaces contribute.
+# exact); between cells of different impedance the integrand is
+# ([p]^2 + Z- Z+ [v.n]^2) / (Z- + Z+).  Reading E15 takes Z = rho c of the 3D
+# medium, and E18 gives each triangle and line cell the material of its tet:
+# with three layers of rho c far from 1 the identity pins the auxiliary
+# fluxes' signs, factors, lift and neighbour matching against those readings,
+# and Z = 1 must miss it.  The fields are random and discontinuous, and zero
+# on the cells that touch a domain edge (resp. corner), so that only interior
+# interfaces contribute.
 
 def _aux_setup(seed):
     from oracle.mesh import BC_HABC, CuboidMesh
     from oracle.solver import Solver
     from paper_1610_05023_b300 import workloads as W
-    rho, c = 1.5, 1.6                          # Z = rho c = 2.4, far from 1
-    VX, EToV = W.kuhn_mesh(4, 1.0, 0.03, seed=seed)
+    VX, EToV = W.kuhn_mesh(6, 1.0, 0.03, seed=seed)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.6, 2.0, 1.2], [1.5, 1.8, 2.5])   # Z = 2.4, 3.6, 3.0
     m = CuboidMesh(VX, EToV, 3, 2, [BC_HABC] * 6, rho, c)
-    return m, Solver(m), rho, c
+    return m, Solver(m)
 
 
 def test_face_system_energy_rate_is_the_upwind_dissipation():
-    m, o, rho, c = _aux_setup(81)
+    m, o = _aux_setup(81)
     ref, T, P = m.ref2, m.Ktri, m.P
+    rho, cc = m.rho2, m.c2
     Nfp = ref.Nfp
     interior = np.all(m.EToE2 >= 0, axis=1)
     assert 0 < interior.sum() < T
@@ -184,10 +188,11 @@ def test_face_system_energy_rate_is_the_upwind_dissipation():
     J = np.abs(m.J2)
     Mr = np.einsum("nk,tpfk->tpfn", ref.M, rhs)
     w = 1.0 + o.cP
-    dE = np.sum(J[:, None] * (w[None, :] / (rho * c * c) * np.sum(q2[:, :, 0] * Mr[:, :, 0], axis=-1)
-                              + rho * np.sum(q2[:, :, 1:3] * Mr[:, :, 1:3], axis=(-1, -2))))
+    dE = np.sum(J[:, None] * (w[None, :] / (rho * cc * cc)[:, None] * np.sum(q2[:, :, 0] * Mr[:, :, 0], axis=-1)
+                              + rho[:, None] * np.sum(q2[:, :, 1:3] * Mr[:, :, 1:3], axis=(-1, -2))))
     E = ref.M @ ref.LIFT                       # edge mass blocks (Np x 3 Nfp)
-    jj = {"p": 0.0, "v": 0.0}
+    Z = rho * cc
+    diss, diss1, jumps = 0.0, 0.0, 0
     for t in range(T):
         for e in range(3):
             t2 = m.EToE2[t, e]
@@ -196,19 +201,22 @@ def test_face_system_energy_rate_is_the_upwind_dissipation():
             own = ref.Fmask[e]
             nb = ref.Fmask[m.EToF2[t, e]][m.nbr_perm2[t, e]]
             Ee = E[own][:, e * Nfp:(e + 1) * Nfp] * J[t] * m.Fscale2[t, e]
+            jumps += Z[t] != Z[t2]
             for a in range(P):
                 jp = q2[t, a, 0, own] - q2[t2, a, 0, nb]
                 jv = m.n2[t, e] @ (q2[t, a, 1:3][:, own] - q2[t2, a, 1:3][:, nb])
-                jj["p"] += 0.5 * jp @ Ee @ jp       # each interior edge is seen from both sides
-                jj["v"] += 0.5 * jv @ Ee @ jv
-    rate = lambda Z: -(jj["p"] / (2 * Z) + Z * jj["v"] / 2)
-    assert abs(dE - rate(rho * c)) <= 1e-10 * abs(rate(rho * c))
-    assert abs(dE - rate(1.0)) > 1e-2 * abs(rate(rho * c))
+                pp, vv = jp @ Ee @ jp, jv @ Ee @ jv
+                diss += 0.5 * (pp + Z[t] * Z[t2] * vv) / (Z[t] + Z[t2])   # each edge seen from both sides
+                diss1 += 0.5 * (pp + vv) / 2.0
+    assert jumps > 0
+    assert abs(dE + diss) <= 1e-10 * diss
+    assert abs(dE + diss1) > 1e-2 * diss
 
 
 def test_edge_system_energy_rate_is_the_upwind_dissipation():
-    m, o, rho, c = _aux_setup(82)
+    m, o = _aux_setup(82)
     ref, L, S = m.ref1, m.Klin, m.P ** 2
+    rho, cc = m.rho1, m.c1
     interior = np.all(m.EToE1 >= 0, axis=1)
     assert 0 < interior.sum() < L
     q1 = np.random.default_rng(6).normal(size=(L, S, 2, ref.Np)) * interior[:, None, None, None]
@@ -216,11 +224,12 @@ def test_edge_system_energy_rate_is_the_upwind_dissipation():
     J = np.abs(m.J1)
     Mr = np.einsum("nk,lsfk->lsfn", ref.M, rhs)
     w = np.array([1.0 + o.cP[s % m.P] + o.cP[s // m.P] for s in range(S)])   # set s = a + P b
-    dE = np.sum(J[:, None] * (w[None, :] / (rho * c * c) * np.sum(q1[:, :, 0] * Mr[:, :, 0], axis=-1)
-                              + rho * np.sum(q1[:, :, 1] * Mr[:, :, 1], axis=-1)))
+    dE = np.sum(J[:, None] * (w[None, :] / (rho * cc * cc)[:, None] * np.sum(q1[:, :, 0] * Mr[:, :, 0], axis=-1)
+                              + rho[:, None] * np.sum(q1[:, :, 1] * Mr[:, :, 1], axis=-1)))
     end = [0, ref.Np - 1]
     tau = [-1.0, 1.0]                          # outward tangent at the r = -1 and r = +1 ends
-    jj = {"p": 0.0, "v": 0.0}
+    Z = rho * cc
+    diss, diss1, jumps = 0.0, 0.0, 0
     for l in range(L):
         for e in range(2):
             l2 = m.EToE1[l, e]
@@ -229,8 +238,10 @@ def test_edge_system_energy_rate_is_the_upwind_dissipation():
             n2 = end[m.EToF1[l, e]]
             jp = q1[l, :, 0, end[e]] - q1[l2, :, 0, n2]
             jv = tau[e] * (q1[l, :, 1, end[e]] - q1[l2, :, 1, n2])
-            jj["p"] += 0.5 * np.sum(jp * jp)
-            jj["v"] += 0.5 * np.sum(jv * jv)
-    rate = lambda Z: -(jj["p"] / (2 * Z) + Z * jj["v"] / 2)
-    assert abs(dE - rate(rho * c)) <= 1e-10 * abs(rate(rho * c))
-    assert abs(dE - rate(1.0)) > 1e-2 * abs(rate(rho * c))
+            pp, vv = np.sum(jp * jp), np.sum(jv * jv)
+            diss += 0.5 * (pp + Z[l] * Z[l2] * vv) / (Z[l] + Z[l2])      # each point seen from both sides
+            diss1 += 0.5 * (pp + vv) / 2.0
+            jumps += Z[l] != Z[l2]
+    assert jumps > 0
+    assert abs(dE + diss) <= 1e-10 * diss
+    assert abs(dE + diss1) > 1e-2 * diss
