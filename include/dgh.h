@@ -12,7 +12,11 @@
  *
  * Conventions shared by every call
  *  - Status: every int-returning call returns DGH_OK (0) or a negative code;
- *    dgh_last_error() gives a message.  No call aborts or throws.
+ *    dgh_last_error() gives a message.  No call aborts or throws: a C++
+ *    exception inside a call is caught at the boundary (a failed host
+ *    allocation returns DGH_ENOMEM, anything else DGH_EINVAL, with a message
+ *    starting "internal error:"), and a create call that fails for any reason
+ *    frees everything it had built.
  *  - Memory: arrays passed in are HOST arrays owned by the caller and only
  *    read during the call (copied).  Arrays passed out are HOST arrays owned
  *    by the caller, of the size stated, written during the call.  All device

@@ -7,7 +7,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -39,6 +41,32 @@ const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 
                         2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
 thread_local std::string g_create_error = "no error";
+
+// No C++ exception crosses the C ABI: every int entry point runs its body
+// through dgh_guarded.  A failed host allocation returns DGH_ENOMEM and any
+// other exception DGH_EINVAL; the message goes to the object's last-error
+// string (err_slot), or to the thread's creation error when there is none.
+template <class T>
+static std::string *err_slot(const T *obj) {
+    return obj ? &const_cast<T *>(obj)->err : nullptr;
+}
+
+template <class F>
+static int dgh_guarded(std::string *err, F &&body) noexcept {
+    std::string &slot = err ? *err : g_create_error;
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        try { slot = "internal error: host memory exhausted"; } catch (...) {}
+        return DGH_ENOMEM;
+    } catch (const std::exception &e) {
+        try { slot = std::string("internal error: ") + e.what(); } catch (...) {}
+        return DGH_EINVAL;
+    } catch (...) {
+        try { slot = "internal error: unknown C++ exception"; } catch (...) {}
+        return DGH_EINVAL;
+    }
+}
 
 struct DevBuf {
     void *p = nullptr;
@@ -881,33 +909,35 @@ static int host_setup(const dgh_desc *d, HostMesh &m, RefTet &T3, RefTri &T2, Re
 }
 
 int dgh_plan(const dgh_desc *d, dgh_info *o) {
-    if (!o) {
-        g_create_error = "out is NULL";
-        return DGH_EINVAL;
-    }
-    int rc = validate_desc(d);
-    if (rc) return rc;
-    HostMesh m;
-    RefTet T3;
-    RefTri T2;
-    RefLine T1;
-    HabcOps habc;
-    if ((rc = host_setup(d, m, T3, T2, T1, habc))) return rc;
-    std::memset(o, 0, sizeof(*o));
-    o->order = d->order;
-    o->habc_order = d->habc_order;
-    o->Np = T3.Np;
-    o->Np2 = T2.Np;
-    o->Np1 = T1.Np;
-    o->n_corners = int(m.corners.size());
-    o->n_cells = m.K;
-    o->n_tris = m.Ktri;
-    o->n_lines = m.Klin;
-    o->n_bfaces = int64_t(m.bface.size());
-    const int64_t P = d->habc_order;
-    o->ndof = 4 * int64_t(T3.Np) * m.K + 3 * P * T2.Np * m.Ktri + 2 * P * P * T1.Np * m.Klin;
-    o->dt = d->dt > 0.0 ? d->dt : dt_rule(m, d->cfl > 0.0 ? d->cfl : 1.0);
-    return DGH_OK;
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (!o) {
+            g_create_error = "out is NULL";
+            return DGH_EINVAL;
+        }
+        int rc = validate_desc(d);
+        if (rc) return rc;
+        HostMesh m;
+        RefTet T3;
+        RefTri T2;
+        RefLine T1;
+        HabcOps habc;
+        if ((rc = host_setup(d, m, T3, T2, T1, habc))) return rc;
+        std::memset(o, 0, sizeof(*o));
+        o->order = d->order;
+        o->habc_order = d->habc_order;
+        o->Np = T3.Np;
+        o->Np2 = T2.Np;
+        o->Np1 = T1.Np;
+        o->n_corners = int(m.corners.size());
+        o->n_cells = m.K;
+        o->n_tris = m.Ktri;
+        o->n_lines = m.Klin;
+        o->n_bfaces = int64_t(m.bface.size());
+        const int64_t P = d->habc_order;
+        o->ndof = 4 * int64_t(T3.Np) * m.K + 3 * P * T2.Np * m.Ktri + 2 * P * P * T1.Np * m.Klin;
+        o->dt = d->dt > 0.0 ? d->dt : dt_rule(m, d->cfl > 0.0 ? d->cfl : 1.0);
+        return DGH_OK;
+    });
 }
 
 }  // extern "C"
@@ -1238,629 +1268,676 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
 extern "C" {
 
 int dgh_create(const dgh_desc *d, void *stream, dgh_ctx **out) {
-    ApiRange nvtx_range("dgh_create");
-    if (!out) {
-        g_create_error = "out is NULL";
-        return DGH_EINVAL;
-    }
-    *out = nullptr;
-    int vrc = validate_desc(d);
-    if (vrc) return vrc;
-    dgh_ctx *ctx = new dgh_ctx();
-    ctx->stream = static_cast<cudaStream_t>(stream);
-    cudaGetDevice(&ctx->device);
-    ctx->N = d->order;
-    ctx->P = d->habc_order;
-    ctx->precision = d->precision;
-    int rc = host_setup(d, ctx->mesh, ctx->ref3, ctx->ref2, ctx->ref1, ctx->habc);
-    if (rc) {
-        dgh_destroy(ctx);
-        return rc;
-    }
-    ctx->cfl = d->cfl > 0.0 ? d->cfl : 1.0;
-    ctx->dt_fixed = d->dt > 0.0;
-    ctx->dt = d->dt > 0.0 ? d->dt : dt_rule(ctx->mesh, ctx->cfl);
-    rc = build_context(ctx, {0, ctx->mesh.K});
-    if (rc) {
-        g_create_error = ctx->err;
-        dgh_destroy(ctx);
-        return rc;
-    }
-    *out = ctx;
-    return DGH_OK;
+    return dgh_guarded(nullptr, [&]() -> int {
+        ApiRange nvtx_range("dgh_create");
+        if (!out) {
+            g_create_error = "out is NULL";
+            return DGH_EINVAL;
+        }
+        *out = nullptr;
+        int vrc = validate_desc(d);
+        if (vrc) return vrc;
+        struct Owner {   // destroys the partly built context on every failure, thrown or returned
+            dgh_ctx *c;
+            ~Owner() { if (c) dgh_destroy(c); }
+        } owner{new dgh_ctx()};
+        dgh_ctx *ctx = owner.c;
+        ctx->stream = static_cast<cudaStream_t>(stream);
+        cudaGetDevice(&ctx->device);
+        ctx->N = d->order;
+        ctx->P = d->habc_order;
+        ctx->precision = d->precision;
+        int rc = host_setup(d, ctx->mesh, ctx->ref3, ctx->ref2, ctx->ref1, ctx->habc);
+        if (rc) return rc;
+        ctx->cfl = d->cfl > 0.0 ? d->cfl : 1.0;
+        ctx->dt_fixed = d->dt > 0.0;
+        ctx->dt = d->dt > 0.0 ? d->dt : dt_rule(ctx->mesh, ctx->cfl);
+        rc = build_context(ctx, {0, ctx->mesh.K});
+        if (rc) {
+            g_create_error = ctx->err;
+            return rc;
+        }
+        *out = ctx;
+        owner.c = nullptr;
+        return DGH_OK;
+    });
 }
 
 int dgh_get_info(const dgh_ctx *ctx, dgh_info *o) {
-    if (!ctx || !o) return DGH_EINVAL;
-    o->order = ctx->N;
-    o->habc_order = ctx->P;
-    o->Np = ctx->Np;
-    o->Np2 = ctx->Np2;
-    o->Np1 = ctx->Np1;
-    o->n_corners = ctx->C;
-    o->n_cells = ctx->K;
-    o->n_tris = ctx->T;
-    o->n_lines = ctx->L;
-    o->n_bfaces = ctx->Fb;
-    o->ndof = 4 * int64_t(ctx->Np) * ctx->K + 3 * int64_t(ctx->P) * ctx->Np2 * ctx->T +
-              2 * int64_t(ctx->P) * ctx->P * ctx->Np1 * ctx->L;
-    o->step_count = ctx->step_count;
-    o->dt = ctx->dt;
-    o->time = ctx->t0 + ctx->step_count * 0.0;
-    o->device_bytes = ctx->device_bytes;
-    double t = 0.0;
-    if (cudaMemcpy(&t, ctx->d_time, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) o->time = t;
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !o) return DGH_EINVAL;
+        o->order = ctx->N;
+        o->habc_order = ctx->P;
+        o->Np = ctx->Np;
+        o->Np2 = ctx->Np2;
+        o->Np1 = ctx->Np1;
+        o->n_corners = ctx->C;
+        o->n_cells = ctx->K;
+        o->n_tris = ctx->T;
+        o->n_lines = ctx->L;
+        o->n_bfaces = ctx->Fb;
+        o->ndof = 4 * int64_t(ctx->Np) * ctx->K + 3 * int64_t(ctx->P) * ctx->Np2 * ctx->T +
+                  2 * int64_t(ctx->P) * ctx->P * ctx->Np1 * ctx->L;
+        o->step_count = ctx->step_count;
+        o->dt = ctx->dt;
+        o->time = ctx->t0 + ctx->step_count * 0.0;
+        o->device_bytes = ctx->device_bytes;
+        double t = 0.0;
+        if (cudaMemcpy(&t, ctx->d_time, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) o->time = t;
+        return DGH_OK;
+    });
 }
 
 int dgh_get_nodes(const dgh_ctx *ctx, int level, double *xyz, size_t count) {
-    if (!ctx || !xyz) return DGH_EINVAL;
-    const HostMesh &m = ctx->mesh;
-    if (level == 3) {
-        if (count != size_t(ctx->K) * ctx->Np * 3) return DGH_EINVAL;
-        for (int64_t k = 0; k < ctx->K; ++k)
-            for (int n = 0; n < ctx->Np; ++n) {
-                const double r = ctx->ref3.r[n], s = ctx->ref3.s[n], t = ctx->ref3.t[n];
-                const double l[4] = {-(1 + r + s + t) / 2, (1 + r) / 2, (1 + s) / 2, (1 + t) / 2};
-                for (int d = 0; d < 3; ++d) {
-                    double x = 0;
-                    for (int v = 0; v < 4; ++v) x += l[v] * m.VX[3 * m.EToV[4 * k + v] + d];
-                    xyz[(size_t(k) * ctx->Np + n) * 3 + d] = x;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !xyz) return DGH_EINVAL;
+        const HostMesh &m = ctx->mesh;
+        if (level == 3) {
+            if (count != size_t(ctx->K) * ctx->Np * 3) return DGH_EINVAL;
+            for (int64_t k = 0; k < ctx->K; ++k)
+                for (int n = 0; n < ctx->Np; ++n) {
+                    const double r = ctx->ref3.r[n], s = ctx->ref3.s[n], t = ctx->ref3.t[n];
+                    const double l[4] = {-(1 + r + s + t) / 2, (1 + r) / 2, (1 + s) / 2, (1 + t) / 2};
+                    for (int d = 0; d < 3; ++d) {
+                        double x = 0;
+                        for (int v = 0; v < 4; ++v) x += l[v] * m.VX[3 * m.EToV[4 * k + v] + d];
+                        xyz[(size_t(k) * ctx->Np + n) * 3 + d] = x;
+                    }
                 }
-            }
-        return DGH_OK;
-    }
-    if (level == 2) {
-        if (count != size_t(ctx->T) * ctx->Np2 * 3) return DGH_EINVAL;
-        for (int64_t t = 0; t < ctx->T; ++t)
-            for (int n = 0; n < ctx->Np2; ++n) {
-                const double r = ctx->ref2.r[n], s = ctx->ref2.s[n];
-                const double l[3] = {-(r + s) / 2, (1 + r) / 2, (1 + s) / 2};
-                for (int d = 0; d < 3; ++d) {
-                    double x = 0;
-                    for (int v = 0; v < 3; ++v) x += l[v] * m.VX[3 * m.triV[3 * t + v] + d];
-                    xyz[(size_t(t) * ctx->Np2 + n) * 3 + d] = x;
+            return DGH_OK;
+        }
+        if (level == 2) {
+            if (count != size_t(ctx->T) * ctx->Np2 * 3) return DGH_EINVAL;
+            for (int64_t t = 0; t < ctx->T; ++t)
+                for (int n = 0; n < ctx->Np2; ++n) {
+                    const double r = ctx->ref2.r[n], s = ctx->ref2.s[n];
+                    const double l[3] = {-(r + s) / 2, (1 + r) / 2, (1 + s) / 2};
+                    for (int d = 0; d < 3; ++d) {
+                        double x = 0;
+                        for (int v = 0; v < 3; ++v) x += l[v] * m.VX[3 * m.triV[3 * t + v] + d];
+                        xyz[(size_t(t) * ctx->Np2 + n) * 3 + d] = x;
+                    }
                 }
-            }
-        return DGH_OK;
-    }
-    if (level == 1) {
-        if (count != size_t(ctx->L) * ctx->Np1 * 3) return DGH_EINVAL;
-        for (int64_t l = 0; l < ctx->L; ++l)
-            for (int n = 0; n < ctx->Np1; ++n) {
-                const double r = ctx->ref1.r[n];
-                for (int d = 0; d < 3; ++d)
-                    xyz[(size_t(l) * ctx->Np1 + n) * 3 + d] =
-                        (1 - r) / 2 * m.VX[3 * m.linV[2 * l] + d] + (1 + r) / 2 * m.VX[3 * m.linV[2 * l + 1] + d];
-            }
-        return DGH_OK;
-    }
-    const_cast<dgh_ctx *>(ctx)->err = "level must be 3, 2 or 1";
-    return DGH_EINVAL;
+            return DGH_OK;
+        }
+        if (level == 1) {
+            if (count != size_t(ctx->L) * ctx->Np1 * 3) return DGH_EINVAL;
+            for (int64_t l = 0; l < ctx->L; ++l)
+                for (int n = 0; n < ctx->Np1; ++n) {
+                    const double r = ctx->ref1.r[n];
+                    for (int d = 0; d < 3; ++d)
+                        xyz[(size_t(l) * ctx->Np1 + n) * 3 + d] =
+                            (1 - r) / 2 * m.VX[3 * m.linV[2 * l] + d] + (1 + r) / 2 * m.VX[3 * m.linV[2 * l + 1] + d];
+                }
+            return DGH_OK;
+        }
+        const_cast<dgh_ctx *>(ctx)->err = "level must be 3, 2 or 1";
+        return DGH_EINVAL;
+    });
 }
 
 int dgh_set_time(dgh_ctx *ctx, double t) {
-    if (!ctx) return DGH_EINVAL;
-    CK(cudaMemcpyAsync(ctx->d_time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx) return DGH_EINVAL;
+        CK(cudaMemcpyAsync(ctx->d_time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return DGH_OK;
+    });
 }
 
 int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp) {
-    if (!ctx || !x0 || !(width > 0.0)) return DGH_EINVAL;
-    for (int lv = 1; lv <= 3; ++lv) {
-        size_t n;
-        level_count(ctx, lv, n);
-        if (lv == 3) n = size_t(ctx->K32) * 32 * 4 * ctx->Np;
-        CK(cudaMemsetAsync(level_ptr(ctx, lv, false), 0, n * sizeof(float), ctx->stream));
-        CK(cudaMemsetAsync(level_ptr(ctx, lv, true), 0, n * sizeof(float), ctx->stream));
-    }
-    if (ctx->sh) {   // shadow chain restarts at zero with the fields
-        dgh_ctx::Shadow *h = ctx->sh;
-        const size_t n2 = size_t(ctx->T) * h->P * 3 * ctx->Np2, n1 = size_t(ctx->L) * h->P * h->P * 2 * ctx->Np1;
-        CK(cudaMemsetAsync(h->q2, 0, std::max<size_t>(n2, 1) * sizeof(float), ctx->stream));
-        CK(cudaMemsetAsync(h->res2, 0, std::max<size_t>(n2, 1) * sizeof(float), ctx->stream));
-        CK(cudaMemsetAsync(h->q1, 0, std::max<size_t>(n1, 1) * sizeof(float), ctx->stream));
-        CK(cudaMemsetAsync(h->res1, 0, std::max<size_t>(n1, 1) * sizeof(float), ctx->stream));
-    }
-    const int64_t total = ctx->K32 * 32 * ctx->Np;
-    const int blocks = int((total + 255) / 256);
-    switch (ctx->N) {
-        case 1: k_init_gaussian<1><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
-        case 2: k_init_gaussian<2><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
-        case 3: k_init_gaussian<3><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
-        case 4: k_init_gaussian<4><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
-        case 5: k_init_gaussian<5><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
-        case 6: k_init_gaussian<6><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
-    }
-    CK(cudaGetLastError());
-    ctx->step_count = 0;
-    ctx->t0 = 0.0;
-    CK(cudaMemsetAsync(ctx->d_time, 0, sizeof(double), ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream));
-    ctx->dirty = true;
-    CK(cudaStreamSynchronize(ctx->stream));
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !x0 || !(width > 0.0)) return DGH_EINVAL;
+        for (int lv = 1; lv <= 3; ++lv) {
+            size_t n;
+            level_count(ctx, lv, n);
+            if (lv == 3) n = size_t(ctx->K32) * 32 * 4 * ctx->Np;
+            CK(cudaMemsetAsync(level_ptr(ctx, lv, false), 0, n * sizeof(float), ctx->stream));
+            CK(cudaMemsetAsync(level_ptr(ctx, lv, true), 0, n * sizeof(float), ctx->stream));
+        }
+        if (ctx->sh) {   // shadow chain restarts at zero with the fields
+            dgh_ctx::Shadow *h = ctx->sh;
+            const size_t n2 = size_t(ctx->T) * h->P * 3 * ctx->Np2, n1 = size_t(ctx->L) * h->P * h->P * 2 * ctx->Np1;
+            CK(cudaMemsetAsync(h->q2, 0, std::max<size_t>(n2, 1) * sizeof(float), ctx->stream));
+            CK(cudaMemsetAsync(h->res2, 0, std::max<size_t>(n2, 1) * sizeof(float), ctx->stream));
+            CK(cudaMemsetAsync(h->q1, 0, std::max<size_t>(n1, 1) * sizeof(float), ctx->stream));
+            CK(cudaMemsetAsync(h->res1, 0, std::max<size_t>(n1, 1) * sizeof(float), ctx->stream));
+        }
+        const int64_t total = ctx->K32 * 32 * ctx->Np;
+        const int blocks = int((total + 255) / 256);
+        switch (ctx->N) {
+            case 1: k_init_gaussian<1><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+            case 2: k_init_gaussian<2><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+            case 3: k_init_gaussian<3><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+            case 4: k_init_gaussian<4><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+            case 5: k_init_gaussian<5><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+            case 6: k_init_gaussian<6><<<blocks, 256, 0, ctx->stream>>>(ctx->q3, ctx->cellv, ctx->rst, ctx->K32 * 32, x0[0], x0[1], x0[2], width, amp); break;
+        }
+        CK(cudaGetLastError());
+        ctx->step_count = 0;
+        ctx->t0 = 0.0;
+        CK(cudaMemsetAsync(ctx->d_time, 0, sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream));
+        ctx->dirty = true;
+        CK(cudaStreamSynchronize(ctx->stream));
+        return DGH_OK;
+    });
 }
 
 int dgh_init_fields(dgh_ctx *ctx, const double *q3d, size_t count) {
-    if (!ctx || !q3d) return DGH_EINVAL;
-    size_t n;
-    level_count(ctx, 3, n);
-    if (count != n) {
-        ctx->err = "state size mismatch";
-        return DGH_EINVAL;
-    }
-    const double x0[3] = {0.0, 0.0, 0.0};
-    int rc = dgh_init_gaussian(ctx, x0, 1.0, 0.0);   // every level and the clock to zero
-    if (rc) return rc;
-    return dgh_set_state(ctx, 3, q3d, count);
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !q3d) return DGH_EINVAL;
+        size_t n;
+        level_count(ctx, 3, n);
+        if (count != n) {
+            ctx->err = "state size mismatch";
+            return DGH_EINVAL;
+        }
+        const double x0[3] = {0.0, 0.0, 0.0};
+        int rc = dgh_init_gaussian(ctx, x0, 1.0, 0.0);   // every level and the clock to zero
+        if (rc) return rc;
+        return dgh_set_state(ctx, 3, q3d, count);
+    });
 }
 
 int dgh_set_material(dgh_ctx *ctx, const double *c, const double *rho, size_t count) {
-    if (!ctx || !c || !rho) return DGH_EINVAL;
-    if (count != size_t(ctx->mesh.K)) {
-        ctx->err = "material: one (c, rho) per cell";
-        return DGH_EINVAL;
-    }
-    if (ctx->no_overlap || ctx->part_blk0.size() > 2) {
-        ctx->err = "material: not for a batch group";
-        return DGH_ESTATE;
-    }
-    for (size_t k = 0; k < count; ++k)
-        if (!(c[k] > 0.0) || !(rho[k] > 0.0) || !std::isfinite(c[k]) || !std::isfinite(rho[k])) {
-            ctx->err = "material: c and rho must be positive and finite";
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !c || !rho) return DGH_EINVAL;
+        if (count != size_t(ctx->mesh.K)) {
+            ctx->err = "material: one (c, rho) per cell";
             return DGH_EINVAL;
         }
-    // the state (all levels, time, step count) moves through a checkpoint blob
-    size_t sz = 0;
-    int rc = dgh_save_state(ctx, nullptr, &sz);
-    if (rc) return rc;
-    std::vector<char> blob(sz);
-    if ((rc = dgh_save_state(ctx, blob.data(), &sz))) return rc;
-    dgh_ctx *n = new dgh_ctx();
-    n->stream = ctx->stream;
-    n->device = ctx->device;
-    n->N = ctx->N;
-    n->P = ctx->P;
-    n->precision = ctx->precision;
-    n->mesh = ctx->mesh;
-    n->mesh.c.assign(c, c + count);
-    n->mesh.rho.assign(rho, rho + count);
-    n->ref3 = ctx->ref3;
-    n->ref2 = ctx->ref2;
-    n->ref1 = ctx->ref1;
-    n->habc = ctx->habc;
-    n->cfl = ctx->cfl;
-    n->dt_fixed = ctx->dt_fixed;
-    n->dt = ctx->dt_fixed ? ctx->dt : dt_rule(n->mesh, ctx->cfl);
-    n->t0 = ctx->t0;
-    auto give_up = [&](int code) {
-        ctx->err = n->err;
+        if (ctx->no_overlap || ctx->part_blk0.size() > 2) {
+            ctx->err = "material: not for a batch group";
+            return DGH_ESTATE;
+        }
+        for (size_t k = 0; k < count; ++k)
+            if (!(c[k] > 0.0) || !(rho[k] > 0.0) || !std::isfinite(c[k]) || !std::isfinite(rho[k])) {
+                ctx->err = "material: c and rho must be positive and finite";
+                return DGH_EINVAL;
+            }
+        // the state (all levels, time, step count) moves through a checkpoint blob
+        size_t sz = 0;
+        int rc = dgh_save_state(ctx, nullptr, &sz);
+        if (rc) return rc;
+        std::vector<char> blob(sz);
+        if ((rc = dgh_save_state(ctx, blob.data(), &sz))) return rc;
+        dgh_ctx *n = new dgh_ctx();
+        n->stream = ctx->stream;
+        n->device = ctx->device;
+        n->N = ctx->N;
+        n->P = ctx->P;
+        n->precision = ctx->precision;
+        n->mesh = ctx->mesh;
+        n->mesh.c.assign(c, c + count);
+        n->mesh.rho.assign(rho, rho + count);
+        n->ref3 = ctx->ref3;
+        n->ref2 = ctx->ref2;
+        n->ref1 = ctx->ref1;
+        n->habc = ctx->habc;
+        n->cfl = ctx->cfl;
+        n->dt_fixed = ctx->dt_fixed;
+        n->dt = ctx->dt_fixed ? ctx->dt : dt_rule(n->mesh, ctx->cfl);
+        n->t0 = ctx->t0;
+        auto give_up = [&](int code) {
+            ctx->err = n->err;
+            dgh_destroy(n);
+            return code;
+        };
+        if ((rc = build_context(n, {0, n->mesh.K}))) return give_up(rc);
+        // sources, launch shapes and the watchdog carry over; the closure and a
+        // recording shadow chain do not (set them again)
+        n->src = ctx->src;
+        if (ctx->src.n > 0 && cudaMemcpy(n->srcvec, ctx->srcvec, sizeof(float) * MAXSRC * ctx->Np,
+                                         cudaMemcpyDeviceToDevice) != cudaSuccess)
+            return give_up(DGH_ECUDA);
+        n->tile2 = ctx->tile2;
+        n->tile1 = ctx->tile1;
+        n->cta3_per_sm = ctx->cta3_per_sm;
+        n->thr2 = ctx->thr2;
+        n->thr1 = ctx->thr1;
+        if (dispatchN<Shapes>(n->N, n) != DGH_OK) return give_up(DGH_EINVAL);
+        n->wd_every = ctx->wd_every;
+        n->wd_limit = ctx->wd_limit;
+        if ((rc = dgh_load_state(n, blob.data(), sz))) return give_up(rc);
+        std::swap(*ctx, *n);   // the handle keeps its address; n now holds the old context
         dgh_destroy(n);
-        return code;
-    };
-    if ((rc = build_context(n, {0, n->mesh.K}))) return give_up(rc);
-    // sources, launch shapes and the watchdog carry over; the closure and a
-    // recording shadow chain do not (set them again)
-    n->src = ctx->src;
-    if (ctx->src.n > 0 && cudaMemcpy(n->srcvec, ctx->srcvec, sizeof(float) * MAXSRC * ctx->Np,
-                                     cudaMemcpyDeviceToDevice) != cudaSuccess)
-        return give_up(DGH_ECUDA);
-    n->tile2 = ctx->tile2;
-    n->tile1 = ctx->tile1;
-    n->cta3_per_sm = ctx->cta3_per_sm;
-    n->thr2 = ctx->thr2;
-    n->thr1 = ctx->thr1;
-    if (dispatchN<Shapes>(n->N, n) != DGH_OK) return give_up(DGH_EINVAL);
-    n->wd_every = ctx->wd_every;
-    n->wd_limit = ctx->wd_limit;
-    if ((rc = dgh_load_state(n, blob.data(), sz))) return give_up(rc);
-    std::swap(*ctx, *n);   // the handle keeps its address; n now holds the old context
-    dgh_destroy(n);
-    return DGH_OK;
+        return DGH_OK;
+    });
 }
 
 int dgh_set_material_layers(dgh_ctx *ctx, int nlayers, const double *z_top, const double *c, const double *rho) {
-    if (!ctx || nlayers < 1 || !c || !rho || (nlayers > 1 && !z_top)) return DGH_EINVAL;
-    for (int l = 0; l + 2 < nlayers; ++l)
-        if (!(z_top[l] < z_top[l + 1])) {
-            ctx->err = "material layers: z_top must increase";
-            return DGH_EINVAL;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || nlayers < 1 || !c || !rho || (nlayers > 1 && !z_top)) return DGH_EINVAL;
+        for (int l = 0; l + 2 < nlayers; ++l)
+            if (!(z_top[l] < z_top[l + 1])) {
+                ctx->err = "material layers: z_top must increase";
+                return DGH_EINVAL;
+            }
+        const HostMesh &m = ctx->mesh;
+        std::vector<double> cc(size_t(m.K)), rr(size_t(m.K));
+        for (int64_t k = 0; k < m.K; ++k) {
+            double z = 0.0;
+            for (int v = 0; v < 4; ++v) z += m.VX[size_t(m.EToV[size_t(k) * 4 + v]) * 3 + 2];
+            z *= 0.25;
+            int l = 0;
+            while (l < nlayers - 1 && z_top[l] <= z) ++l;   // layer l holds z < z_top[l]
+            cc[size_t(k)] = c[l];
+            rr[size_t(k)] = rho[l];
         }
-    const HostMesh &m = ctx->mesh;
-    std::vector<double> cc(size_t(m.K)), rr(size_t(m.K));
-    for (int64_t k = 0; k < m.K; ++k) {
-        double z = 0.0;
-        for (int v = 0; v < 4; ++v) z += m.VX[size_t(m.EToV[size_t(k) * 4 + v]) * 3 + 2];
-        z *= 0.25;
-        int l = 0;
-        while (l < nlayers - 1 && z_top[l] <= z) ++l;   // layer l holds z < z_top[l]
-        cc[size_t(k)] = c[l];
-        rr[size_t(k)] = rho[l];
-    }
-    return dgh_set_material(ctx, cc.data(), rr.data(), cc.size());
+        return dgh_set_material(ctx, cc.data(), rr.data(), cc.size());
+    });
 }
 
 int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count) {
-    ApiRange nvtx_range("dgh_set_state");
-    if (!ctx || (!in && count)) return DGH_EINVAL;
-    size_t n;
-    if (level_count(ctx, level, n) || n != count) {
-        if (ctx) ctx->err = "state size mismatch";
-        return DGH_EINVAL;
-    }
-    if (n == 0) return DGH_OK;
-    int rc = copy_in_level(ctx, level, in, level_ptr(ctx, level, false), n);
-    if (rc) return rc;
-    ctx->dirty = true;
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        ApiRange nvtx_range("dgh_set_state");
+        if (!ctx || (!in && count)) return DGH_EINVAL;
+        size_t n;
+        if (level_count(ctx, level, n) || n != count) {
+            if (ctx) ctx->err = "state size mismatch";
+            return DGH_EINVAL;
+        }
+        if (n == 0) return DGH_OK;
+        int rc = copy_in_level(ctx, level, in, level_ptr(ctx, level, false), n);
+        if (rc) return rc;
+        ctx->dirty = true;
+        return DGH_OK;
+    });
 }
 
 int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count) {
-    ApiRange nvtx_range("dgh_get_state");
-    if (!ctx || (!out && count)) return DGH_EINVAL;
-    size_t n;
-    if (level_count(ctx, level, n) || n != count) {
-        ctx->err = "state size mismatch";
-        return DGH_EINVAL;
-    }
-    return copy_out_level(ctx, level, level_ptr(ctx, level, false), out, n);
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        ApiRange nvtx_range("dgh_get_state");
+        if (!ctx || (!out && count)) return DGH_EINVAL;
+        size_t n;
+        if (level_count(ctx, level, n) || n != count) {
+            ctx->err = "state size mismatch";
+            return DGH_EINVAL;
+        }
+        return copy_out_level(ctx, level, level_ptr(ctx, level, false), out, n);
+    });
 }
 
 int dgh_get_fields(dgh_ctx *ctx, int level, double *out, size_t count) {
-    if (!ctx || (!out && count)) return DGH_EINVAL;
-    size_t n;
-    if (level_count(ctx, level, n) || n != count) {
-        ctx->err = "field size mismatch";
-        return DGH_EINVAL;
-    }
-    if (level == 3) return copy_out_level(ctx, 3, ctx->q3, out, n);
-    if (n == 0) return DGH_OK;
-    if (ctx->dirty) {
-        int rc = run_closure(ctx);
-        if (rc) return rc;
-    }
-    float *tmp = nullptr;
-    CK(cudaMallocAsync((void **)&tmp, n * sizeof(float), ctx->stream));
-    const int blocks = int((n + 255) / 256);
-    if (level == 2)
-        k_full2<<<blocks, 256, 0, ctx->stream>>>(ctx->q2, ctx->q0_3, tmp, ctx->T, ctx->P, ctx->Np2);
-    else
-        k_full1<<<blocks, 256, 0, ctx->stream>>>(ctx->q1, ctx->q0_2, ctx->cP, tmp, ctx->L, ctx->P, ctx->Np1);
-    int rc = copy_out_level(ctx, level, tmp, out, n);
-    cudaFreeAsync(tmp, ctx->stream);
-    return rc;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || (!out && count)) return DGH_EINVAL;
+        size_t n;
+        if (level_count(ctx, level, n) || n != count) {
+            ctx->err = "field size mismatch";
+            return DGH_EINVAL;
+        }
+        if (level == 3) return copy_out_level(ctx, 3, ctx->q3, out, n);
+        if (n == 0) return DGH_OK;
+        if (ctx->dirty) {
+            int rc = run_closure(ctx);
+            if (rc) return rc;
+        }
+        float *tmp = nullptr;
+        CK(cudaMallocAsync((void **)&tmp, n * sizeof(float), ctx->stream));
+        const int blocks = int((n + 255) / 256);
+        if (level == 2)
+            k_full2<<<blocks, 256, 0, ctx->stream>>>(ctx->q2, ctx->q0_3, tmp, ctx->T, ctx->P, ctx->Np2);
+        else
+            k_full1<<<blocks, 256, 0, ctx->stream>>>(ctx->q1, ctx->q0_2, ctx->cP, tmp, ctx->L, ctx->P, ctx->Np1);
+        int rc = copy_out_level(ctx, level, tmp, out, n);
+        cudaFreeAsync(tmp, ctx->stream);
+        return rc;
+    });
 }
 
 int dgh_add_point_source(dgh_ctx *ctx, const double xs[3], double f_peak, double t_s, double amp) {
-    if (!ctx || !xs) return DGH_EINVAL;
-    if (ctx->src.n >= MAXSRC) {
-        ctx->err = "too many sources";
-        return DGH_EINVAL;
-    }
-    const HostMesh &m = ctx->mesh;
-    for (int64_t k = 0; k < m.K; ++k) {
-        const double *v0 = &m.VX[3 * m.EToV[4 * k]];
-        double c0[3];
-        for (int d = 0; d < 3; ++d)
-            c0[d] = 0.5 * (m.VX[3 * m.EToV[4 * k + 1] + d] + m.VX[3 * m.EToV[4 * k + 2] + d] + m.VX[3 * m.EToV[4 * k + 3] + d] - v0[d]);
-        double rst[3] = {0, 0, 0};
-        for (int j = 0; j < 3; ++j)
-            for (int i = 0; i < 3; ++i) rst[j] += m.drdx[9 * k + 3 * j + i] * (xs[i] - c0[i]);
-        if (rst[0] >= -1 - 1e-12 && rst[1] >= -1 - 1e-12 && rst[2] >= -1 - 1e-12 && rst[0] + rst[1] + rst[2] <= -1 + 1e-12) {
-            std::vector<double> row = tet_interp_row(ctx->ref3, rst[0], rst[1], rst[2]);
-            // M_k^{-1} l(xs) = V V^T l(xs) / |J_k|
-            const Mat &V = ctx->ref3.V;
-            const int Np = ctx->Np;
-            std::vector<double> tmp(Np, 0.0);
-            std::vector<float> vec(Np);
-            for (int j = 0; j < Np; ++j)
-                for (int n = 0; n < Np; ++n) tmp[j] += V(n, j) * row[n];
-            for (int n = 0; n < Np; ++n) {
-                double s = 0;
-                for (int j = 0; j < Np; ++j) s += V(n, j) * tmp[j];
-                vec[n] = float(s / std::fabs(m.J[k]));
-            }
-            const int s = ctx->src.n;
-            CK(cudaMemcpy(ctx->srcvec + size_t(s) * Np, vec.data(), Np * sizeof(float), cudaMemcpyHostToDevice));
-            ctx->src.cell[s] = ctx->can2dev[k];
-            ctx->src.f_peak[s] = f_peak;
-            ctx->src.t_s[s] = t_s;
-            ctx->src.amp[s] = amp;
-            ctx->src.n = s + 1;
-            ctx->src_k.push_back(k);
-            ctx->src_vec_h.insert(ctx->src_vec_h.end(), vec.begin(), vec.end());
-            drop_graphs(ctx);
-            return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !xs) return DGH_EINVAL;
+        if (ctx->src.n >= MAXSRC) {
+            ctx->err = "too many sources";
+            return DGH_EINVAL;
         }
-    }
-    ctx->err = "source point outside the mesh";
-    return DGH_EINVAL;
+        const HostMesh &m = ctx->mesh;
+        for (int64_t k = 0; k < m.K; ++k) {
+            const double *v0 = &m.VX[3 * m.EToV[4 * k]];
+            double c0[3];
+            for (int d = 0; d < 3; ++d)
+                c0[d] = 0.5 * (m.VX[3 * m.EToV[4 * k + 1] + d] + m.VX[3 * m.EToV[4 * k + 2] + d] + m.VX[3 * m.EToV[4 * k + 3] + d] - v0[d]);
+            double rst[3] = {0, 0, 0};
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i) rst[j] += m.drdx[9 * k + 3 * j + i] * (xs[i] - c0[i]);
+            if (rst[0] >= -1 - 1e-12 && rst[1] >= -1 - 1e-12 && rst[2] >= -1 - 1e-12 && rst[0] + rst[1] + rst[2] <= -1 + 1e-12) {
+                std::vector<double> row = tet_interp_row(ctx->ref3, rst[0], rst[1], rst[2]);
+                // M_k^{-1} l(xs) = V V^T l(xs) / |J_k|
+                const Mat &V = ctx->ref3.V;
+                const int Np = ctx->Np;
+                std::vector<double> tmp(Np, 0.0);
+                std::vector<float> vec(Np);
+                for (int j = 0; j < Np; ++j)
+                    for (int n = 0; n < Np; ++n) tmp[j] += V(n, j) * row[n];
+                for (int n = 0; n < Np; ++n) {
+                    double s = 0;
+                    for (int j = 0; j < Np; ++j) s += V(n, j) * tmp[j];
+                    vec[n] = float(s / std::fabs(m.J[k]));
+                }
+                const int s = ctx->src.n;
+                CK(cudaMemcpy(ctx->srcvec + size_t(s) * Np, vec.data(), Np * sizeof(float), cudaMemcpyHostToDevice));
+                ctx->src.cell[s] = ctx->can2dev[k];
+                ctx->src.f_peak[s] = f_peak;
+                ctx->src.t_s[s] = t_s;
+                ctx->src.amp[s] = amp;
+                ctx->src.n = s + 1;
+                ctx->src_k.push_back(k);
+                ctx->src_vec_h.insert(ctx->src_vec_h.end(), vec.begin(), vec.end());
+                drop_graphs(ctx);
+                return DGH_OK;
+            }
+        }
+        ctx->err = "source point outside the mesh";
+        return DGH_EINVAL;
+    });
 }
 
 int dgh_step(dgh_ctx *ctx, int64_t nsteps) {
-    ApiRange nvtx_range("dgh_step");
-    if (!ctx || nsteps < 0) return DGH_EINVAL;
-    if (ctx->dirty) {
-        int rc = run_closure(ctx);
-        if (rc) return rc;
-    }
-    const bool use_graph = ctx->stream != nullptr;
-    for (int64_t i = 0; i < nsteps; ++i) {
-        if (use_graph) {
-            if (!ctx->graph[ctx->cur]) {
-                int rc = build_graph(ctx, ctx->cur);
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        ApiRange nvtx_range("dgh_step");
+        if (!ctx || nsteps < 0) return DGH_EINVAL;
+        if (ctx->dirty) {
+            int rc = run_closure(ctx);
+            if (rc) return rc;
+        }
+        const bool use_graph = ctx->stream != nullptr;
+        for (int64_t i = 0; i < nsteps; ++i) {
+            if (use_graph) {
+                if (!ctx->graph[ctx->cur]) {
+                    int rc = build_graph(ctx, ctx->cur);
+                    if (rc) return rc;
+                }
+                CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+            } else {
+                int rc = enqueue_step(ctx, ctx->cur, false);
                 if (rc) return rc;
             }
-            CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
-        } else {
-            int rc = enqueue_step(ctx, ctx->cur, false);
-            if (rc) return rc;
-        }
-        ctx->cur ^= 1;   // 5 stages: odd number of trace swaps
-        ctx->step_count++;
-        if (ctx->wd_every > 0 && ctx->step_count % ctx->wd_every == 0) {
-            double E = 0.0;
-            int rc = dgh_get_energy(ctx, &E);
-            if (rc) return rc;
-            if (!std::isfinite(E) || (ctx->wd_limit > 0.0 && E > ctx->wd_limit)) {
-                char msg[160];
-                std::snprintf(msg, sizeof msg, "watchdog: energy %.6e at step %lld (limit %.6e)", E,
-                              (long long)ctx->step_count, ctx->wd_limit);
-                ctx->err = msg;
-                return DGH_EUNSTABLE;
+            ctx->cur ^= 1;   // 5 stages: odd number of trace swaps
+            ctx->step_count++;
+            if (ctx->wd_every > 0 && ctx->step_count % ctx->wd_every == 0) {
+                double E = 0.0;
+                int rc = dgh_get_energy(ctx, &E);
+                if (rc) return rc;
+                if (!std::isfinite(E) || (ctx->wd_limit > 0.0 && E > ctx->wd_limit)) {
+                    char msg[160];
+                    std::snprintf(msg, sizeof msg, "watchdog: energy %.6e at step %lld (limit %.6e)", E,
+                                  (long long)ctx->step_count, ctx->wd_limit);
+                    ctx->err = msg;
+                    return DGH_EUNSTABLE;
+                }
             }
         }
-    }
-    CK(cudaGetLastError());
-    return DGH_OK;
+        CK(cudaGetLastError());
+        return DGH_OK;
+    });
 }
 
 int dgh_set_watchdog(dgh_ctx *ctx, int64_t every, double energy_limit) {
-    if (!ctx) return DGH_EINVAL;
-    if (every < 0 || !std::isfinite(energy_limit)) {
-        ctx->err = "watchdog: every >= 0 and a finite energy limit";
-        return DGH_EINVAL;
-    }
-    ctx->wd_every = every;
-    ctx->wd_limit = energy_limit;
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx) return DGH_EINVAL;
+        if (every < 0 || !std::isfinite(energy_limit)) {
+            ctx->err = "watchdog: every >= 0 and a finite energy limit";
+            return DGH_EINVAL;
+        }
+        ctx->wd_every = every;
+        ctx->wd_limit = energy_limit;
+        return DGH_OK;
+    });
 }
 
 int dgh_time_kernels(dgh_ctx *ctx, int64_t nsteps, double out_ms[5]) {
-    if (!ctx || !out_ms || nsteps < 1) return DGH_EINVAL;
-    if (ctx->dirty) {
-        int rc = run_closure(ctx);
-        if (rc) return rc;
-    }
-    const int per_step = 5 * 4;
-    std::vector<cudaEvent_t> ev(size_t(2 * per_step) * nsteps + 2);
-    for (auto &e : ev) CK(cudaEventCreate(&e));
-    double acc[4] = {0, 0, 0, 0};
-    int cnt[4] = {0, 0, 0, 0};
-    size_t ie = 0;
-    CK(cudaEventRecord(ev[ie++], ctx->stream));
-    int cur = ctx->cur;
-    std::vector<std::pair<int, size_t>> marks;
-    for (int64_t i = 0; i < nsteps; ++i) {
-        for (int s = 0; s < 5; ++s) {
-            for (int lv = 0; lv < 4; ++lv) {
-                const bool present = lv == 0 || (lv == 1 && ctx->T) || (lv == 2 && ctx->L) || (lv == 3 && ctx->C);
-                if (!present) continue;
-                CK(cudaEventRecord(ev[ie], ctx->stream));
-                int rc = DGH_OK;
-                if (lv == 0) rc = dispatchN<Launch3>(ctx->N, ctx, cur, s, true);
-                if (lv == 1) rc = dispatchN<Launch2>(ctx->N, ctx, cur, s, true);
-                if (lv == 2) rc = dispatchN<Launch1>(ctx->N, ctx, cur, s, true);
-                if (lv == 3) launch0(ctx, cur ^ 1);
-                if (rc) return rc;
-                CK(cudaEventRecord(ev[ie + 1], ctx->stream));
-                marks.push_back({lv, ie});
-                ie += 2;
-            }
-            cur ^= 1;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !out_ms || nsteps < 1) return DGH_EINVAL;
+        if (ctx->dirty) {
+            int rc = run_closure(ctx);
+            if (rc) return rc;
         }
-        k_advance_time<<<1, 1, 0, ctx->stream>>>(ctx->d_time, ctx->d_step, ctx->dt);
-        ctx->cur ^= 1;
-        ctx->step_count++;
-    }
-    CK(cudaEventRecord(ev[ie], ctx->stream));
-    CK(cudaEventSynchronize(ev[ie]));
-    for (auto &mk : marks) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ev[mk.second], ev[mk.second + 1]));
-        acc[mk.first] += ms;
-        cnt[mk.first]++;
-    }
-    float total = 0.f;
-    CK(cudaEventElapsedTime(&total, ev[0], ev[ie]));
-    for (int lv = 0; lv < 4; ++lv) out_ms[lv] = cnt[lv] ? acc[lv] / cnt[lv] : 0.0;
-    out_ms[4] = total / double(nsteps);
-    for (auto &e : ev) cudaEventDestroy(e);
-    return DGH_OK;
+        const int per_step = 5 * 4;
+        std::vector<cudaEvent_t> ev(size_t(2 * per_step) * nsteps + 2);
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        double acc[4] = {0, 0, 0, 0};
+        int cnt[4] = {0, 0, 0, 0};
+        size_t ie = 0;
+        CK(cudaEventRecord(ev[ie++], ctx->stream));
+        int cur = ctx->cur;
+        std::vector<std::pair<int, size_t>> marks;
+        for (int64_t i = 0; i < nsteps; ++i) {
+            for (int s = 0; s < 5; ++s) {
+                for (int lv = 0; lv < 4; ++lv) {
+                    const bool present = lv == 0 || (lv == 1 && ctx->T) || (lv == 2 && ctx->L) || (lv == 3 && ctx->C);
+                    if (!present) continue;
+                    CK(cudaEventRecord(ev[ie], ctx->stream));
+                    int rc = DGH_OK;
+                    if (lv == 0) rc = dispatchN<Launch3>(ctx->N, ctx, cur, s, true);
+                    if (lv == 1) rc = dispatchN<Launch2>(ctx->N, ctx, cur, s, true);
+                    if (lv == 2) rc = dispatchN<Launch1>(ctx->N, ctx, cur, s, true);
+                    if (lv == 3) launch0(ctx, cur ^ 1);
+                    if (rc) return rc;
+                    CK(cudaEventRecord(ev[ie + 1], ctx->stream));
+                    marks.push_back({lv, ie});
+                    ie += 2;
+                }
+                cur ^= 1;
+            }
+            k_advance_time<<<1, 1, 0, ctx->stream>>>(ctx->d_time, ctx->d_step, ctx->dt);
+            ctx->cur ^= 1;
+            ctx->step_count++;
+        }
+        CK(cudaEventRecord(ev[ie], ctx->stream));
+        CK(cudaEventSynchronize(ev[ie]));
+        for (auto &mk : marks) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[mk.second], ev[mk.second + 1]));
+            acc[mk.first] += ms;
+            cnt[mk.first]++;
+        }
+        float total = 0.f;
+        CK(cudaEventElapsedTime(&total, ev[0], ev[ie]));
+        for (int lv = 0; lv < 4; ++lv) out_ms[lv] = cnt[lv] ? acc[lv] / cnt[lv] : 0.0;
+        out_ms[4] = total / double(nsteps);
+        for (auto &e : ev) cudaEventDestroy(e);
+        return DGH_OK;
+    });
 }
 
 int dgh_sync(dgh_ctx *ctx) {
-    if (!ctx) return DGH_EINVAL;
-    CK(cudaStreamSynchronize(ctx->stream));
-    int err = 0;
-    CK(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err == 2) {
-        ctx->err = "checked build: an index outside its array (the access was skipped)";
-        return DGH_EBOUNDS;
-    }
-    if (err) {
-        ctx->err = "a device-side wait timed out (stage kernel aborted)";
-        return DGH_ETIMEOUT;
-    }
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx) return DGH_EINVAL;
+        CK(cudaStreamSynchronize(ctx->stream));
+        int err = 0;
+        CK(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err == 2) {
+            ctx->err = "checked build: an index outside its array (the access was skipped)";
+            return DGH_EBOUNDS;
+        }
+        if (err) {
+            ctx->err = "a device-side wait timed out (stage kernel aborted)";
+            return DGH_ETIMEOUT;
+        }
+        return DGH_OK;
+    });
 }
 
 int dgh_is_checked_build(void) {
-#ifdef DGH_CHECKED
-    return 1;
-#else
-    return 0;
-#endif
+    return dgh_guarded(nullptr, [&]() -> int {
+    #ifdef DGH_CHECKED
+        return 1;
+    #else
+        return 0;
+    #endif
+    });
 }
 
 int dgh_get_energy(dgh_ctx *ctx, double *E) {
-    if (!ctx || !E) return DGH_EINVAL;
-    const int nb = ctx->energy_blocks;
-    switch (ctx->N) {
-        case 1: k_energy_partial<1><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-        case 2: k_energy_partial<2><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-        case 3: k_energy_partial<3><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-        case 4: k_energy_partial<4><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-        case 5: k_energy_partial<5><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-        case 6: k_energy_partial<6><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-    }
-    k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, nb, ctx->d_energy);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !E) return DGH_EINVAL;
+        const int nb = ctx->energy_blocks;
+        switch (ctx->N) {
+            case 1: k_energy_partial<1><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+            case 2: k_energy_partial<2><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+            case 3: k_energy_partial<3><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+            case 4: k_energy_partial<4><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+            case 5: k_energy_partial<5><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+            case 6: k_energy_partial<6><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
+        }
+        k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, nb, ctx->d_energy);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return DGH_OK;
+    });
 }
 
 int dgh_get_error_energy(dgh_ctx *ctx, const double *ref, size_t count, double *E) {
-    if (!ctx || !ref || !E) return DGH_EINVAL;
-    size_t n = 0;
-    level_count(ctx, 3, n);
-    if (count != n) {
-        ctx->err = "reference size mismatch";
-        return DGH_EINVAL;
-    }
-    double *dref = nullptr;
-    CK(cudaMallocAsync((void **)&dref, n * sizeof(double), ctx->stream));
-    cudaError_t e = cudaMemcpyAsync(dref, ref, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) {
-        dispatchN<EnergyDiff>(ctx->N, ctx, (const double *)dref);
-        k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, ctx->energy_blocks, ctx->d_energy);
-        e = cudaGetLastError();
-    }
-    cudaFreeAsync(dref, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) {
-        ctx->err = std::string("error energy: ") + cudaGetErrorString(e);
-        return DGH_ECUDA;
-    }
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !ref || !E) return DGH_EINVAL;
+        size_t n = 0;
+        level_count(ctx, 3, n);
+        if (count != n) {
+            ctx->err = "reference size mismatch";
+            return DGH_EINVAL;
+        }
+        double *dref = nullptr;
+        CK(cudaMallocAsync((void **)&dref, n * sizeof(double), ctx->stream));
+        cudaError_t e = cudaMemcpyAsync(dref, ref, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) {
+            dispatchN<EnergyDiff>(ctx->N, ctx, (const double *)dref);
+            k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, ctx->energy_blocks, ctx->d_energy);
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(dref, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("error energy: ") + cudaGetErrorString(e);
+            return DGH_ECUDA;
+        }
+        return DGH_OK;
+    });
 }
 
 // Checkpoint blob: header (magic, sizes, time, step) then q/res of levels 3, 2, 1.
 int dgh_save_state(dgh_ctx *ctx, void *buf, size_t *size) {
-    if (!ctx || !size) return DGH_EINVAL;
-    size_t n3, n2, n1;
-    n3 = size_t(ctx->K32) * 32 * 4 * ctx->Np;   // raw interleaved arrays
-    level_count(ctx, 2, n2);
-    level_count(ctx, 1, n1);
-    const size_t header = 8 * sizeof(int64_t);
-    const size_t need = header + 2 * (n3 + n2 + n1) * sizeof(float);
-    if (!buf) {
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !size) return DGH_EINVAL;
+        size_t n3, n2, n1;
+        n3 = size_t(ctx->K32) * 32 * 4 * ctx->Np;   // raw interleaved arrays
+        level_count(ctx, 2, n2);
+        level_count(ctx, 1, n1);
+        const size_t header = 8 * sizeof(int64_t);
+        const size_t need = header + 2 * (n3 + n2 + n1) * sizeof(float);
+        if (!buf) {
+            *size = need;
+            return DGH_OK;
+        }
+        if (*size < need) {
+            ctx->err = "checkpoint buffer too small";
+            return DGH_EINVAL;
+        }
+        double t = 0.0;
+        CK(cudaMemcpyAsync(&t, ctx->d_time, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        int64_t h[8] = {0x4447484350543031LL, int64_t(n3), int64_t(n2), int64_t(n1), ctx->step_count, 0, 0, 0};
+        std::memcpy(&h[5], &t, sizeof(double));
+        char *p = static_cast<char *>(buf);
+        std::memcpy(p, h, header);
+        p += header;
+        const size_t ns[3] = {n3, n2, n1};
+        for (int i = 0; i < 3; ++i)
+            for (int r = 0; r < 2; ++r) {
+                if (ns[i]) CK(cudaMemcpyAsync(p, level_ptr(ctx, 3 - i, r), ns[i] * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+                p += ns[i] * sizeof(float);
+            }
+        CK(cudaStreamSynchronize(ctx->stream));
         *size = need;
         return DGH_OK;
-    }
-    if (*size < need) {
-        ctx->err = "checkpoint buffer too small";
-        return DGH_EINVAL;
-    }
-    double t = 0.0;
-    CK(cudaMemcpyAsync(&t, ctx->d_time, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    int64_t h[8] = {0x4447484350543031LL, int64_t(n3), int64_t(n2), int64_t(n1), ctx->step_count, 0, 0, 0};
-    std::memcpy(&h[5], &t, sizeof(double));
-    char *p = static_cast<char *>(buf);
-    std::memcpy(p, h, header);
-    p += header;
-    const size_t ns[3] = {n3, n2, n1};
-    for (int i = 0; i < 3; ++i)
-        for (int r = 0; r < 2; ++r) {
-            if (ns[i]) CK(cudaMemcpyAsync(p, level_ptr(ctx, 3 - i, r), ns[i] * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-            p += ns[i] * sizeof(float);
-        }
-    CK(cudaStreamSynchronize(ctx->stream));
-    *size = need;
-    return DGH_OK;
+    });
 }
 
 int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size) {
-    if (!ctx || !buf) return DGH_EINVAL;
-    size_t n3, n2, n1;
-    n3 = size_t(ctx->K32) * 32 * 4 * ctx->Np;
-    level_count(ctx, 2, n2);
-    level_count(ctx, 1, n1);
-    const size_t header = 8 * sizeof(int64_t);
-    const size_t need = header + 2 * (n3 + n2 + n1) * sizeof(float);
-    int64_t h[8];
-    if (size != need) {
-        ctx->err = "checkpoint size mismatch";
-        return DGH_EINVAL;
-    }
-    std::memcpy(h, buf, header);
-    if (h[0] != 0x4447484350543031LL || h[1] != int64_t(n3) || h[2] != int64_t(n2) || h[3] != int64_t(n1)) {
-        ctx->err = "checkpoint does not match this context";
-        return DGH_EINVAL;
-    }
-    double t;
-    std::memcpy(&t, &h[5], sizeof(double));
-    const char *p = static_cast<const char *>(buf) + header;
-    const size_t ns[3] = {n3, n2, n1};
-    for (int i = 0; i < 3; ++i)
-        for (int r = 0; r < 2; ++r) {
-            if (ns[i]) CK(cudaMemcpyAsync(level_ptr(ctx, 3 - i, r), p, ns[i] * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-            p += ns[i] * sizeof(float);
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !buf) return DGH_EINVAL;
+        size_t n3, n2, n1;
+        n3 = size_t(ctx->K32) * 32 * 4 * ctx->Np;
+        level_count(ctx, 2, n2);
+        level_count(ctx, 1, n1);
+        const size_t header = 8 * sizeof(int64_t);
+        const size_t need = header + 2 * (n3 + n2 + n1) * sizeof(float);
+        int64_t h[8];
+        if (size != need) {
+            ctx->err = "checkpoint size mismatch";
+            return DGH_EINVAL;
         }
-    CK(cudaMemcpyAsync(ctx->d_time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d_step, &h[4], sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    ctx->step_count = h[4];
-    ctx->dirty = true;
-    return DGH_OK;
+        std::memcpy(h, buf, header);
+        if (h[0] != 0x4447484350543031LL || h[1] != int64_t(n3) || h[2] != int64_t(n2) || h[3] != int64_t(n1)) {
+            ctx->err = "checkpoint does not match this context";
+            return DGH_EINVAL;
+        }
+        double t;
+        std::memcpy(&t, &h[5], sizeof(double));
+        const char *p = static_cast<const char *>(buf) + header;
+        const size_t ns[3] = {n3, n2, n1};
+        for (int i = 0; i < 3; ++i)
+            for (int r = 0; r < 2; ++r) {
+                if (ns[i]) CK(cudaMemcpyAsync(level_ptr(ctx, 3 - i, r), p, ns[i] * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+                p += ns[i] * sizeof(float);
+            }
+        CK(cudaMemcpyAsync(ctx->d_time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_step, &h[4], sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->step_count = h[4];
+        ctx->dirty = true;
+        return DGH_OK;
+    });
 }
 
 
 // ---------------------------------------------------------------- launch shapes and tuning
 int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *o) {
-    if (!ctx || !o) return DGH_EINVAL;
-    o->tile2 = ctx->tile2;
-    o->tile1 = ctx->tile1;
-    o->cta3_per_sm = ctx->cta3_per_sm;
-    o->grid3 = ctx->grid3;
-    o->grid2 = ctx->grid2;
-    o->grid1 = ctx->grid1;
-    o->occ3 = ctx->occ3;
-    o->sms = ctx->sms;
-    o->thr2 = ctx->thr2;
-    o->thr1 = ctx->thr1;
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !o) return DGH_EINVAL;
+        o->tile2 = ctx->tile2;
+        o->tile1 = ctx->tile1;
+        o->cta3_per_sm = ctx->cta3_per_sm;
+        o->grid3 = ctx->grid3;
+        o->grid2 = ctx->grid2;
+        o->grid1 = ctx->grid1;
+        o->occ3 = ctx->occ3;
+        o->sms = ctx->sms;
+        o->thr2 = ctx->thr2;
+        o->thr1 = ctx->thr1;
+        return DGH_OK;
+    });
 }
 
 int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in) {
-    auto thr_ok = [](int t) { return t == 32 || t == 64 || t == 128 || t == 256; };
-    if (!ctx || !in || in->tile2 < 1 || in->tile1 < 1 || in->cta3_per_sm < 0 || !thr_ok(in->thr2) || !thr_ok(in->thr1)) {
-        if (ctx) ctx->err = "tile2, tile1 must be >= 1, cta3_per_sm >= 0, thr2 / thr1 one of 32, 64, 128, 256";
-        return DGH_EINVAL;
-    }
-    const int t2 = ctx->tile2, t1 = ctx->tile1, c3 = ctx->cta3_per_sm, h2 = ctx->thr2, h1 = ctx->thr1;
-    ctx->tile2 = in->tile2;
-    ctx->tile1 = in->tile1;
-    ctx->cta3_per_sm = in->cta3_per_sm;
-    ctx->thr2 = in->thr2;
-    ctx->thr1 = in->thr1;
-    if (dispatchN<Shapes>(ctx->N, ctx) != DGH_OK) {
-        ctx->tile2 = t2;
-        ctx->tile1 = t1;
-        ctx->cta3_per_sm = c3;
-        ctx->thr2 = h2;
-        ctx->thr1 = h1;
-        dispatchN<Shapes>(ctx->N, ctx);
-        ctx->err = "launch shape does not fit (shared memory, or tile2 * P > thr2)";
-        return DGH_EINVAL;
-    }
-    drop_graphs(ctx);
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        auto thr_ok = [](int t) { return t == 32 || t == 64 || t == 128 || t == 256; };
+        if (!ctx || !in || in->tile2 < 1 || in->tile1 < 1 || in->cta3_per_sm < 0 || !thr_ok(in->thr2) || !thr_ok(in->thr1)) {
+            if (ctx) ctx->err = "tile2, tile1 must be >= 1, cta3_per_sm >= 0, thr2 / thr1 one of 32, 64, 128, 256";
+            return DGH_EINVAL;
+        }
+        const int t2 = ctx->tile2, t1 = ctx->tile1, c3 = ctx->cta3_per_sm, h2 = ctx->thr2, h1 = ctx->thr1;
+        ctx->tile2 = in->tile2;
+        ctx->tile1 = in->tile1;
+        ctx->cta3_per_sm = in->cta3_per_sm;
+        ctx->thr2 = in->thr2;
+        ctx->thr1 = in->thr1;
+        if (dispatchN<Shapes>(ctx->N, ctx) != DGH_OK) {
+            ctx->tile2 = t2;
+            ctx->tile1 = t1;
+            ctx->cta3_per_sm = c3;
+            ctx->thr2 = h2;
+            ctx->thr1 = h1;
+            dispatchN<Shapes>(ctx->N, ctx);
+            ctx->err = "launch shape does not fit (shared memory, or tile2 * P > thr2)";
+            return DGH_EINVAL;
+        }
+        drop_graphs(ctx);
+        return DGH_OK;
+    });
 }
 
 }  // extern "C"
@@ -1970,14 +2047,16 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
 }  // namespace
 
 extern "C" int dgh_tune(dgh_ctx *ctx, int steps, double *ms_before, double *ms_after) {
-    ApiRange nvtx_range("dgh_tune");
-    if (!ctx || steps < 1) return DGH_EINVAL;
-    const int64_t sc0 = ctx->step_count;
-    int rc = tune_contexts(
-        {ctx}, ctx->stream, steps, [&](int n) { return dgh_step(ctx, n); }, [&]() { drop_graphs(ctx); }, ms_before,
-        ms_after, ctx->err);
-    ctx->step_count = sc0;
-    return rc;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        ApiRange nvtx_range("dgh_tune");
+        if (!ctx || steps < 1) return DGH_EINVAL;
+        const int64_t sc0 = ctx->step_count;
+        int rc = tune_contexts(
+            {ctx}, ctx->stream, steps, [&](int n) { return dgh_step(ctx, n); }, [&]() { drop_graphs(ctx); }, ms_before,
+            ms_after, ctx->err);
+        ctx->step_count = sc0;
+        return rc;
+    });
 }
 
 // ============================================================================
@@ -2089,482 +2168,516 @@ void dgh_batch_destroy(dgh_batch *b) {
 }
 
 int dgh_batch_plan(const dgh_desc *descs, int count, int *group_of, dgh_info *group_info, int *n_groups) {
-    if (!descs || count < 1 || !group_of || !group_info || !n_groups) {
-        g_create_error = "invalid batch plan arguments";
-        return DGH_EINVAL;
-    }
-    std::vector<std::pair<int, int>> np(static_cast<size_t>(count));
-    for (int i = 0; i < count; ++i) {
-        int rc = validate_desc(&descs[i]);
-        if (rc) return rc;
-        np[i] = {descs[i].order, descs[i].habc_order * 8 + descs[i].precision};
-    }
-    int ng = 0;
-    std::vector<int> g = group_by_order(np, ng);
-    for (int gi = 0; gi < ng; ++gi) {
-        std::vector<HostMesh> parts;
-        RefTet T3;
-        RefTri T2;
-        RefLine T1;
-        HabcOps habc;
-        for (int i = 0; i < count; ++i) {
-            if (g[i] != gi) continue;
-            parts.emplace_back();
-            int rc = host_setup(&descs[i], parts.back(), T3, T2, T1, habc);
-            if (rc) return rc;
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (!descs || count < 1 || !group_of || !group_info || !n_groups) {
+            g_create_error = "invalid batch plan arguments";
+            return DGH_EINVAL;
         }
-        HostMesh u;
-        merge_meshes(parts, u);
-        dgh_info &o = group_info[gi];
-        std::memset(&o, 0, sizeof(o));
-        o.order = u.N;
-        o.habc_order = u.P;
-        o.Np = T3.Np;
-        o.Np2 = T2.Np;
-        o.Np1 = T1.Np;
-        o.n_corners = int(u.corners.size());
-        o.n_cells = u.K;
-        o.n_tris = u.Ktri;
-        o.n_lines = u.Klin;
-        o.n_bfaces = int64_t(u.bface.size());
-        const int64_t P = u.P;
-        o.ndof = 4 * int64_t(T3.Np) * u.K + 3 * P * T2.Np * u.Ktri + 2 * P * P * T1.Np * u.Klin;
-    }
-    for (int i = 0; i < count; ++i) group_of[i] = g[i];
-    *n_groups = ng;
-    return DGH_OK;
+        std::vector<std::pair<int, int>> np(static_cast<size_t>(count));
+        for (int i = 0; i < count; ++i) {
+            int rc = validate_desc(&descs[i]);
+            if (rc) return rc;
+            np[i] = {descs[i].order, descs[i].habc_order * 8 + descs[i].precision};
+        }
+        int ng = 0;
+        std::vector<int> g = group_by_order(np, ng);
+        for (int gi = 0; gi < ng; ++gi) {
+            std::vector<HostMesh> parts;
+            RefTet T3;
+            RefTri T2;
+            RefLine T1;
+            HabcOps habc;
+            for (int i = 0; i < count; ++i) {
+                if (g[i] != gi) continue;
+                parts.emplace_back();
+                int rc = host_setup(&descs[i], parts.back(), T3, T2, T1, habc);
+                if (rc) return rc;
+            }
+            HostMesh u;
+            merge_meshes(parts, u);
+            dgh_info &o = group_info[gi];
+            std::memset(&o, 0, sizeof(o));
+            o.order = u.N;
+            o.habc_order = u.P;
+            o.Np = T3.Np;
+            o.Np2 = T2.Np;
+            o.Np1 = T1.Np;
+            o.n_corners = int(u.corners.size());
+            o.n_cells = u.K;
+            o.n_tris = u.Ktri;
+            o.n_lines = u.Klin;
+            o.n_bfaces = int64_t(u.bface.size());
+            const int64_t P = u.P;
+            o.ndof = 4 * int64_t(T3.Np) * u.K + 3 * P * T2.Np * u.Ktri + 2 * P * P * T1.Np * u.Klin;
+        }
+        for (int i = 0; i < count; ++i) group_of[i] = g[i];
+        *n_groups = ng;
+        return DGH_OK;
+    });
 }
 
 int dgh_batch_create(dgh_ctx *const *problems, int count, dgh_batch **out) {
-    if (!out || !problems || count < 1) {
-        g_create_error = "invalid batch arguments";
-        return DGH_EINVAL;
-    }
-    *out = nullptr;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::vector<std::pair<int, int>> np(static_cast<size_t>(count));
-    for (int i = 0; i < count; ++i) {
-        if (!problems[i]) {
-            g_create_error = "null problem context";
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (!out || !problems || count < 1) {
+            g_create_error = "invalid batch arguments";
             return DGH_EINVAL;
         }
-        if (problems[i]->device != dev) {
-            g_create_error = "all problems must live on the current device";
-            return DGH_EINVAL;
-        }
-        if (problems[i]->cl_on || problems[i]->sh) {
-            g_create_error = "a learned closure or sample recording is not supported in a batch";
-            return DGH_EUNSUPPORTED;
-        }
-        np[i] = {problems[i]->N, problems[i]->P * 8 + problems[i]->precision};
-    }
-    int ng = 0;
-    std::vector<int> gof = group_by_order(np, ng);
-    dgh_batch *b = new dgh_batch();
-    b->device = dev;
-    auto fail = [&](int rc, const std::string &msg) {
-        g_create_error = msg;
-        dgh_batch_destroy(b);
-        return rc;
-    };
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
-        return fail(DGH_ECUDA, "batch stream / event");
-    b->probs.resize(size_t(count));
-    for (int gi = 0; gi < ng; ++gi) {
-        std::vector<int> members;
-        for (int i = 0; i < count; ++i)
-            if (gof[i] == gi) members.push_back(i);
-        dgh_ctx *u = new dgh_ctx();
-        b->groups.push_back(u);
-        const dgh_ctx *first = problems[members[0]];
-        u->stream = b->stream;
-        u->device = dev;
-        u->N = first->N;
-        u->P = first->P;
-        u->precision = first->precision;
-        u->ref3 = first->ref3;
-        u->ref2 = first->ref2;
-        u->ref1 = first->ref1;
-        u->habc = first->habc;
-        u->dt = 1.0;   // time steps folded into the coefficients: the clock counts steps
-        std::vector<HostMesh> parts;
-        std::vector<int64_t> offs{0};
-        int64_t t0 = 0, l0 = 0;
-        for (size_t j = 0; j < members.size(); ++j) {
-            dgh_ctx *pc = problems[members[j]];
-            double tnow = 0.0;
-            if (cudaStreamSynchronize(pc->stream) != cudaSuccess ||
-                cudaMemcpy(&tnow, pc->d_time, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-                return fail(DGH_ECUDA, "reading a problem's time");
-            parts.push_back(pc->mesh);
-            parts.back().dtCell.assign(size_t(pc->mesh.K), pc->dt);
-            dgh_batch::Prob &pr = b->probs[size_t(members[j])];
-            pr.group = gi;
-            pr.part = int(j);
-            pr.N = pc->N;
-            pr.P = pc->P;
-            pr.cell0 = offs.back();
-            pr.K = pc->K;
-            pr.tri0 = t0;
-            pr.T = pc->T;
-            pr.lin0 = l0;
-            pr.L = pc->L;
-            pr.C = pc->C;
-            pr.Fb = pc->Fb;
-            pr.dt = pc->dt;
-            pr.t0 = tnow;
-            pr.step0 = pc->step_count;
-            offs.push_back(offs.back() + pc->K);
-            t0 += pc->T;
-            l0 += pc->L;
-        }
-        merge_meshes(parts, u->mesh);
-        parts.clear();
-        int rc = build_context(u, offs);
-        if (rc) return fail(rc, u->err);
-        // sources: time measured in steps of the problem's own dt
-        for (size_t j = 0; j < members.size(); ++j) {
-            const dgh_ctx *pc = problems[members[j]];
-            const dgh_batch::Prob &pr = b->probs[size_t(members[j])];
-            for (int s = 0; s < pc->src.n; ++s) {
-                const int d = u->src.n;
-                if (d >= MAXSRC) return fail(DGH_EINVAL, "more than MAXSRC point sources in one (N, P) group");
-                const std::vector<float> vec(pc->src_vec_h.begin() + size_t(s) * pc->Np,
-                                             pc->src_vec_h.begin() + size_t(s + 1) * pc->Np);
-                if (cudaMemcpy(u->srcvec + size_t(d) * u->Np, vec.data(), vec.size() * sizeof(float),
-                               cudaMemcpyHostToDevice) != cudaSuccess)
-                    return fail(DGH_ECUDA, "source upload");
-                u->src.cell[d] = u->can2dev[size_t(pr.cell0 + pc->src_k[size_t(s)])];
-                u->src.f_peak[d] = pc->src.f_peak[s] * pr.dt;
-                u->src.t_s[d] = (pc->src.t_s[s] - pr.t0) / pr.dt;
-                u->src.amp[d] = pc->src.amp[s] * pr.dt * pr.dt;
-                u->src.n = d + 1;
-                u->src_k.push_back(pr.cell0 + pc->src_k[size_t(s)]);
-                u->src_vec_h.insert(u->src_vec_h.end(), vec.begin(), vec.end());
+        *out = nullptr;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::vector<std::pair<int, int>> np(static_cast<size_t>(count));
+        for (int i = 0; i < count; ++i) {
+            if (!problems[i]) {
+                g_create_error = "null problem context";
+                return DGH_EINVAL;
             }
-        }
-        // current fields of every problem, concatenated in canonical order
-        for (int lv = 3; lv >= 1; --lv) {
-            size_t ntot = 0;
-            level_count(u, lv, ntot);
-            std::vector<double> all(ntot);
-            size_t at = 0;
-            for (int i : members) {
-                size_t n = 0;
-                level_count(problems[i], lv, n);
-                if (n && dgh_get_state(problems[i], lv, all.data() + at, n) != DGH_OK)
-                    return fail(DGH_ECUDA, std::string("reading a problem's state: ") + problems[i]->err);
-                at += n;
+            if (problems[i]->device != dev) {
+                g_create_error = "all problems must live on the current device";
+                return DGH_EINVAL;
             }
-            if (ntot && (rc = dgh_set_state(u, lv, all.data(), ntot))) return fail(rc, u->err);
+            if (problems[i]->cl_on || problems[i]->sh) {
+                g_create_error = "a learned closure or sample recording is not supported in a batch";
+                return DGH_EUNSUPPORTED;
+            }
+            np[i] = {problems[i]->N, problems[i]->P * 8 + problems[i]->precision};
         }
-        cudaStream_t gs = nullptr;
-        cudaEvent_t ge = nullptr;
-        if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) return fail(DGH_ECUDA, "group stream");
-        b->gstream.push_back(gs);
-        if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) return fail(DGH_ECUDA, "group event");
-        b->gjoin.push_back(ge);
-    }
-    *out = b;
-    return DGH_OK;
+        int ng = 0;
+        std::vector<int> gof = group_by_order(np, ng);
+        struct Owner {   // destroys the partly built batch on every failure, thrown or returned
+            dgh_batch *b;
+            ~Owner() { if (b) dgh_batch_destroy(b); }
+        } owner{new dgh_batch()};
+        dgh_batch *b = owner.b;
+        b->device = dev;
+        auto fail = [&](int rc, const std::string &msg) {
+            g_create_error = msg;
+            return rc;
+        };
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+            return fail(DGH_ECUDA, "batch stream / event");
+        b->probs.resize(size_t(count));
+        for (int gi = 0; gi < ng; ++gi) {
+            std::vector<int> members;
+            for (int i = 0; i < count; ++i)
+                if (gof[i] == gi) members.push_back(i);
+            b->groups.push_back(nullptr);
+            dgh_ctx *u = b->groups.back() = new dgh_ctx();
+            const dgh_ctx *first = problems[members[0]];
+            u->stream = b->stream;
+            u->device = dev;
+            u->N = first->N;
+            u->P = first->P;
+            u->precision = first->precision;
+            u->ref3 = first->ref3;
+            u->ref2 = first->ref2;
+            u->ref1 = first->ref1;
+            u->habc = first->habc;
+            u->dt = 1.0;   // time steps folded into the coefficients: the clock counts steps
+            std::vector<HostMesh> parts;
+            std::vector<int64_t> offs{0};
+            int64_t t0 = 0, l0 = 0;
+            for (size_t j = 0; j < members.size(); ++j) {
+                dgh_ctx *pc = problems[members[j]];
+                double tnow = 0.0;
+                if (cudaStreamSynchronize(pc->stream) != cudaSuccess ||
+                    cudaMemcpy(&tnow, pc->d_time, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return fail(DGH_ECUDA, "reading a problem's time");
+                parts.push_back(pc->mesh);
+                parts.back().dtCell.assign(size_t(pc->mesh.K), pc->dt);
+                dgh_batch::Prob &pr = b->probs[size_t(members[j])];
+                pr.group = gi;
+                pr.part = int(j);
+                pr.N = pc->N;
+                pr.P = pc->P;
+                pr.cell0 = offs.back();
+                pr.K = pc->K;
+                pr.tri0 = t0;
+                pr.T = pc->T;
+                pr.lin0 = l0;
+                pr.L = pc->L;
+                pr.C = pc->C;
+                pr.Fb = pc->Fb;
+                pr.dt = pc->dt;
+                pr.t0 = tnow;
+                pr.step0 = pc->step_count;
+                offs.push_back(offs.back() + pc->K);
+                t0 += pc->T;
+                l0 += pc->L;
+            }
+            merge_meshes(parts, u->mesh);
+            parts.clear();
+            int rc = build_context(u, offs);
+            if (rc) return fail(rc, u->err);
+            // sources: time measured in steps of the problem's own dt
+            for (size_t j = 0; j < members.size(); ++j) {
+                const dgh_ctx *pc = problems[members[j]];
+                const dgh_batch::Prob &pr = b->probs[size_t(members[j])];
+                for (int s = 0; s < pc->src.n; ++s) {
+                    const int d = u->src.n;
+                    if (d >= MAXSRC) return fail(DGH_EINVAL, "more than MAXSRC point sources in one (N, P) group");
+                    const std::vector<float> vec(pc->src_vec_h.begin() + size_t(s) * pc->Np,
+                                                 pc->src_vec_h.begin() + size_t(s + 1) * pc->Np);
+                    if (cudaMemcpy(u->srcvec + size_t(d) * u->Np, vec.data(), vec.size() * sizeof(float),
+                                   cudaMemcpyHostToDevice) != cudaSuccess)
+                        return fail(DGH_ECUDA, "source upload");
+                    u->src.cell[d] = u->can2dev[size_t(pr.cell0 + pc->src_k[size_t(s)])];
+                    u->src.f_peak[d] = pc->src.f_peak[s] * pr.dt;
+                    u->src.t_s[d] = (pc->src.t_s[s] - pr.t0) / pr.dt;
+                    u->src.amp[d] = pc->src.amp[s] * pr.dt * pr.dt;
+                    u->src.n = d + 1;
+                    u->src_k.push_back(pr.cell0 + pc->src_k[size_t(s)]);
+                    u->src_vec_h.insert(u->src_vec_h.end(), vec.begin(), vec.end());
+                }
+            }
+            // current fields of every problem, concatenated in canonical order
+            for (int lv = 3; lv >= 1; --lv) {
+                size_t ntot = 0;
+                level_count(u, lv, ntot);
+                std::vector<double> all(ntot);
+                size_t at = 0;
+                for (int i : members) {
+                    size_t n = 0;
+                    level_count(problems[i], lv, n);
+                    if (n && dgh_get_state(problems[i], lv, all.data() + at, n) != DGH_OK)
+                        return fail(DGH_ECUDA, std::string("reading a problem's state: ") + problems[i]->err);
+                    at += n;
+                }
+                if (ntot && (rc = dgh_set_state(u, lv, all.data(), ntot))) return fail(rc, u->err);
+            }
+            cudaStream_t gs = nullptr;
+            cudaEvent_t ge = nullptr;
+            if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) return fail(DGH_ECUDA, "group stream");
+            b->gstream.push_back(gs);
+            if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) return fail(DGH_ECUDA, "group event");
+            b->gjoin.push_back(ge);
+        }
+        *out = b;
+        owner.b = nullptr;
+        return DGH_OK;
+    });
 }
 
 int dgh_batch_stream(const dgh_batch *b, void **stream) {
-    if (!b || !stream) return DGH_EINVAL;
-    *stream = static_cast<void *>(b->stream);
-    return DGH_OK;
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        if (!b || !stream) return DGH_EINVAL;
+        *stream = static_cast<void *>(b->stream);
+        return DGH_OK;
+    });
 }
 
 int dgh_batch_count(const dgh_batch *b, int *n_problems, int *n_groups) {
-    if (!b) return DGH_EINVAL;
-    if (n_problems) *n_problems = int(b->probs.size());
-    if (n_groups) *n_groups = int(b->groups.size());
-    return DGH_OK;
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        if (!b) return DGH_EINVAL;
+        if (n_problems) *n_problems = int(b->probs.size());
+        if (n_groups) *n_groups = int(b->groups.size());
+        return DGH_OK;
+    });
 }
 
 int dgh_batch_step(dgh_batch *b, int64_t nsteps) {
-    ApiRange nvtx_range("dgh_batch_step");
-    if (!b || nsteps < 0) return DGH_EINVAL;
-    for (dgh_ctx *u : b->groups)
-        if (u->dirty) {
-            int rc = run_closure(u);
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        ApiRange nvtx_range("dgh_batch_step");
+        if (!b || nsteps < 0) return DGH_EINVAL;
+        for (dgh_ctx *u : b->groups)
+            if (u->dirty) {
+                int rc = run_closure(u);
+                if (rc) {
+                    b->err = u->err;
+                    return rc;
+                }
+            }
+        for (int64_t i = 0; i < nsteps; ++i) {
+            if (!b->graph[b->cur]) {
+                int rc = batch_build_graph(b);
+                if (rc) return rc;
+            }
+            cudaError_t e = cudaGraphLaunch(b->graph[b->cur], b->stream);
+            if (e != cudaSuccess) {
+                b->err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+                return DGH_ECUDA;
+            }
+            b->cur ^= 1;
+            for (dgh_ctx *u : b->groups) {
+                u->cur ^= 1;
+                u->step_count++;
+            }
+            b->step_count++;
+        }
+        return DGH_OK;
+    });
+}
+
+int dgh_batch_sync(dgh_batch *b) {
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        if (!b) return DGH_EINVAL;
+        for (dgh_ctx *u : b->groups) {
+            int rc = dgh_sync(u);
             if (rc) {
                 b->err = u->err;
                 return rc;
             }
         }
-    for (int64_t i = 0; i < nsteps; ++i) {
-        if (!b->graph[b->cur]) {
-            int rc = batch_build_graph(b);
-            if (rc) return rc;
-        }
-        cudaError_t e = cudaGraphLaunch(b->graph[b->cur], b->stream);
-        if (e != cudaSuccess) {
-            b->err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
-            return DGH_ECUDA;
-        }
-        b->cur ^= 1;
-        for (dgh_ctx *u : b->groups) {
-            u->cur ^= 1;
-            u->step_count++;
-        }
-        b->step_count++;
-    }
-    return DGH_OK;
+        return DGH_OK;
+    });
 }
 
-int dgh_batch_sync(dgh_batch *b) {
-    if (!b) return DGH_EINVAL;
-    for (dgh_ctx *u : b->groups) {
-        int rc = dgh_sync(u);
+int dgh_batch_get_info(const dgh_batch *b, int i, dgh_info *o) {
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        if (!b || !o || i < 0 || i >= int(b->probs.size())) return DGH_EINVAL;
+        const dgh_batch::Prob &p = b->probs[size_t(i)];
+        const dgh_ctx *u = b->groups[size_t(p.group)];
+        std::memset(o, 0, sizeof(*o));
+        o->order = p.N;
+        o->habc_order = p.P;
+        o->Np = u->Np;
+        o->Np2 = u->Np2;
+        o->Np1 = u->Np1;
+        o->n_corners = int(p.C);
+        o->n_cells = p.K;
+        o->n_tris = p.T;
+        o->n_lines = p.L;
+        o->n_bfaces = p.Fb;
+        o->ndof = 4 * int64_t(u->Np) * p.K + 3 * int64_t(p.P) * u->Np2 * p.T + 2 * int64_t(p.P) * p.P * u->Np1 * p.L;
+        o->step_count = p.step0 + b->step_count;
+        o->dt = p.dt;
+        o->time = p.t0 + double(b->step_count) * p.dt;
+        o->device_bytes = u->device_bytes;
+        return DGH_OK;
+    });
+}
+
+int dgh_batch_get_state(dgh_batch *b, int i, int level, double *out, size_t count) {
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        if (!b || i < 0 || i >= int(b->probs.size()) || (!out && count)) return DGH_EINVAL;
+        const dgh_batch::Prob &p = b->probs[size_t(i)];
+        dgh_ctx *u = b->groups[size_t(p.group)];
+        size_t per = 0, off = 0, n = 0;
+        if (level == 3) {
+            per = size_t(4) * u->Np;
+            off = size_t(p.cell0) * per;
+            n = size_t(p.K) * per;
+        } else if (level == 2) {
+            per = size_t(p.P) * 3 * u->Np2;
+            off = size_t(p.tri0) * per;
+            n = size_t(p.T) * per;
+        } else if (level == 1) {
+            per = size_t(p.P) * p.P * 2 * u->Np1;
+            off = size_t(p.lin0) * per;
+            n = size_t(p.L) * per;
+        } else {
+            b->err = "level must be 3, 2 or 1";
+            return DGH_EINVAL;
+        }
+        if (n != count) {
+            b->err = "state size mismatch";
+            return DGH_EINVAL;
+        }
+        if (n == 0) return DGH_OK;
+        size_t ntot = 0;
+        level_count(u, level, ntot);
+        std::vector<double> all(ntot);
+        int rc = dgh_get_state(u, level, all.data(), ntot);
         if (rc) {
             b->err = u->err;
             return rc;
         }
-    }
-    return DGH_OK;
-}
-
-int dgh_batch_get_info(const dgh_batch *b, int i, dgh_info *o) {
-    if (!b || !o || i < 0 || i >= int(b->probs.size())) return DGH_EINVAL;
-    const dgh_batch::Prob &p = b->probs[size_t(i)];
-    const dgh_ctx *u = b->groups[size_t(p.group)];
-    std::memset(o, 0, sizeof(*o));
-    o->order = p.N;
-    o->habc_order = p.P;
-    o->Np = u->Np;
-    o->Np2 = u->Np2;
-    o->Np1 = u->Np1;
-    o->n_corners = int(p.C);
-    o->n_cells = p.K;
-    o->n_tris = p.T;
-    o->n_lines = p.L;
-    o->n_bfaces = p.Fb;
-    o->ndof = 4 * int64_t(u->Np) * p.K + 3 * int64_t(p.P) * u->Np2 * p.T + 2 * int64_t(p.P) * p.P * u->Np1 * p.L;
-    o->step_count = p.step0 + b->step_count;
-    o->dt = p.dt;
-    o->time = p.t0 + double(b->step_count) * p.dt;
-    o->device_bytes = u->device_bytes;
-    return DGH_OK;
-}
-
-int dgh_batch_get_state(dgh_batch *b, int i, int level, double *out, size_t count) {
-    if (!b || i < 0 || i >= int(b->probs.size()) || (!out && count)) return DGH_EINVAL;
-    const dgh_batch::Prob &p = b->probs[size_t(i)];
-    dgh_ctx *u = b->groups[size_t(p.group)];
-    size_t per = 0, off = 0, n = 0;
-    if (level == 3) {
-        per = size_t(4) * u->Np;
-        off = size_t(p.cell0) * per;
-        n = size_t(p.K) * per;
-    } else if (level == 2) {
-        per = size_t(p.P) * 3 * u->Np2;
-        off = size_t(p.tri0) * per;
-        n = size_t(p.T) * per;
-    } else if (level == 1) {
-        per = size_t(p.P) * p.P * 2 * u->Np1;
-        off = size_t(p.lin0) * per;
-        n = size_t(p.L) * per;
-    } else {
-        b->err = "level must be 3, 2 or 1";
-        return DGH_EINVAL;
-    }
-    if (n != count) {
-        b->err = "state size mismatch";
-        return DGH_EINVAL;
-    }
-    if (n == 0) return DGH_OK;
-    size_t ntot = 0;
-    level_count(u, level, ntot);
-    std::vector<double> all(ntot);
-    int rc = dgh_get_state(u, level, all.data(), ntot);
-    if (rc) {
-        b->err = u->err;
-        return rc;
-    }
-    std::memcpy(out, all.data() + off, n * sizeof(double));
-    return DGH_OK;
+        std::memcpy(out, all.data() + off, n * sizeof(double));
+        return DGH_OK;
+    });
 }
 
 int dgh_batch_get_energy(dgh_batch *b, int i, double *E) {
-    if (!b || !E || i < 0 || i >= int(b->probs.size())) return DGH_EINVAL;
-    const dgh_batch::Prob &p = b->probs[size_t(i)];
-    dgh_ctx *u = b->groups[size_t(p.group)];
-    const int64_t blk0 = u->part_blk0[size_t(p.part)], nblk = u->part_blk0[size_t(p.part) + 1] - blk0;
-    const float *q = u->q3 + blk0 * 4 * u->Np * 32;
-    const double *ew = u->ew + blk0 * 32 * 2;
-    const int nb = u->energy_blocks;
-    cudaStream_t st = u->stream;
-    switch (u->N) {
-        case 1: k_energy_partial<1><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-        case 2: k_energy_partial<2><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-        case 3: k_energy_partial<3><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-        case 4: k_energy_partial<4><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-        case 5: k_energy_partial<5><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-        case 6: k_energy_partial<6><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-    }
-    k_sum_partials<<<1, 256, 0, st>>>(u->partial, nb, u->d_energy);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(E, u->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-        b->err = std::string("energy: ") + cudaGetErrorString(e);
-        return DGH_ECUDA;
-    }
-    return DGH_OK;
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        if (!b || !E || i < 0 || i >= int(b->probs.size())) return DGH_EINVAL;
+        const dgh_batch::Prob &p = b->probs[size_t(i)];
+        dgh_ctx *u = b->groups[size_t(p.group)];
+        const int64_t blk0 = u->part_blk0[size_t(p.part)], nblk = u->part_blk0[size_t(p.part) + 1] - blk0;
+        const float *q = u->q3 + blk0 * 4 * u->Np * 32;
+        const double *ew = u->ew + blk0 * 32 * 2;
+        const int nb = u->energy_blocks;
+        cudaStream_t st = u->stream;
+        switch (u->N) {
+            case 1: k_energy_partial<1><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+            case 2: k_energy_partial<2><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+            case 3: k_energy_partial<3><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+            case 4: k_energy_partial<4><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+            case 5: k_energy_partial<5><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+            case 6: k_energy_partial<6><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
+        }
+        k_sum_partials<<<1, 256, 0, st>>>(u->partial, nb, u->d_energy);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(E, u->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            b->err = std::string("energy: ") + cudaGetErrorString(e);
+            return DGH_ECUDA;
+        }
+        return DGH_OK;
+    });
 }
 
 int dgh_batch_get_launch(const dgh_batch *b, int group, dgh_launch *o) {
-    if (!b || group < 0 || group >= int(b->groups.size())) return DGH_EINVAL;
-    return dgh_get_launch(b->groups[size_t(group)], o);
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        if (!b || group < 0 || group >= int(b->groups.size())) return DGH_EINVAL;
+        return dgh_get_launch(b->groups[size_t(group)], o);
+    });
 }
 
 int dgh_batch_tune(dgh_batch *b, int steps, double *ms_before, double *ms_after) {
-    ApiRange nvtx_range("dgh_batch_tune");
-    if (!b || steps < 1) return DGH_EINVAL;
-    const int64_t sc0 = b->step_count;
-    std::vector<int64_t> gsc;
-    for (dgh_ctx *u : b->groups) gsc.push_back(u->step_count);
-    int rc = tune_contexts(
-        b->groups, b->stream, steps, [&](int n) { return dgh_batch_step(b, n); }, [&]() { batch_drop_graphs(b); },
-        ms_before, ms_after, b->err);
-    b->step_count = sc0;
-    for (size_t i = 0; i < b->groups.size(); ++i) b->groups[i]->step_count = gsc[i];
-    return rc;
+    return dgh_guarded(err_slot(b), [&]() -> int {
+        ApiRange nvtx_range("dgh_batch_tune");
+        if (!b || steps < 1) return DGH_EINVAL;
+        const int64_t sc0 = b->step_count;
+        std::vector<int64_t> gsc;
+        for (dgh_ctx *u : b->groups) gsc.push_back(u->step_count);
+        int rc = tune_contexts(
+            b->groups, b->stream, steps, [&](int n) { return dgh_batch_step(b, n); }, [&]() { batch_drop_graphs(b); },
+            ms_before, ms_after, b->err);
+        b->step_count = sc0;
+        for (size_t i = 0; i < b->groups.size(); ++i) b->groups[i]->step_count = gsc[i];
+        return rc;
+    });
 }
 
 
 // ---------------------------------------------------------------- learned closure
 int dgh_closure_set_weights(dgh_ctx *ctx, const float *w, size_t n) {
-    if (!ctx) return DGH_EINVAL;
-    if (!w) {   // disable
-        ctx->cl_on = false;
-        ctx->dirty = true;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx) return DGH_EINVAL;
+        if (!w) {   // disable
+            ctx->cl_on = false;
+            ctx->dirty = true;
+            drop_graphs(ctx);
+            return DGH_OK;
+        }
+        if (n != size_t(MLP_NPARAM) && n != size_t(MLP_NPARAM + MLP_IN + 1)) {
+            ctx->err = "closure weights: expected " + std::to_string(MLP_NPARAM) + " values (or " +
+                       std::to_string(MLP_NPARAM + MLP_IN + 1) + " for the homogeneous form)";
+            return DGH_EINVAL;
+        }
+        if (ctx->P < 1 || ctx->T == 0) {
+            ctx->err = "closure needs HABC faces (P >= 1)";
+            return DGH_EINVAL;
+        }
+        std::vector<float> wb(n);   // BF16 weights (FP32 arithmetic); the scales of the homogeneous form stay FP32
+        for (size_t i = 0; i < n; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
+        int rc = DGH_OK;
+        if (!ctx->cl_w && ((rc = dalloc(ctx, ctx->cl_w, size_t(CL_MLP0 + 1))) || (rc = dalloc(ctx, ctx->cl_feat, size_t(ctx->T) * ctx->Np2 * MLP_IN)) ||
+                           (rc = dalloc(ctx, ctx->cl_rm, size_t(ctx->T) * ctx->Np2))))
+            return rc;
+        CK(cudaMemcpy(ctx->cl_w, wb.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+        k_mlp_zero<<<1, 256, 0, ctx->stream>>>(ctx->cl_w, ctx->cl_w + CL_MLP0);   // once per weight set
+        CK(cudaGetLastError());
+        ctx->cl_on = true;
+        ctx->cl_homog = n != size_t(MLP_NPARAM);
+        ctx->dirty = true;   // the exterior state is rebuilt with the closure before the next step
         drop_graphs(ctx);
         return DGH_OK;
-    }
-    if (n != size_t(MLP_NPARAM) && n != size_t(MLP_NPARAM + MLP_IN + 1)) {
-        ctx->err = "closure weights: expected " + std::to_string(MLP_NPARAM) + " values (or " +
-                   std::to_string(MLP_NPARAM + MLP_IN + 1) + " for the homogeneous form)";
-        return DGH_EINVAL;
-    }
-    if (ctx->P < 1 || ctx->T == 0) {
-        ctx->err = "closure needs HABC faces (P >= 1)";
-        return DGH_EINVAL;
-    }
-    std::vector<float> wb(n);   // BF16 weights (FP32 arithmetic); the scales of the homogeneous form stay FP32
-    for (size_t i = 0; i < n; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
-    int rc = DGH_OK;
-    if (!ctx->cl_w && ((rc = dalloc(ctx, ctx->cl_w, size_t(CL_MLP0 + 1))) || (rc = dalloc(ctx, ctx->cl_feat, size_t(ctx->T) * ctx->Np2 * MLP_IN)) ||
-                       (rc = dalloc(ctx, ctx->cl_rm, size_t(ctx->T) * ctx->Np2))))
-        return rc;
-    CK(cudaMemcpy(ctx->cl_w, wb.data(), n * sizeof(float), cudaMemcpyHostToDevice));
-    k_mlp_zero<<<1, 256, 0, ctx->stream>>>(ctx->cl_w, ctx->cl_w + CL_MLP0);   // once per weight set
-    CK(cudaGetLastError());
-    ctx->cl_on = true;
-    ctx->cl_homog = n != size_t(MLP_NPARAM);
-    ctx->dirty = true;   // the exterior state is rebuilt with the closure before the next step
-    drop_graphs(ctx);
-    return DGH_OK;
+    });
 }
 
 int dgh_closure_record(dgh_ctx *ctx, int shadow_order, int every, double fraction, int64_t max_samples, uint64_t seed) {
-    if (!ctx) return DGH_EINVAL;
-    if (ctx->sh) {
-        ctx->err = "recording is already enabled on this context";
-        return DGH_ESTATE;
-    }
-    if (shadow_order < 1 || shadow_order > MAXP || every < 1 || !(fraction > 0.0 && fraction <= 1.0) || max_samples < 1) {
-        ctx->err = "record: shadow order 1..12, every >= 1, 0 < fraction <= 1, max_samples >= 1";
-        return DGH_EINVAL;
-    }
-    if (ctx->P < 1 || ctx->T == 0) {
-        ctx->err = "record needs HABC faces (P >= 1)";
-        return DGH_EINVAL;
-    }
-    auto *h = new dgh_ctx::Shadow();
-    ctx->sh = h;
-    h->P = shadow_order;
-    std::string err;
-    if (!build_habc(h->P, h->habc, err)) {
-        ctx->err = err;
-        return DGH_EINVAL;
-    }
-    h->M = h->habc.M;
-    const int P = h->P, N = ctx->N, Np2 = ctx->Np2, Np1 = ctx->Np1;
-    const int64_t T = ctx->T, L = ctx->L;
-    std::vector<float> cP(static_cast<size_t>(P));
-    for (int a = 0; a < P; ++a) cP[a] = float(h->habc.c[a]);
-    int rc;
-    if ((rc = dalloc(ctx, h->q2, size_t(T) * P * 3 * Np2)) || (rc = dalloc(ctx, h->res2, size_t(T) * P * 3 * Np2)) ||
-        (rc = dalloc(ctx, h->tr2[0], size_t(T) * P * 3 * 2 * (N + 1))) || (rc = dalloc(ctx, h->tr2[1], size_t(T) * P * 3 * 2 * (N + 1))) ||
-        (rc = dalloc(ctx, h->qb2, size_t(T) * 3 * P * (N + 1))) || (rc = dalloc(ctx, h->q0_3, size_t(T) * Np2)) ||
-        (rc = dalloc(ctx, h->q1, size_t(L) * P * P * 2 * Np1)) || (rc = dalloc(ctx, h->res1, size_t(L) * P * P * 2 * Np1)) ||
-        (rc = dalloc(ctx, h->tr1[0], size_t(L) * P * P * 4)) || (rc = dalloc(ctx, h->tr1[1], size_t(L) * P * P * 4)) ||
-        (rc = dalloc(ctx, h->qb1, size_t(L) * 2 * P * P)) || (rc = dalloc(ctx, h->q0_2, size_t(L) * 2 * P * Np1)) ||
-        (rc = upload(ctx, h->H1, to_f(h->habc.H1))) || (rc = upload(ctx, h->H2, to_f(h->habc.H2))) ||
-        (rc = upload(ctx, h->Hc, to_f(h->habc.Hc))) || (rc = upload(ctx, h->cP, cP)) ||
-        (rc = dalloc(ctx, h->feat, size_t(T) * Np2 * MLP_IN)) || (rc = dalloc(ctx, h->rm, size_t(T) * Np2)) ||
-        (rc = dalloc(ctx, h->rm_main, size_t(T) * Np2)) || (rc = dalloc(ctx, h->samples, size_t(max_samples) * SAMPLE_W)) ||
-        (rc = dalloc(ctx, h->count, 1)))
-        return rc;
-    h->max_samples = max_samples;
-    h->every = every;
-    h->threshold = fraction >= 1.0 ? 0xFFFFFFFFu : uint32_t(fraction * 4294967296.0);
-    h->seed = seed;
-    h->tile2 = k2d_tile_max(P, 256);
-    h->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
-    h->smem2 = k2d_smem(N, P, h->tile2);
-    h->smem1 = k1d_smem(N, P, h->tile1);
-    h->smem0 = sizeof(float) * 3 * P * P;
-    if ((int64_t)h->smem2 > ctx->smem_optin || (int64_t)h->smem1 > ctx->smem_optin) {
-        ctx->err = "shadow chain tile does not fit in shared memory";
-        return DGH_EUNSUPPORTED;
-    }
-    h->grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((T + h->tile2 - 1) / h->tile2, int64_t(8) * ctx->sms));
-    h->grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((L + h->tile1 - 1) / h->tile1, int64_t(8) * ctx->sms));
-    ctx->dirty = true;
-    drop_graphs(ctx);
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx) return DGH_EINVAL;
+        if (ctx->sh) {
+            ctx->err = "recording is already enabled on this context";
+            return DGH_ESTATE;
+        }
+        if (shadow_order < 1 || shadow_order > MAXP || every < 1 || !(fraction > 0.0 && fraction <= 1.0) || max_samples < 1) {
+            ctx->err = "record: shadow order 1..12, every >= 1, 0 < fraction <= 1, max_samples >= 1";
+            return DGH_EINVAL;
+        }
+        if (ctx->P < 1 || ctx->T == 0) {
+            ctx->err = "record needs HABC faces (P >= 1)";
+            return DGH_EINVAL;
+        }
+        auto *h = new dgh_ctx::Shadow();
+        ctx->sh = h;
+        h->P = shadow_order;
+        std::string err;
+        if (!build_habc(h->P, h->habc, err)) {
+            ctx->err = err;
+            return DGH_EINVAL;
+        }
+        h->M = h->habc.M;
+        const int P = h->P, N = ctx->N, Np2 = ctx->Np2, Np1 = ctx->Np1;
+        const int64_t T = ctx->T, L = ctx->L;
+        std::vector<float> cP(static_cast<size_t>(P));
+        for (int a = 0; a < P; ++a) cP[a] = float(h->habc.c[a]);
+        int rc;
+        if ((rc = dalloc(ctx, h->q2, size_t(T) * P * 3 * Np2)) || (rc = dalloc(ctx, h->res2, size_t(T) * P * 3 * Np2)) ||
+            (rc = dalloc(ctx, h->tr2[0], size_t(T) * P * 3 * 2 * (N + 1))) || (rc = dalloc(ctx, h->tr2[1], size_t(T) * P * 3 * 2 * (N + 1))) ||
+            (rc = dalloc(ctx, h->qb2, size_t(T) * 3 * P * (N + 1))) || (rc = dalloc(ctx, h->q0_3, size_t(T) * Np2)) ||
+            (rc = dalloc(ctx, h->q1, size_t(L) * P * P * 2 * Np1)) || (rc = dalloc(ctx, h->res1, size_t(L) * P * P * 2 * Np1)) ||
+            (rc = dalloc(ctx, h->tr1[0], size_t(L) * P * P * 4)) || (rc = dalloc(ctx, h->tr1[1], size_t(L) * P * P * 4)) ||
+            (rc = dalloc(ctx, h->qb1, size_t(L) * 2 * P * P)) || (rc = dalloc(ctx, h->q0_2, size_t(L) * 2 * P * Np1)) ||
+            (rc = upload(ctx, h->H1, to_f(h->habc.H1))) || (rc = upload(ctx, h->H2, to_f(h->habc.H2))) ||
+            (rc = upload(ctx, h->Hc, to_f(h->habc.Hc))) || (rc = upload(ctx, h->cP, cP)) ||
+            (rc = dalloc(ctx, h->feat, size_t(T) * Np2 * MLP_IN)) || (rc = dalloc(ctx, h->rm, size_t(T) * Np2)) ||
+            (rc = dalloc(ctx, h->rm_main, size_t(T) * Np2)) || (rc = dalloc(ctx, h->samples, size_t(max_samples) * SAMPLE_W)) ||
+            (rc = dalloc(ctx, h->count, 1)))
+            return rc;
+        h->max_samples = max_samples;
+        h->every = every;
+        h->threshold = fraction >= 1.0 ? 0xFFFFFFFFu : uint32_t(fraction * 4294967296.0);
+        h->seed = seed;
+        h->tile2 = k2d_tile_max(P, 256);
+        h->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
+        h->smem2 = k2d_smem(N, P, h->tile2);
+        h->smem1 = k1d_smem(N, P, h->tile1);
+        h->smem0 = sizeof(float) * 3 * P * P;
+        if ((int64_t)h->smem2 > ctx->smem_optin || (int64_t)h->smem1 > ctx->smem_optin) {
+            ctx->err = "shadow chain tile does not fit in shared memory";
+            return DGH_EUNSUPPORTED;
+        }
+        h->grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((T + h->tile2 - 1) / h->tile2, int64_t(8) * ctx->sms));
+        h->grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((L + h->tile1 - 1) / h->tile1, int64_t(8) * ctx->sms));
+        ctx->dirty = true;
+        drop_graphs(ctx);
+        return DGH_OK;
+    });
 }
 
 int dgh_closure_samples(dgh_ctx *ctx, float *out, int64_t max_rows, int64_t *count) {
-    if (!ctx || !count || (!out && max_rows > 0)) return DGH_EINVAL;
-    if (!ctx->sh) {
-        ctx->err = "recording is not enabled on this context";
-        return DGH_ESTATE;
-    }
-    unsigned long long c = 0;
-    CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpy(&c, ctx->sh->count, sizeof(c), cudaMemcpyDeviceToHost));
-    const int64_t have = std::min<int64_t>((int64_t)c, ctx->sh->max_samples);
-    *count = have;
-    const int64_t rows = std::min<int64_t>(have, max_rows);
-    if (rows > 0) CK(cudaMemcpy(out, ctx->sh->samples, size_t(rows) * SAMPLE_W * sizeof(float), cudaMemcpyDeviceToHost));
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !count || (!out && max_rows > 0)) return DGH_EINVAL;
+        if (!ctx->sh) {
+            ctx->err = "recording is not enabled on this context";
+            return DGH_ESTATE;
+        }
+        unsigned long long c = 0;
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpy(&c, ctx->sh->count, sizeof(c), cudaMemcpyDeviceToHost));
+        const int64_t have = std::min<int64_t>((int64_t)c, ctx->sh->max_samples);
+        *count = have;
+        const int64_t rows = std::min<int64_t>(have, max_rows);
+        if (rows > 0) CK(cudaMemcpy(out, ctx->sh->samples, size_t(rows) * SAMPLE_W * sizeof(float), cudaMemcpyDeviceToHost));
+        return DGH_OK;
+    });
 }
 
 int dgh_closure_train(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist, double *final_mse) {
-    if (!ctx || !cfg || !w_out) return DGH_EINVAL;
-    int64_t n = 0;
-    int rc = dgh_closure_samples(ctx, nullptr, 0, &n);
-    if (rc) return rc;
-    if (n < 2) {
-        ctx->err = "closure train: fewer than 2 recorded rows";
-        return DGH_ESTATE;
-    }
-    std::vector<float> rows(static_cast<size_t>(n) * SAMPLE_W), X(static_cast<size_t>(n) * MLP_IN),
-        Y(static_cast<size_t>(n));
-    if ((rc = dgh_closure_samples(ctx, rows.data(), n, &n))) return rc;
-    for (int64_t r = 0; r < n; ++r) {
-        for (int i = 0; i < MLP_IN; ++i) X[size_t(r) * MLP_IN + i] = rows[size_t(r) * SAMPLE_W + i];
-        Y[size_t(r)] = rows[size_t(r) * SAMPLE_W + MLP_IN];
-    }
-    rc = dgh_mlp_train(X.data(), Y.data(), n, cfg, w_out, loss_hist, final_mse);
-    if (rc) ctx->err = dgh_last_error(nullptr);
-    return rc;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !cfg || !w_out) return DGH_EINVAL;
+        int64_t n = 0;
+        int rc = dgh_closure_samples(ctx, nullptr, 0, &n);
+        if (rc) return rc;
+        if (n < 2) {
+            ctx->err = "closure train: fewer than 2 recorded rows";
+            return DGH_ESTATE;
+        }
+        std::vector<float> rows(static_cast<size_t>(n) * SAMPLE_W), X(static_cast<size_t>(n) * MLP_IN),
+            Y(static_cast<size_t>(n));
+        if ((rc = dgh_closure_samples(ctx, rows.data(), n, &n))) return rc;
+        for (int64_t r = 0; r < n; ++r) {
+            for (int i = 0; i < MLP_IN; ++i) X[size_t(r) * MLP_IN + i] = rows[size_t(r) * SAMPLE_W + i];
+            Y[size_t(r)] = rows[size_t(r) * SAMPLE_W + MLP_IN];
+        }
+        rc = dgh_mlp_train(X.data(), Y.data(), n, cfg, w_out, loss_hist, final_mse);
+        if (rc) ctx->err = dgh_last_error(nullptr);
+        return rc;
+    });
 }
 
 }  // extern "C"
@@ -2614,139 +2727,145 @@ int mlp_setup(int &sms) {
 extern "C" {
 
 int dgh_closure_eval(const float *w, size_t nw, const float *X, int64_t n, float *y) {
-    if (!w || (n > 0 && (!X || !y)) || n < 0 || (nw != size_t(MLP_NPARAM) && nw != size_t(MLP_NPARAM + MLP_IN + 1)))
-        return mlp_fail("closure eval: invalid arguments", DGH_EINVAL);
-    if (n == 0) return DGH_OK;
-    std::vector<float> wb(nw);
-    for (size_t i = 0; i < nw; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
-    DevScratch d;
-    float *dw = d.get<float>(nw), *dX = d.get<float>(size_t(n) * MLP_IN), *dy = d.get<float>(size_t(n));
-    float *d0 = d.get<float>(1);
-    if (!dw || !dX || !dy || !d0) return mlp_fail("closure eval: device allocation failed", DGH_ENOMEM);
-    cudaMemcpy(dw, wb.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
-    k_mlp_zero<<<1, 256>>>(dw, d0);
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    k_closure_apply<<<blocks, 256>>>(dw, nw == size_t(MLP_NPARAM) ? nullptr : dw + MLP_NPARAM, d0, dX, nullptr, n, 1,
-                                     nullptr, nullptr, dy);
-    cudaError_t e = cudaMemcpy(y, dy, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return mlp_fail(std::string("closure eval: ") + cudaGetErrorString(e), DGH_ECUDA);
-    return DGH_OK;
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (!w || (n > 0 && (!X || !y)) || n < 0 || (nw != size_t(MLP_NPARAM) && nw != size_t(MLP_NPARAM + MLP_IN + 1)))
+            return mlp_fail("closure eval: invalid arguments", DGH_EINVAL);
+        if (n == 0) return DGH_OK;
+        std::vector<float> wb(nw);
+        for (size_t i = 0; i < nw; ++i) wb[i] = i < size_t(MLP_NPARAM) ? __bfloat162float(__float2bfloat16_rn(w[i])) : w[i];
+        DevScratch d;
+        float *dw = d.get<float>(nw), *dX = d.get<float>(size_t(n) * MLP_IN), *dy = d.get<float>(size_t(n));
+        float *d0 = d.get<float>(1);
+        if (!dw || !dX || !dy || !d0) return mlp_fail("closure eval: device allocation failed", DGH_ENOMEM);
+        cudaMemcpy(dw, wb.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
+        k_mlp_zero<<<1, 256>>>(dw, d0);
+        const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+        k_closure_apply<<<blocks, 256>>>(dw, nw == size_t(MLP_NPARAM) ? nullptr : dw + MLP_NPARAM, d0, dX, nullptr, n, 1,
+                                         nullptr, nullptr, dy);
+        cudaError_t e = cudaMemcpy(y, dy, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return mlp_fail(std::string("closure eval: ") + cudaGetErrorString(e), DGH_ECUDA);
+        return DGH_OK;
+    });
 }
 
 int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n, double *loss, float *grad) {
-    if (!w || !X || !Y || n < 1 || !loss || !grad) return mlp_fail("mlp loss/grad: invalid arguments", DGH_EINVAL);
-    int sms = 1, rc = mlp_setup(sms);
-    if (rc) return rc;
-    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
-    DevScratch d;
-    float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dY = d.get<float>(size_t(n));
-    float *dpart = d.get<float>(size_t(nblocks) * (MLP_NPARAM + 1)), *dg = d.get<float>(MLP_NPARAM);
-    double *dl = d.get<double>(1);
-    if (!dw || !dX || !dY || !dpart || !dg || !dl) return mlp_fail("mlp loss/grad: device allocation failed", DGH_ENOMEM);
-    cudaMemcpy(dw, w, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(dY, Y, size_t(n) * sizeof(float), cudaMemcpyHostToDevice);
-    if ((rc = mlp_loss_grad_dev(dw, dX, dY, nullptr, n, dpart, nblocks, dg, dl))) return rc;
-    cudaMemcpy(grad, dg, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
-    cudaError_t e = cudaMemcpy(loss, dl, sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return mlp_fail(std::string("mlp loss/grad: ") + cudaGetErrorString(e), DGH_ECUDA);
-    return DGH_OK;
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (!w || !X || !Y || n < 1 || !loss || !grad) return mlp_fail("mlp loss/grad: invalid arguments", DGH_EINVAL);
+        int sms = 1, rc = mlp_setup(sms);
+        if (rc) return rc;
+        const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
+        DevScratch d;
+        float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dY = d.get<float>(size_t(n));
+        float *dpart = d.get<float>(size_t(nblocks) * (MLP_NPARAM + 1)), *dg = d.get<float>(MLP_NPARAM);
+        double *dl = d.get<double>(1);
+        if (!dw || !dX || !dY || !dpart || !dg || !dl) return mlp_fail("mlp loss/grad: device allocation failed", DGH_ENOMEM);
+        cudaMemcpy(dw, w, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(dX, X, size_t(n) * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(dY, Y, size_t(n) * sizeof(float), cudaMemcpyHostToDevice);
+        if ((rc = mlp_loss_grad_dev(dw, dX, dY, nullptr, n, dpart, nblocks, dg, dl))) return rc;
+        cudaMemcpy(grad, dg, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpy(loss, dl, sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return mlp_fail(std::string("mlp loss/grad: ") + cudaGetErrorString(e), DGH_ECUDA);
+        return DGH_OK;
+    });
 }
 
 int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
                   double *final_mse) {
-    ApiRange nvtx_range("dgh_mlp_train");
-    if (!X || !Y || n < 2 || !cfg || !w_out || cfg->steps < 0 || cfg->batch < 1 || !(cfg->lr > 0.f))
-        return mlp_fail("mlp train: invalid arguments", DGH_EINVAL);
-    int sms = 1, rc = mlp_setup(sms);
-    if (rc) return rc;
-    // standardise inputs and target (folded back into the weights at the end)
-    double mu[MLP_IN + 1] = {0}, sd[MLP_IN + 1] = {0};
-    for (int64_t r = 0; r < n; ++r) {
-        for (int i = 0; i < MLP_IN; ++i) mu[i] += X[r * MLP_IN + i];
-        mu[MLP_IN] += Y[r];
-    }
-    for (int i = 0; i <= MLP_IN; ++i) mu[i] /= double(n);
-    for (int64_t r = 0; r < n; ++r) {
-        for (int i = 0; i < MLP_IN; ++i) sd[i] += (X[r * MLP_IN + i] - mu[i]) * (X[r * MLP_IN + i] - mu[i]);
-        sd[MLP_IN] += (Y[r] - mu[MLP_IN]) * (Y[r] - mu[MLP_IN]);
-    }
-    for (int i = 0; i <= MLP_IN; ++i) sd[i] = std::sqrt(sd[i] / double(n)) > 1e-30 ? std::sqrt(sd[i] / double(n)) : 1.0;
-    std::vector<float> Xn(static_cast<size_t>(n) * MLP_IN), Yn(static_cast<size_t>(n));
-    for (int64_t r = 0; r < n; ++r) {
-        for (int i = 0; i < MLP_IN; ++i) Xn[r * MLP_IN + i] = float((X[r * MLP_IN + i] - mu[i]) / sd[i]);
-        Yn[r] = float((Y[r] - mu[MLP_IN]) / sd[MLP_IN]);
-    }
-    // Glorot-uniform initial weights (splitmix64 stream), zero biases
-    std::vector<float> w(MLP_NPARAM, 0.f);
-    uint64_t st = cfg->seed;
-    auto uni = [&]() {
-        st += 0x9E3779B97F4A7C15ull;
-        uint64_t z = st;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        return double(z >> 11) / double(1ull << 53);
-    };
-    auto glorot = [&](int off, int fan_in, int fan_out, int count) {
-        const double a = std::sqrt(6.0 / (fan_in + fan_out));
-        for (int i = 0; i < count; ++i) w[off + i] = float((2.0 * uni() - 1.0) * a);
-    };
-    glorot(MLP_OW1, MLP_IN, MLP_H, MLP_H * MLP_IN);
-    glorot(MLP_OW2, MLP_H, MLP_H, MLP_H * MLP_H);
-    glorot(MLP_OW3, MLP_H, 1, MLP_H);
-    const int64_t bs = std::min<int64_t>(cfg->batch, n);
-    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((bs + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
-    DevScratch d;
-    float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dY = d.get<float>(size_t(n));
-    float *dm = d.get<float>(MLP_NPARAM), *dv = d.get<float>(MLP_NPARAM), *dg = d.get<float>(MLP_NPARAM);
-    float *dpart = d.get<float>(size_t(2 * sms) * (MLP_NPARAM + 1));
-    int64_t *didx = d.get<int64_t>(size_t(bs));
-    double *dl = d.get<double>(size_t(std::max<int64_t>(cfg->steps, 1)) + 1);
-    if (!dw || !dX || !dY || !dm || !dv || !dg || !dpart || !didx || !dl)
-        return mlp_fail("mlp train: device allocation failed", DGH_ENOMEM);
-    cudaMemcpy(dw, w.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(dX, Xn.data(), Xn.size() * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(dY, Yn.data(), Yn.size() * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemset(dm, 0, MLP_NPARAM * sizeof(float));
-    cudaMemset(dv, 0, MLP_NPARAM * sizeof(float));
-    const float b1 = cfg->beta1 > 0.f ? cfg->beta1 : 0.9f, b2 = cfg->beta2 > 0.f ? cfg->beta2 : 0.999f;
-    const float eps = cfg->eps > 0.f ? cfg->eps : 1e-8f;
-    double pb1 = 1.0, pb2 = 1.0;
-    for (int64_t it = 0; it < cfg->steps; ++it) {
-        k_batch_indices<<<(int)((bs + 255) / 256), 256>>>(didx, bs, n, cfg->seed * 0x100000001B3ull + uint64_t(it));
-        if ((rc = mlp_loss_grad_dev(dw, dX, dY, didx, bs, dpart, nblocks, dg, dl + it))) return rc;
-        pb1 *= b1;
-        pb2 *= b2;
-        k_adam<<<(MLP_NPARAM + 255) / 256, 256>>>(dw, dg, dm, dv, MLP_NPARAM, cfg->lr, b1, b2, eps, float(1.0 - pb1),
-                                                  float(1.0 - pb2));
-    }
-    // final loss on all rows (normalised units)
-    const int nbf = (int)std::max<int64_t>(1, std::min<int64_t>((n + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
-    if ((rc = mlp_loss_grad_dev(dw, dX, dY, nullptr, n, dpart, nbf, dg, dl + cfg->steps))) return rc;
-    std::vector<double> hist(size_t(cfg->steps) + 1);
-    cudaMemcpy(w.data(), dw, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
-    cudaError_t e = cudaMemcpy(hist.data(), dl, hist.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return mlp_fail(std::string("mlp train: ") + cudaGetErrorString(e), DGH_ECUDA);
-    // losses are 0.5 * mean squared error of the standardised target
-    if (loss_hist)
-        for (int64_t it = 0; it < cfg->steps; ++it) loss_hist[it] = 2.0 * hist[size_t(it)] * sd[MLP_IN] * sd[MLP_IN];
-    if (final_mse) *final_mse = 2.0 * hist[size_t(cfg->steps)] * sd[MLP_IN] * sd[MLP_IN];
-    // fold the standardisation into the weights: raw features in, raw target out
-    for (int j = 0; j < MLP_H; ++j) {
-        double b = w[MLP_OB1 + j];
-        for (int i = 0; i < MLP_IN; ++i) {
-            const double wi = w[MLP_OW1 + j * MLP_IN + i] / sd[i];
-            b -= wi * mu[i];
-            w_out[MLP_OW1 + j * MLP_IN + i] = float(wi);
+    return dgh_guarded(nullptr, [&]() -> int {
+        ApiRange nvtx_range("dgh_mlp_train");
+        if (!X || !Y || n < 2 || !cfg || !w_out || cfg->steps < 0 || cfg->batch < 1 || !(cfg->lr > 0.f))
+            return mlp_fail("mlp train: invalid arguments", DGH_EINVAL);
+        int sms = 1, rc = mlp_setup(sms);
+        if (rc) return rc;
+        // standardise inputs and target (folded back into the weights at the end)
+        double mu[MLP_IN + 1] = {0}, sd[MLP_IN + 1] = {0};
+        for (int64_t r = 0; r < n; ++r) {
+            for (int i = 0; i < MLP_IN; ++i) mu[i] += X[r * MLP_IN + i];
+            mu[MLP_IN] += Y[r];
         }
-        w_out[MLP_OB1 + j] = float(b);
-    }
-    for (int i = MLP_OW2; i < MLP_OW3; ++i) w_out[i] = w[i];
-    for (int j = 0; j < MLP_H; ++j) w_out[MLP_OW3 + j] = float(w[MLP_OW3 + j] * sd[MLP_IN]);
-    w_out[MLP_OB3] = float(w[MLP_OB3] * sd[MLP_IN] + mu[MLP_IN]);
-    return DGH_OK;
+        for (int i = 0; i <= MLP_IN; ++i) mu[i] /= double(n);
+        for (int64_t r = 0; r < n; ++r) {
+            for (int i = 0; i < MLP_IN; ++i) sd[i] += (X[r * MLP_IN + i] - mu[i]) * (X[r * MLP_IN + i] - mu[i]);
+            sd[MLP_IN] += (Y[r] - mu[MLP_IN]) * (Y[r] - mu[MLP_IN]);
+        }
+        for (int i = 0; i <= MLP_IN; ++i) sd[i] = std::sqrt(sd[i] / double(n)) > 1e-30 ? std::sqrt(sd[i] / double(n)) : 1.0;
+        std::vector<float> Xn(static_cast<size_t>(n) * MLP_IN), Yn(static_cast<size_t>(n));
+        for (int64_t r = 0; r < n; ++r) {
+            for (int i = 0; i < MLP_IN; ++i) Xn[r * MLP_IN + i] = float((X[r * MLP_IN + i] - mu[i]) / sd[i]);
+            Yn[r] = float((Y[r] - mu[MLP_IN]) / sd[MLP_IN]);
+        }
+        // Glorot-uniform initial weights (splitmix64 stream), zero biases
+        std::vector<float> w(MLP_NPARAM, 0.f);
+        uint64_t st = cfg->seed;
+        auto uni = [&]() {
+            st += 0x9E3779B97F4A7C15ull;
+            uint64_t z = st;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            return double(z >> 11) / double(1ull << 53);
+        };
+        auto glorot = [&](int off, int fan_in, int fan_out, int count) {
+            const double a = std::sqrt(6.0 / (fan_in + fan_out));
+            for (int i = 0; i < count; ++i) w[off + i] = float((2.0 * uni() - 1.0) * a);
+        };
+        glorot(MLP_OW1, MLP_IN, MLP_H, MLP_H * MLP_IN);
+        glorot(MLP_OW2, MLP_H, MLP_H, MLP_H * MLP_H);
+        glorot(MLP_OW3, MLP_H, 1, MLP_H);
+        const int64_t bs = std::min<int64_t>(cfg->batch, n);
+        const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((bs + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
+        DevScratch d;
+        float *dw = d.get<float>(MLP_NPARAM), *dX = d.get<float>(size_t(n) * MLP_IN), *dY = d.get<float>(size_t(n));
+        float *dm = d.get<float>(MLP_NPARAM), *dv = d.get<float>(MLP_NPARAM), *dg = d.get<float>(MLP_NPARAM);
+        float *dpart = d.get<float>(size_t(2 * sms) * (MLP_NPARAM + 1));
+        int64_t *didx = d.get<int64_t>(size_t(bs));
+        double *dl = d.get<double>(size_t(std::max<int64_t>(cfg->steps, 1)) + 1);
+        if (!dw || !dX || !dY || !dm || !dv || !dg || !dpart || !didx || !dl)
+            return mlp_fail("mlp train: device allocation failed", DGH_ENOMEM);
+        cudaMemcpy(dw, w.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(dX, Xn.data(), Xn.size() * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(dY, Yn.data(), Yn.size() * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemset(dm, 0, MLP_NPARAM * sizeof(float));
+        cudaMemset(dv, 0, MLP_NPARAM * sizeof(float));
+        const float b1 = cfg->beta1 > 0.f ? cfg->beta1 : 0.9f, b2 = cfg->beta2 > 0.f ? cfg->beta2 : 0.999f;
+        const float eps = cfg->eps > 0.f ? cfg->eps : 1e-8f;
+        double pb1 = 1.0, pb2 = 1.0;
+        for (int64_t it = 0; it < cfg->steps; ++it) {
+            k_batch_indices<<<(int)((bs + 255) / 256), 256>>>(didx, bs, n, cfg->seed * 0x100000001B3ull + uint64_t(it));
+            if ((rc = mlp_loss_grad_dev(dw, dX, dY, didx, bs, dpart, nblocks, dg, dl + it))) return rc;
+            pb1 *= b1;
+            pb2 *= b2;
+            k_adam<<<(MLP_NPARAM + 255) / 256, 256>>>(dw, dg, dm, dv, MLP_NPARAM, cfg->lr, b1, b2, eps, float(1.0 - pb1),
+                                                      float(1.0 - pb2));
+        }
+        // final loss on all rows (normalised units)
+        const int nbf = (int)std::max<int64_t>(1, std::min<int64_t>((n + MLP_BS - 1) / MLP_BS, int64_t(2) * sms));
+        if ((rc = mlp_loss_grad_dev(dw, dX, dY, nullptr, n, dpart, nbf, dg, dl + cfg->steps))) return rc;
+        std::vector<double> hist(size_t(cfg->steps) + 1);
+        cudaMemcpy(w.data(), dw, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpy(hist.data(), dl, hist.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return mlp_fail(std::string("mlp train: ") + cudaGetErrorString(e), DGH_ECUDA);
+        // losses are 0.5 * mean squared error of the standardised target
+        if (loss_hist)
+            for (int64_t it = 0; it < cfg->steps; ++it) loss_hist[it] = 2.0 * hist[size_t(it)] * sd[MLP_IN] * sd[MLP_IN];
+        if (final_mse) *final_mse = 2.0 * hist[size_t(cfg->steps)] * sd[MLP_IN] * sd[MLP_IN];
+        // fold the standardisation into the weights: raw features in, raw target out
+        for (int j = 0; j < MLP_H; ++j) {
+            double b = w[MLP_OB1 + j];
+            for (int i = 0; i < MLP_IN; ++i) {
+                const double wi = w[MLP_OW1 + j * MLP_IN + i] / sd[i];
+                b -= wi * mu[i];
+                w_out[MLP_OW1 + j * MLP_IN + i] = float(wi);
+            }
+            w_out[MLP_OB1 + j] = float(b);
+        }
+        for (int i = MLP_OW2; i < MLP_OW3; ++i) w_out[i] = w[i];
+        for (int j = 0; j < MLP_H; ++j) w_out[MLP_OW3 + j] = float(w[MLP_OW3 + j] * sd[MLP_IN]);
+        w_out[MLP_OB3] = float(w[MLP_OB3] * sd[MLP_IN] + mu[MLP_IN]);
+        return DGH_OK;
+    });
 }
 
 
@@ -2804,50 +2923,56 @@ __global__ void __launch_bounds__(256) k_probe_ffma2(float *out, int iters, floa
 }  // namespace
 
 extern "C" int dgh_fp32_probe(double *tflops_ffma, double *tflops_ffma2) {
-    if (!tflops_ffma || !tflops_ffma2) return mlp_fail("fp32 probe: null output", DGH_EINVAL);
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    DevScratch d;
-    float *out = d.get<float>(size_t(sms) * 64);
-    cudaEvent_t e0, e1;
-    if (!out || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-        return mlp_fail("fp32 probe: set-up failed", DGH_ECUDA);
-    const int blocks = sms * 8, iters = 1 << 14;
-    double best[2] = {0.0, 0.0};
-    for (int kind = 0; kind < 2; ++kind)
-        for (int rep = 0; rep < 4; ++rep) {   // first repetition warms up
-            cudaEventRecord(e0);
-            if (kind == 0) k_probe_ffma<<<blocks, 256>>>(out, iters, -1.f);
-            else k_probe_ffma2<<<blocks, 256>>>(out, iters, -1.f);
-            cudaEventRecord(e1);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const double fma = double(blocks) * 256 * iters * 8 * (kind == 0 ? 1 : 2);
-            if (rep > 0) best[kind] = std::max(best[kind], 2.0 * fma / (ms * 1e-3) / 1e12);
-        }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return mlp_fail(std::string("fp32 probe: ") + cudaGetErrorString(e), DGH_ECUDA);
-    *tflops_ffma = best[0];
-    *tflops_ffma2 = best[1];
-    return DGH_OK;
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (!tflops_ffma || !tflops_ffma2) return mlp_fail("fp32 probe: null output", DGH_EINVAL);
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        DevScratch d;
+        float *out = d.get<float>(size_t(sms) * 64);
+        cudaEvent_t e0, e1;
+        if (!out || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            return mlp_fail("fp32 probe: set-up failed", DGH_ECUDA);
+        const int blocks = sms * 8, iters = 1 << 14;
+        double best[2] = {0.0, 0.0};
+        for (int kind = 0; kind < 2; ++kind)
+            for (int rep = 0; rep < 4; ++rep) {   // first repetition warms up
+                cudaEventRecord(e0);
+                if (kind == 0) k_probe_ffma<<<blocks, 256>>>(out, iters, -1.f);
+                else k_probe_ffma2<<<blocks, 256>>>(out, iters, -1.f);
+                cudaEventRecord(e1);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double fma = double(blocks) * 256 * iters * 8 * (kind == 0 ? 1 : 2);
+                if (rep > 0) best[kind] = std::max(best[kind], 2.0 * fma / (ms * 1e-3) / 1e12);
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return mlp_fail(std::string("fp32 probe: ") + cudaGetErrorString(e), DGH_ECUDA);
+        *tflops_ffma = best[0];
+        *tflops_ffma2 = best[1];
+        return DGH_OK;
+    });
 }
 
 extern "C" int dgh_selftest_wait(dgh_ctx *ctx, int64_t limit) {
-    if (!ctx || limit < 1) return DGH_EINVAL;
-    k_selftest_wait<<<1, 32, 0, ctx->stream>>>(ctx->d_err, (unsigned long long)limit);
-    CK(cudaGetLastError());
-    return dgh_sync(ctx);
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || limit < 1) return DGH_EINVAL;
+        k_selftest_wait<<<1, 32, 0, ctx->stream>>>(ctx->d_err, (unsigned long long)limit);
+        CK(cudaGetLastError());
+        return dgh_sync(ctx);
+    });
 }
 
 extern "C" int dgh_clear_error(dgh_ctx *ctx) {
-    if (!ctx) return DGH_EINVAL;
-    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx) return DGH_EINVAL;
+        CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return DGH_OK;
+    });
 }
 
 extern "C" {
@@ -2930,28 +3055,30 @@ __global__ void __launch_bounds__(kNoAllocBlock) k_energy_partial_fixed(const fl
 }  // namespace
 
 extern "C" int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stream) {
-    if (!ctx || !d_energy) return DGH_EINVAL;
-    const int64_t nblocks = (ctx->K32 * 32 * 4 + kNoAllocBlock - 1) / kNoAllocBlock;
-    if (nblocks > kNoAllocMaxPartials) {
-        ctx->err = "dgh_get_energy_noalloc: " + std::to_string(ctx->K) + " cells need " + std::to_string(nblocks) +
-                   " partial sums, more than the static scratch holds (" + std::to_string(kNoAllocMaxPartials) +
-                   ", i.e. at most " + std::to_string(kNoAllocMaxPartials * kNoAllocBlock / 4) + " cells)";
-        return DGH_EINVAL;
-    }
-    double *scratch = nullptr;
-    int rc = noalloc_scratch(ctx, &scratch);
-    if (rc) return rc;
-    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
-    const int nb = (int)nblocks;
-    switch (ctx->N) {
-        case 1: k_energy_partial_fixed<1><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-        case 2: k_energy_partial_fixed<2><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-        case 3: k_energy_partial_fixed<3><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-        case 4: k_energy_partial_fixed<4><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-        case 5: k_energy_partial_fixed<5><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-        case 6: k_energy_partial_fixed<6><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-    }
-    k_sum_partials<<<1, 256, 0, s>>>(scratch, nb, d_energy);
-    CK(cudaGetLastError());
-    return DGH_OK;
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        if (!ctx || !d_energy) return DGH_EINVAL;
+        const int64_t nblocks = (ctx->K32 * 32 * 4 + kNoAllocBlock - 1) / kNoAllocBlock;
+        if (nblocks > kNoAllocMaxPartials) {
+            ctx->err = "dgh_get_energy_noalloc: " + std::to_string(ctx->K) + " cells need " + std::to_string(nblocks) +
+                       " partial sums, more than the static scratch holds (" + std::to_string(kNoAllocMaxPartials) +
+                       ", i.e. at most " + std::to_string(kNoAllocMaxPartials * kNoAllocBlock / 4) + " cells)";
+            return DGH_EINVAL;
+        }
+        double *scratch = nullptr;
+        int rc = noalloc_scratch(ctx, &scratch);
+        if (rc) return rc;
+        cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+        const int nb = (int)nblocks;
+        switch (ctx->N) {
+            case 1: k_energy_partial_fixed<1><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+            case 2: k_energy_partial_fixed<2><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+            case 3: k_energy_partial_fixed<3><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+            case 4: k_energy_partial_fixed<4><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+            case 5: k_energy_partial_fixed<5><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+            case 6: k_energy_partial_fixed<6><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+        }
+        k_sum_partials<<<1, 256, 0, s>>>(scratch, nb, d_energy);
+        CK(cudaGetLastError());
+        return DGH_OK;
+    });
 }
