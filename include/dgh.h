@@ -268,6 +268,13 @@ int dgh_fp32_probe(double *tflops_ffma, double *tflops_ffma2);
 int dgh_selftest_wait(dgh_ctx *ctx, int64_t limit);
 int dgh_clear_error(dgh_ctx *ctx);
 
+/* Boundary self-test (host only, no GPU): throws inside the guard every entry
+ * point runs under -- kind 0 std::bad_alloc (returns DGH_ENOMEM), 1 a
+ * std::runtime_error, 2 a non-standard exception (both DGH_EINVAL); the
+ * message ("internal error: ...") is in dgh_last_error(NULL).  Any other
+ * kind throws nothing and returns DGH_OK. */
+int dgh_selftest_throw(int kind);
+
 /* Serialises the complete time-stepping state (all levels, residuals,
  * boundary algebra, time, step count) into buf.  Call with buf == NULL to
  * query the size in *size.  dgh_load_state restores it into a context

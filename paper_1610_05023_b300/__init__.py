@@ -25,8 +25,13 @@ PREC_SPLIT_BF16 = 3
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ETIMEOUT", -6: "ESTATE",
            -7: "EUNSUPPORTED", -8: "EBOUNDS"}
-DGH_ETIMEOUT = -5
+DGH_EINVAL = -1
+DGH_ENOMEM = -2
+DGH_ECUDA = -3
 DGH_EUNSTABLE = -4
+DGH_ETIMEOUT = -5
+DGH_ESTATE = -6
+DGH_EUNSUPPORTED = -7
 DGH_EBOUNDS = -8
 
 
@@ -128,6 +133,7 @@ def load_library(path=LIB_PATH):
         "dgh_batch_get_launch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_Launch)]),
         "dgh_batch_tune": (ctypes.c_int, [P, ctypes.c_int, D, D]),
         "dgh_selftest_wait": (ctypes.c_int, [P, ctypes.c_int64]),
+        "dgh_selftest_throw": (ctypes.c_int, [ctypes.c_int]),
         "dgh_fp32_probe": (ctypes.c_int, [D, D]),
         "dgh_clear_error": (ctypes.c_int, [P]),
         "dgh_closure_set_weights": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),

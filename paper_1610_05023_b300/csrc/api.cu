@@ -10,6 +10,7 @@
 #include <exception>
 #include <mutex>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -2953,6 +2954,15 @@ extern "C" int dgh_fp32_probe(double *tflops_ffma, double *tflops_ffma2) {
         if (e != cudaSuccess) return mlp_fail(std::string("fp32 probe: ") + cudaGetErrorString(e), DGH_ECUDA);
         *tflops_ffma = best[0];
         *tflops_ffma2 = best[1];
+        return DGH_OK;
+    });
+}
+
+extern "C" int dgh_selftest_throw(int kind) {
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (kind == 0) throw std::bad_alloc();
+        if (kind == 1) throw std::runtime_error("self-test exception");
+        if (kind == 2) throw kind;
         return DGH_OK;
     });
 }

@@ -153,3 +153,16 @@ def test_batch_plan_separates_precisions():
              dict(VX=VX, EToV=EToV, N=3, P=2)]
     gof, infos = dgh.batch_plan(probs)
     assert gof == [0, 1, 0] and len(infos) == 2
+
+
+def test_exceptions_stop_at_the_boundary():
+    """No C++ exception crosses the C ABI: every entry point runs under one
+    guard, exercised here by a host-only self-test call."""
+    lib = dgh.load_library()
+    cases = [(0, dgh.DGH_ENOMEM, "host memory exhausted"), (1, dgh.DGH_EINVAL, "self-test exception"),
+             (2, dgh.DGH_EINVAL, "unknown C++ exception")]
+    for kind, code, text in cases:
+        assert lib.dgh_selftest_throw(kind) == code
+        msg = lib.dgh_last_error(None).decode()
+        assert msg.startswith("internal error:") and text in msg, msg
+    assert lib.dgh_selftest_throw(3) == 0
