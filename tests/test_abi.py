@@ -166,3 +166,17 @@ def test_exceptions_stop_at_the_boundary():
         msg = lib.dgh_last_error(None).decode()
         assert msg.startswith("internal error:") and text in msg, msg
     assert lib.dgh_selftest_throw(3) == 0
+
+
+def test_create_fails_cleanly_without_a_gpu():
+    """On a machine without a usable GPU, creating a solver stops at its first
+    device allocation with DGH_ECUDA and a message; repeated attempts work,
+    because a failed create frees the context it had built."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    VX, EToV = W.kuhn_mesh(2, 1.0, 0.02, seed=1)
+    for _ in range(3):
+        with pytest.raises(dgh.DghError) as e:
+            dgh.Solver(VX, EToV, 3, 2)
+        assert e.value.code == dgh.DGH_ECUDA and "cuda" in str(e.value).lower()
