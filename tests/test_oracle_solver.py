@@ -370,3 +370,47 @@ def test_volume_energy_rate_is_the_upwind_dissipation_across_materials():
     assert jumps > 0
     assert abs(dE + diss) <= 1e-12 * diss
     assert abs(dE + diss1) > 1e-2 * diss
+
+
+def test_point_source_is_the_delta_functional_of_its_cell():
+    """Reading E14: the point source enters the pressure equation as
+    S(t) M_k^-1 l(x_s) in the cell k that contains x_s.  Pins: the cell
+    contains x_s (barycentric coordinates, independent of the oracle's
+    reference map), and for every monomial q of degree <= N the cell's exact
+    mass matrix gives int_k q s dV = q(x_s)."""
+    N = 3
+    VX, EToV = W.kuhn_mesh(2, 1.0, 0.05, seed=91)
+    m = CuboidMesh(VX, EToV, N, 0, [BC_HABC] * 6, 1.0, 1.0)
+    o = Solver(m)
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        xs = rng.uniform(-0.9, 0.9, 3)
+        k = o.add_point_source(xs, 2.0, 0.5)
+        vec = o.sources[-1][1]
+        v = m.VX[m.EToV[k]]
+        lam = np.linalg.solve(np.vstack([v.T, np.ones(4)]), np.append(xs, 1.0))
+        assert lam.min() >= -1e-12
+        Mk = abs(m.J[k]) * m.ref3.M
+        x = m.x[k]
+        for a in range(N + 1):
+            for b in range(N + 1 - a):
+                for c in range(N + 1 - a - b):
+                    q = x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** c
+                    assert abs(q @ Mk @ vec - xs[0] ** a * xs[1] ** b * xs[2] ** c) < 1e-10
+
+
+def test_ricker_integral_is_the_antiderivative_of_the_wavelet():
+    """Sec. 4.1 Ricker wavelet s(t) = (1 - 2 a) exp(-a), a = (pi f (t - t_s))^2,
+    and the source time function S = its antiderivative that vanishes far
+    from t_s: central differences of S give s, s(t_s) = 1, S(t_s) = 0, and
+    the wavelet has zero mean (S vanishes on both sides)."""
+    from oracle.solver import ricker, ricker_integral
+    f, ts, h = 2.5, 0.5, 1e-5
+    for t in np.linspace(0.0, 1.5, 31):
+        fd = (ricker_integral(t + h, f, ts) - ricker_integral(t - h, f, ts)) / (2 * h)
+        assert abs(fd - ricker(t, f, ts)) < 1e-8
+    assert ricker(ts, f, ts) == 1.0 and ricker_integral(ts, f, ts) == 0.0
+    tt = np.linspace(ts - 2.0, ts + 2.0, 400001)
+    s = np.array([ricker(t, f, ts) for t in tt])
+    assert abs(np.trapezoid(s, tt)) < 1e-9
+    assert abs(ricker_integral(ts - 2.0, f, ts)) < 1e-12 and abs(ricker_integral(ts + 2.0, f, ts)) < 1e-12
