@@ -414,3 +414,30 @@ def test_ricker_integral_is_the_antiderivative_of_the_wavelet():
     s = np.array([ricker(t, f, ts) for t in tt])
     assert abs(np.trapezoid(s, tt)) < 1e-9
     assert abs(ricker_integral(ts - 2.0, f, ts)) < 1e-12 and abs(ricker_integral(ts + 2.0, f, ts)) < 1e-12
+
+
+def test_energy_closed_forms():
+    """Sec. 4.1 energy E = sum_k int p^2 / (2 rho c^2) + rho |u|^2 / 2 with
+    the exact cell mass matrices: a constant state on three layers gives
+    sum_k vol_k (p0^2 / (2 rho_k c_k^2) + rho_k |u0|^2 / 2) with the volumes
+    from the vertices, and p = x (u = 0, rho = c = 1) on the jittered cube
+    [-1, 1]^3, which the cells still tile exactly, gives int x^2 / 2 = 4/3."""
+    N = 2
+    VX, EToV = W.kuhn_mesh(3, 1.0, 0.04, seed=92)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.0, 1.5, 2.0], [1.0, 1.2, 1.5])
+    m = CuboidMesh(VX, EToV, N, 0, [BC_HABC] * 6, rho, c)
+    o = Solver(m)
+    p0, u0 = 0.7, np.array([0.3, -0.4, 0.5])
+    Y = o.zero_state()
+    Y["q3"][:, 0] = p0
+    Y["q3"][:, 1:] = u0[None, :, None]
+    v = VX[EToV]
+    vol = np.abs(np.linalg.det(np.stack([v[:, 1] - v[:, 0], v[:, 2] - v[:, 0], v[:, 3] - v[:, 0]], axis=1))) / 6.0
+    assert abs(vol.sum() - 8.0) < 1e-12
+    E = np.sum(vol * (p0 ** 2 / (2 * rho * c ** 2) + rho * (u0 @ u0) / 2))
+    assert abs(o.energy(Y) - E) < 1e-12 * E
+    m1 = CuboidMesh(VX, EToV, N, 0, [BC_HABC] * 6, 1.0, 1.0)
+    o1 = Solver(m1)
+    Y = o1.zero_state()
+    Y["q3"][:, 0] = m1.x[..., 0]
+    assert abs(o1.energy(Y) - 4.0 / 3.0) < 1e-12
