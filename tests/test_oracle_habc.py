@@ -245,3 +245,56 @@ def test_edge_system_energy_rate_is_the_upwind_dissipation():
     assert jumps > 0
     assert abs(dE + diss) <= 1e-10 * diss
     assert abs(dE + diss1) > 1e-2 * diss
+
+
+def test_face_system_energy_rate_with_domain_edges():
+    """The same identity with fields on every triangle, p = 0 on two domain
+    faces and a random incoming characteristic r- (rm2) at the domain edges of
+    the HABC faces.  A domain edge then adds, per unit length,
+    - (p^2 / (2Z) + Z (v.n)^2 / 2) + r- (p - Z v.n) / Z on an HABC edge
+    (upwind with the exterior state built from r+ and r-), and - p^2 / Z on an
+    edge shared with a p = 0 face (mirror state).  This pins how the face
+    systems combine r+ and r- at domain edges (Sec. 2.3, Algorithm 1)."""
+    from oracle.mesh import BC_DIRICHLET, BC_HABC, CuboidMesh
+    from oracle.solver import Solver
+    from paper_1610_05023_b300 import workloads as W
+    VX, EToV = W.kuhn_mesh(3, 1.0, 0.03, seed=84)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.6, 2.0, 1.2], [1.5, 1.8, 2.5])
+    bc = (BC_DIRICHLET, BC_HABC, BC_HABC, BC_HABC, BC_HABC, BC_DIRICHLET)
+    m = CuboidMesh(VX, EToV, 3, 2, bc, rho, c)
+    o = Solver(m)
+    ref, T, P, Nfp = m.ref2, m.Ktri, m.P, m.ref2.Nfp
+    rng = np.random.default_rng(8)
+    q2 = rng.normal(size=(T, P, 3, ref.Np))
+    rm2 = rng.normal(size=(T, 3, P, Nfp))
+    rhs = o._rhs2(q2, q2[:, :, 0].copy(), rm2)
+    J, Z, w = np.abs(m.J2), m.rho2 * m.c2, 1.0 + o.cP
+    Mr = np.einsum("nk,tpfk->tpfn", ref.M, rhs)
+    dE = np.sum(J[:, None] * (w[None, :] / (m.rho2 * m.c2 ** 2)[:, None] * np.sum(q2[:, :, 0] * Mr[:, :, 0], axis=-1)
+                              + m.rho2[:, None] * np.sum(q2[:, :, 1:3] * Mr[:, :, 1:3], axis=(-1, -2))))
+    E = ref.M @ ref.LIFT
+    rate, kinds = 0.0, set()
+    for t in range(T):
+        for e in range(3):
+            own = ref.Fmask[e]
+            Ee = E[own][:, e * Nfp:(e + 1) * Nfp] * J[t] * m.Fscale2[t, e]
+            t2 = m.EToE2[t, e]
+            for a in range(P):
+                p = q2[t, a, 0, own]
+                vn = m.n2[t, e] @ q2[t, a, 1:3][:, own]
+                if t2 >= 0:
+                    nb = ref.Fmask[m.EToF2[t, e]][m.nbr_perm2[t, e]]
+                    jp = p - q2[t2, a, 0, nb]
+                    jv = vn - m.n2[t, e] @ q2[t2, a, 1:3][:, nb]
+                    rate -= 0.5 * (jp @ Ee @ jp + Z[t] * Z[t2] * (jv @ Ee @ jv)) / (Z[t] + Z[t2])
+                    kinds.add("interior")
+                elif m.bc[m.tri_edge_dom[t, e]] == BC_DIRICHLET:
+                    rate -= (p @ Ee @ p) / Z[t]
+                    kinds.add("p = 0")
+                else:
+                    r = rm2[t, e, a]
+                    rate -= (p @ Ee @ p) / (2 * Z[t]) + Z[t] * (vn @ Ee @ vn) / 2
+                    rate += (r @ Ee @ (p - Z[t] * vn)) / Z[t]
+                    kinds.add("HABC")
+    assert kinds == {"interior", "p = 0", "HABC"}
+    assert abs(dE - rate) <= 1e-10 * abs(rate)
