@@ -298,3 +298,51 @@ def test_face_system_energy_rate_with_domain_edges():
                     kinds.add("HABC")
     assert kinds == {"interior", "p = 0", "HABC"}
     assert abs(dE - rate) <= 1e-10 * abs(rate)
+
+
+def test_edge_system_energy_rate_with_corner_ends():
+    """The edge-system identity with fields on every line cell, p = 0 on two
+    domain faces and a random incoming characteristic r- (rm1) at the line
+    ends that reach a domain corner: an end at a corner whose third face has
+    the HABC adds - (p^2 / (2Z) + Z w^2 / 2) + r- (p - Z w) / Z (w: the
+    velocity along the outward tangent), an end whose third face is p = 0
+    adds - p^2 / Z.  Pins the edge systems' corner fluxes (Sec. 2.3)."""
+    from oracle.mesh import BC_DIRICHLET, BC_HABC, CuboidMesh
+    from oracle.solver import Solver
+    from paper_1610_05023_b300 import workloads as W
+    VX, EToV = W.kuhn_mesh(3, 1.0, 0.03, seed=85)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.6, 2.0, 1.2], [1.5, 1.8, 2.5])
+    bc = (BC_DIRICHLET, BC_HABC, BC_HABC, BC_HABC, BC_HABC, BC_DIRICHLET)
+    m = CuboidMesh(VX, EToV, 3, 2, bc, rho, c)
+    o = Solver(m)
+    ref, L, S, P = m.ref1, m.Klin, m.P ** 2, m.P
+    rng = np.random.default_rng(9)
+    q1 = rng.normal(size=(L, S, 2, ref.Np))
+    rm1 = rng.normal(size=(L, 2, S))
+    rhs = o._rhs1(q1, q1[:, :, 0].copy(), rm1)
+    J, Z = np.abs(m.J1), m.rho1 * m.c1
+    w = np.array([1.0 + o.cP[s % P] + o.cP[s // P] for s in range(S)])
+    Mr = np.einsum("nk,lsfk->lsfn", ref.M, rhs)
+    dE = np.sum(J[:, None] * (w[None, :] / (m.rho1 * m.c1 ** 2)[:, None] * np.sum(q1[:, :, 0] * Mr[:, :, 0], axis=-1)
+                              + m.rho1[:, None] * np.sum(q1[:, :, 1] * Mr[:, :, 1], axis=-1)))
+    end, tau = [0, ref.Np - 1], [-1.0, 1.0]
+    rate, kinds = 0.0, set()
+    for l in range(L):
+        for e in range(2):
+            p, wn = q1[l, :, 0, end[e]], tau[e] * q1[l, :, 1, end[e]]
+            l2 = m.EToE1[l, e]
+            if l2 >= 0:
+                n2 = end[m.EToF1[l, e]]
+                jp = p - q1[l2, :, 0, n2]
+                jv = wn - tau[e] * q1[l2, :, 1, n2]
+                rate -= 0.5 * np.sum(jp * jp + Z[l] * Z[l2] * jv * jv) / (Z[l] + Z[l2])
+                kinds.add("interior")
+            elif m.bc[m.lin_end_dom[l, e]] == BC_DIRICHLET:
+                rate -= np.sum(p * p) / Z[l]
+                kinds.add("p = 0")
+            else:
+                r = rm1[l, e]
+                rate -= np.sum(p * p / (2 * Z[l]) + Z[l] * wn * wn / 2) - np.sum(r * (p - Z[l] * wn)) / Z[l]
+                kinds.add("HABC")
+    assert kinds == {"interior", "p = 0", "HABC"}
+    assert abs(dE - rate) <= 1e-10 * abs(rate)
