@@ -441,3 +441,51 @@ def test_energy_closed_forms():
     Y = o1.zero_state()
     Y["q3"][:, 0] = m1.x[..., 0]
     assert abs(o1.energy(Y) - 4.0 / 3.0) < 1e-12
+
+
+def test_volume_energy_rate_with_boundary_faces():
+    """The 3D identity with fields on every cell, p = 0 on two domain faces
+    and a random incoming characteristic r- (rm3) on the others: a boundary
+    face adds - (p^2 / (2Z) + Z (u.n)^2 / 2) + r- (p - Z u.n) / Z (exterior
+    state 2 r-, 0: Sec. 2.2, eq. proc:faceBC) or, on a p = 0 face, - p^2 / Z
+    (mirror state, Sec. 2.4).  Pins how the 3D boundary fluxes use r-."""
+    from oracle.mesh import BC_DIRICHLET
+    VX, EToV = W.kuhn_mesh(3, 1.0, 0.03, seed=86)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.0, 1.5, 2.0], [1.0, 1.2, 1.5])
+    bc = (BC_DIRICHLET, BC_HABC, BC_HABC, BC_HABC, BC_HABC, BC_DIRICHLET)
+    m = CuboidMesh(VX, EToV, 3, 0, bc, rho, c)
+    o = Solver(m)
+    ref, K, Nfp = m.ref3, m.K, m.ref3.Nfp
+    rng = np.random.default_rng(10)
+    q3 = rng.normal(size=(K, 4, ref.Np))
+    rm3 = rng.normal(size=(len(m.bfaces), Nfp))
+    rhs = o._rhs3(q3, rm3, 0.0)
+    J, Z = np.abs(m.J), m.rho * m.c
+    Mr = np.einsum("nj,kfj->kfn", ref.M, rhs)
+    dE = np.sum(J * (np.sum(q3[:, 0] * Mr[:, 0], -1) / (m.rho * m.c ** 2)
+                     + m.rho * np.sum(q3[:, 1:] * Mr[:, 1:], axis=(-1, -2))))
+    E = ref.M @ ref.LIFT
+    rate, kinds = 0.0, set()
+    for k in range(K):
+        for f in range(4):
+            own = ref.Fmask[f]
+            Ef = E[own][:, f * Nfp:(f + 1) * Nfp] * J[k] * m.Fscale[k, f]
+            p, un = q3[k, 0, own], m.n[k, f] @ q3[k, 1:][:, own]
+            k2 = m.EToE[k, f]
+            if k2 >= 0:
+                nb = ref.Fmask[m.EToF[k, f]][m.nbr_perm[k, f]]
+                jp, ju = p - q3[k2, 0, nb], un - m.n[k, f] @ q3[k2, 1:][:, nb]
+                rate -= 0.5 * (jp @ Ef @ jp + Z[k] * Z[k2] * (ju @ Ef @ ju)) / (Z[k] + Z[k2])
+                kinds.add("interior")
+            else:
+                b = m.bface_index[k, f]
+                if m.bc[m.bface_dom[b]] == BC_DIRICHLET:
+                    rate -= (p @ Ef @ p) / Z[k]
+                    kinds.add("p = 0")
+                else:
+                    r = rm3[b]
+                    rate -= (p @ Ef @ p) / (2 * Z[k]) + Z[k] * (un @ Ef @ un) / 2
+                    rate += (r @ Ef @ (p - Z[k] * un)) / Z[k]
+                    kinds.add("HABC")
+    assert kinds == {"interior", "p = 0", "HABC"}
+    assert abs(dE - rate) <= 1e-10 * abs(rate)
