@@ -346,3 +346,34 @@ def test_edge_system_energy_rate_with_corner_ends():
                 kinds.add("HABC")
     assert kinds == {"interior", "p = 0", "HABC"}
     assert abs(dE - rate) <= 1e-10 * abs(rate)
+
+
+def test_face_boundary_algebra_closed_form():
+    """Face BC of Algorithm 1 (eqs. proc:faceBC, proc:pi00Star) in closed form:
+    with a 3D state of uniform p0 and u0 (so r+ = (p0 + Z n.u0)/2 on a face
+    with outward normal n) and uniform p*_a = k_a, every face node gets
+    r- = (1/M) sum_a c_a k_a with c_a = tan^2(a pi / M),
+    M = 2P + 1, q0 = r- + r+ and the full pressures p_a = k_a + q0."""
+    import math
+    from oracle.mesh import BC_HABC, CuboidMesh
+    from oracle.solver import Solver
+    from paper_1610_05023_b300 import workloads as W
+    P, rho, c = 3, 1.3, 0.9
+    VX, EToV = W.kuhn_mesh(2, 1.0, 0.03, seed=87)
+    m = CuboidMesh(VX, EToV, 2, P, [BC_HABC] * 6, rho, c)
+    o = Solver(m)
+    Y = o.zero_state()
+    p0, u0 = 0.4, np.array([0.3, -0.2, 0.6])
+    Y["q3"][:, 0] = p0
+    Y["q3"][:, 1:] = u0[None, :, None]
+    k = np.array([0.5, -1.0, 2.0])
+    Y["q2"][:, :, 0] = k[None, :, None]
+    cl = o.closure(Y)
+    M = 2 * P + 1
+    ca = np.array([math.tan(a * math.pi / M) ** 2 for a in range(1, P + 1)])
+    rm = np.sum(ca * k) / M
+    d = m.tri_d
+    rp = (p0 + rho * c * np.where(d % 2 == 1, 1.0, -1.0) * u0[d // 2]) / 2.0     # per triangle
+    assert np.abs(cl["rm3"][m.tri_bface] - rm).max() < 1e-13
+    q0 = rm + rp
+    assert np.abs(cl["p2"] - (k[None, :, None] + q0[:, None, None])).max() < 1e-13
