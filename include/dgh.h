@@ -77,11 +77,20 @@ extern "C" {
 /* Arithmetic of the 3D volume / lift contractions (the products
  * D_j x and LIFT x of eq. dgLocalRhs); everything else (fluxes, update,
  * 2D/1D/0D levels) is FP32 in every mode.  The tensor-core modes run the
- * products on tcgen05 tensor cores with FP32 accumulation in tensor memory. */
-#define DGH_PREC_FP32        0   /* FP32 CUDA cores (the plain path)              */
+ * products on tcgen05 tensor cores with FP32 accumulation in tensor memory.
+ * DGH_PREC_FP32 is the plain path held to the FP32 contract (relative L2
+ * error <= 1e-5 per field against the FP64 oracle): for N <= 4 it runs the
+ * split-TF32 tensor-core kernel (each operand to 2^-22, three products, a
+ * few units of FP32 rounding), for N >= 5 the FP32 CUDA-core kernel.
+ * DGH_PREC_FP32_CUDA forces the CUDA-core kernel at every order (packed
+ * FP32 FMAs, no tensor cores); DGH_PREC_SPLIT_TF32 forces the split-TF32
+ * kernel (N <= 4 only: DGH_EUNSUPPORTED otherwise). */
+#define DGH_PREC_FP32        0   /* FP32 contract: split TF32 (N <= 4), else CUDA cores */
 #define DGH_PREC_BF16_TC     1   /* BF16 operands, one product                    */
 #define DGH_PREC_FP16_TC     2   /* FP16 operands, one product                    */
 #define DGH_PREC_SPLIT_BF16  3   /* x = hi + lo in BF16, hi*hi + lo*hi + hi*lo    */
+#define DGH_PREC_FP32_CUDA   4   /* FP32 CUDA cores at every order (the fallback)  */
+#define DGH_PREC_SPLIT_TF32  5   /* x = hi + lo in TF32, hi*hi + lo*hi + hi*lo (N <= 4) */
 
 typedef struct dgh_ctx dgh_ctx;
 
@@ -223,7 +232,9 @@ int dgh_is_checked_build(void);
 
 /* Discrete energy of the 3D fields,
  * E = sum_k |J_k| [p^T M p / (2 rho c^2) + (rho/2) sum_i u_i^T M u_i],
- * reduced on the GPU with FP64 accumulation (synchronising). */
+ * (Sec. 4.1, energy of the pressure-velocity system) reduced on the GPU in
+ * FP64 throughout: the FP32 fields are widened, M is the FP64 mass matrix
+ * and every product and sum is FP64 (synchronising). */
 int dgh_get_energy(dgh_ctx *ctx, double *E);
 
 /* Error reduction (Error(t)^2 = E(q - ref) / E_ref of the paper's accuracy
@@ -237,17 +248,22 @@ int dgh_get_error_energy(dgh_ctx *ctx, const double *ref, size_t count, double *
  * per-block partial sums live in a fixed static device array of the library
  * (65,536 doubles = 512 KiB, held on every GPU that loads the library until
  * the process exits).  Meant for callers that cannot allocate device memory
- * when they need the value -- code running while a CUDA graph is being
- * captured, where cudaMalloc is not allowed, or code inside a framework whose
- * memory pool owns the whole device.  The paper has no counterpart; it is a
- * service of this library.
+ * when they need the value: code inside a framework whose memory pool owns
+ * the whole device, or a monitoring loop on a latency-critical path where
+ * cudaMalloc's implicit device synchronisation is not acceptable.  The paper
+ * has no counterpart; it is a service of this library.
  *  d_energy: DEVICE pointer to one double, owned by the caller, written on
  *            `stream` (NULL = the context's stream); asynchronous, read it
  *            after synchronising that stream.
+ *  Ordering: when `stream` is not the context's stream, the call first makes
+ *            `stream` wait (event record + stream wait) for all work enqueued
+ *            on the context's stream so far, so the energy is that of the
+ *            fields after the last dgh_step.
  *  Limit: at most 4,194,304 cells (65,536 partial sums of 256 (cell, field)
  *         items); larger contexts get DGH_EINVAL with a message.
+ *  Arithmetic: FP64 throughout (FP64 mass matrix, FP64 sums), as dgh_get_energy.
  *  The first call on each device looks up the array's device address with
- *  cudaGetSymbolAddress; make that first call outside any stream capture.
+ *  cudaGetSymbolAddress, once per device.
  *  All calls share the one array (every partial sum is rewritten by each
  *  call, nothing needs clearing), so calls whose kernels overlap on the GPU
  *  -- e.g. on two streams at once -- race and must be serialised. */

@@ -22,6 +22,8 @@ PREC_FP32 = 0
 PREC_BF16_TC = 1
 PREC_FP16_TC = 2
 PREC_SPLIT_BF16 = 3
+PREC_FP32_CUDA = 4     # FP32 CUDA-core contractions at every order
+PREC_SPLIT_TF32 = 5    # split-TF32 tensor-core contractions (N <= 4)
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ETIMEOUT", -6: "ESTATE",
            -7: "EUNSUPPORTED", -8: "EBOUNDS"}
@@ -302,8 +304,11 @@ class Solver:
     BC_DIRICHLET for -x,+x,-y,+y,-z,+z), c and rho per cell (or scalars),
     dt > 0 fixed step (else cfl * the min-over-cells rule), stream a
     torch.cuda.Stream, an integer cudaStream_t or None, precision one of
-    PREC_FP32 (CUDA cores), PREC_BF16_TC, PREC_FP16_TC, PREC_SPLIT_BF16
-    (tensor-core products of the 3D volume and lift terms).
+    PREC_FP32 (the FP32 contract: split-TF32 tensor-core products for
+    N <= 4, FP32 CUDA cores above), PREC_FP32_CUDA (FP32 CUDA cores at every
+    order), PREC_SPLIT_TF32 (split TF32, N <= 4), PREC_BF16_TC,
+    PREC_FP16_TC, PREC_SPLIT_BF16 (the precision form's tensor-core products
+    of the 3D volume and lift terms).
     """
 
     def __init__(self, VX, EToV, N, P, bc=(BC_HABC,) * 6, c=1.0, rho=1.0, dt=0.0, cfl=1.0, stream=None,
@@ -472,7 +477,9 @@ class Solver:
 
     def energy_noalloc(self, d_out, stream=None):
         """Energy written to the device double at address d_out (an int), with no
-        allocation inside the call (see dgh_get_energy_noalloc); asynchronous."""
+        allocation inside the call (see dgh_get_energy_noalloc); asynchronous.
+        A stream other than the solver's is first made to wait for the work
+        already enqueued on the solver's stream."""
         sptr = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
         self._check(self._lib.dgh_get_energy_noalloc(self._h, ctypes.c_void_p(d_out),
                                                      ctypes.c_void_p(sptr) if sptr else None))

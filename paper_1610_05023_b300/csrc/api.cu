@@ -89,6 +89,7 @@ struct dgh_ctx {
     int *can2dev_d = nullptr;         // the same map on the device (state transfers)
     cudaStream_t side = nullptr;      // HABC chain stream (overlaps the interior 3D work)
     cudaEvent_t ev3d[5] = {}, ev2d[5] = {}, evjoin = nullptr;
+    cudaEvent_t ev_order = nullptr;   // orders a caller's stream after the context's work (no-allocation energy)
     int C = 0;
     int M = 1;
     double dt = 0.0, t0 = 0.0;
@@ -346,6 +347,60 @@ int tc_code(int precision) {
     return precision == DGH_PREC_BF16_TC ? TC_BF16 : precision == DGH_PREC_FP16_TC ? TC_FP16 : TC_SPLIT_BF16;
 }
 
+// Which 3D kernel a context runs: the split-TF32 tensor-core kernel
+// (DGH_PREC_FP32 up to N = 4, DGH_PREC_SPLIT_TF32), the BF16/FP16
+// tensor-core kernel (the precision form) or the FP32 CUDA-core kernel.
+enum Kern3 { K3_CUDA = 0, K3_TF32 = 1, K3_TC = 2 };
+constexpr int kMaxTf32Order = 4;   // largest N whose operators and stage fit one CTA's shared memory
+int kern3_of(int precision, int N) {
+    if (precision == DGH_PREC_SPLIT_TF32) return K3_TF32;
+    if (precision == DGH_PREC_FP32) return N <= kMaxTf32Order ? K3_TF32 : K3_CUDA;
+    if (precision == DGH_PREC_FP32_CUDA) return K3_CUDA;
+    return K3_TC;
+}
+
+// Round to the nearest TF32 value (13 low bits of the FP32 significand
+// cleared, ties to even); finite inputs.
+float tf32_round(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    u &= 0xFFFFE000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
+// Operator images of the split-TF32 kernel: B operands with rows = output
+// nodes, K-major canonical layout without swizzle (8-row x 16-byte core
+// matrices of 4 TF32 values; element (n, k) of a matrix with R rows at byte
+// (k/4)(R/8)128 + (n/8)128 + (n%8)16 + (k%4)4), zero padding.
+//   [D_r; D_s; D_t]: 3 NPAD rows x KV (D_j in rows j NPAD .. j NPAD + Np - 1)
+//   LIFT: NPAD rows x 4 FK (face f's nodes at K = f FK + m)
+// hi = TF32 rounding of the FP64 entry, lo = TF32 rounding of the rest; the
+// hi image is followed by the lo image.
+std::vector<uint8_t> tf32_operator_images(const RefTet &T3) {
+    const int Np = T3.Np, Nfp = T3.Nfp;
+    const int NPAD = (Np + 15) / 16 * 16, KV = (Np + 7) / 8 * 8, FK = (Nfp + 7) / 8 * 8;
+    const size_t BD = size_t(3) * NPAD * KV * 4, BL = size_t(NPAD) * 4 * FK * 4, BOPS = BD + BL;
+    std::vector<uint8_t> img(2 * BOPS, 0);
+    auto put = [&](size_t base, int R, int n, int k, double x) {
+        const size_t off = base + size_t(k / 4) * (R / 8) * 128 + size_t(n / 8) * 128 + (n % 8) * 16 + (k % 4) * 4;
+        const float hi = tf32_round(float(x));
+        const float lo = tf32_round(float(x - double(hi)));
+        std::memcpy(&img[off], &hi, 4);
+        std::memcpy(&img[BOPS + off], &lo, 4);
+    };
+    const Mat *Dj[3] = {&T3.Dr, &T3.Ds, &T3.Dt};
+    for (int j = 0; j < 3; ++j)
+        for (int n = 0; n < Np; ++n)
+            for (int k = 0; k < Np; ++k) put(0, 3 * NPAD, j * NPAD + n, k, (*Dj[j])(n, k));
+    for (int n = 0; n < Np; ++n)
+        for (int f = 0; f < 4; ++f)
+            for (int m = 0; m < Nfp; ++m) put(BD, NPAD, n, f * FK + m, T3.LIFT(n, f * Nfp + m));
+    return img;
+}
+
 // Operator images of the tensor-core kernel: the B operands D_r, D_s, D_t
 // (NPAD x NPAD) and LIFT (NPAD x 4 FPAD, face f's nodes at K = f FPAD + m),
 // rows = output nodes, in the K-major canonical layout without swizzle:
@@ -410,7 +465,17 @@ struct Launch3 {
         const int64_t nblk = A.blk_end - A.blk_begin;
         if (nblk <= 0) return DGH_OK;
         A.max_tiles = int(std::min<int64_t>(nblk, int64_t(1) << 30));
-        if (c->precision != DGH_PREC_FP32) {   // tensor-core kernel: tiles of four 32-cell blocks
+        const int kern = kern3_of(c->precision, N);
+        if (kern == K3_TF32) {   // split-TF32 tensor-core kernel: tiles of four 32-cell blocks, one CTA per SM
+            if constexpr (N <= kMaxTf32Order) {
+                const int grid = (int)std::min<int64_t>((nblk + 3) / 4, c->grid3);
+                k3d_tf32<N><<<grid, CfgTF<N>::NTHR, CfgTF<N>::SMEM, st>>>(A, sc, c->tcops);
+                return DGH_OK;
+            } else {
+                return DGH_EUNSUPPORTED;
+            }
+        }
+        if (kern == K3_TC) {   // tensor-core kernel: tiles of four 32-cell blocks
             const int grid = (int)std::min<int64_t>((nblk + 3) / 4, c->grid3);
             switch (tc_code(c->precision)) {
                 case TC_BF16: k3d_tc<N, TC_BF16><<<grid, 256, CfgTC<N, TC_BF16>::SMEM, st>>>(A, sc, c->tcops); break;
@@ -545,8 +610,17 @@ struct SetAttrs {
         cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         c->smem_optin = optin;
         int nb = 0;
-        if (c->precision == DGH_PREC_FP32) {
+        const int kern = kern3_of(c->precision, N);
+        if (kern == K3_CUDA) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N>, Cfg3<N>::NW * 32, c->smem3);
+        } else if (kern == K3_TF32) {
+            if constexpr (N <= kMaxTf32Order) {
+                // one CTA per SM: it owns all 512 tensor-memory columns
+                cudaFuncSetAttribute(k3d_tf32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CfgTF<N>::SMEM);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_tf32<N>, CfgTF<N>::NTHR, CfgTF<N>::SMEM);
+                nb = std::min(nb, 1);
+                c->smem3 = CfgTF<N>::SMEM;
+            }
         } else {
             // one CTA owns TCOLS tensor-memory columns (512 per SM)
             auto occ = [&](auto kern, size_t smem, int tcols) {
@@ -584,7 +658,7 @@ struct Shapes {
         if (P && c->tile2 * P > c->thr2) return DGH_EINVAL;   // one thread per (triangle, set)
         const int sms = c->sms;
         const int per_sm = c->cta3_per_sm > 0 ? std::min(c->cta3_per_sm, std::max(c->occ3, 1)) : std::max(c->occ3, 1);
-        const int64_t tiles3 = c->precision == DGH_PREC_FP32 ? c->K32 : (c->K32 + 3) / 4;
+        const int64_t tiles3 = kern3_of(c->precision, N) == K3_CUDA ? c->K32 : (c->K32 + 3) / 4;
         c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)per_sm * sms));
         int nb2 = 0, nb1 = 0;
         if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, c->thr2, c->smem2);
@@ -820,6 +894,17 @@ __global__ void __launch_bounds__(256) k_energy_diff_partial(const float *q, con
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// Energy partial sums of the 3D fields (FP64 throughout), nb blocks on st.
+template <int N>
+struct EnergyPartial {
+    static int run(const float *q, const double *Md, const double *ew, int64_t K, double *partial, int nb, cudaStream_t st) {
+        const size_t smem = energy_smem(N);
+        cudaFuncSetAttribute(k_energy_partial<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_energy_partial<N><<<nb, 256, smem, st>>>(q, Md, ew, K, partial);
+        return DGH_OK;
+    }
+};
+
 template <int N>
 struct EnergyDiff {
     static int run(dgh_ctx *c, const double *dref) {
@@ -847,6 +932,7 @@ void dgh_destroy(dgh_ctx *ctx) {
         if (ctx->ev2d[i]) cudaEventDestroy(ctx->ev2d[i]);
     }
     if (ctx->evjoin) cudaEventDestroy(ctx->evjoin);
+    if (ctx->ev_order) cudaEventDestroy(ctx->ev_order);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     for (auto &b : ctx->bufs) cudaFree(b.p);
     delete ctx->sh;
@@ -863,8 +949,12 @@ static int validate_desc(const dgh_desc *d) {
         return DGH_EUNSUPPORTED;
     }
     if (d->precision != DGH_PREC_FP32 && d->precision != DGH_PREC_BF16_TC && d->precision != DGH_PREC_FP16_TC &&
-        d->precision != DGH_PREC_SPLIT_BF16) {
+        d->precision != DGH_PREC_SPLIT_BF16 && d->precision != DGH_PREC_FP32_CUDA && d->precision != DGH_PREC_SPLIT_TF32) {
         g_create_error = "unknown precision code";
+        return DGH_EUNSUPPORTED;
+    }
+    if (d->precision == DGH_PREC_SPLIT_TF32 && d->order > kMaxTf32Order) {
+        g_create_error = "split-TF32 products are built for N <= 4 (operators and stage exceed shared memory above)";
         return DGH_EUNSUPPORTED;
     }
     if (d->n_cells > (int64_t(1) << 26)) {
@@ -1102,8 +1192,9 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
             (rc = upload(ctx, ctx->fperm3, fperm)) || (rc = upload(ctx, ctx->nslot3, nslot)) ||
             (rc = upload(ctx, ctx->cellv, cellv)) || (rc = upload(ctx, ctx->rst, rst)) || (rc = upload(ctx, ctx->ew, ew)))
             return fail(rc, "");
-        if (ctx->precision != DGH_PREC_FP32 && (rc = upload(ctx, ctx->tcops, tc_operator_images(T3, ctx->precision))))
-            return fail(rc, "");
+        const int kern = kern3_of(ctx->precision, N);
+        if (kern == K3_TC && (rc = upload(ctx, ctx->tcops, tc_operator_images(T3, ctx->precision)))) return fail(rc, "");
+        if (kern == K3_TF32 && (rc = upload(ctx, ctx->tcops, tf32_operator_images(T3)))) return fail(rc, "");
         std::vector<int> c2d(ctx->can2dev.begin(), ctx->can2dev.end());
         if ((rc = upload(ctx, ctx->can2dev_d, c2d)) || (rc = upload(ctx, ctx->M3d, T3.M.a))) return fail(rc, "");
     }
@@ -1259,7 +1350,9 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
         if (cudaEventCreateWithFlags(&ctx->ev3d[i], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev2d[i], cudaEventDisableTiming) != cudaSuccess)
             return fail(DGH_ECUDA, "events");
-    if (cudaEventCreateWithFlags(&ctx->evjoin, cudaEventDisableTiming) != cudaSuccess) return fail(DGH_ECUDA, "events");
+    if (cudaEventCreateWithFlags(&ctx->evjoin, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_order, cudaEventDisableTiming) != cudaSuccess)
+        return fail(DGH_ECUDA, "events");
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(DGH_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
@@ -1775,14 +1868,8 @@ int dgh_get_energy(dgh_ctx *ctx, double *E) {
     return dgh_guarded(err_slot(ctx), [&]() -> int {
         if (!ctx || !E) return DGH_EINVAL;
         const int nb = ctx->energy_blocks;
-        switch (ctx->N) {
-            case 1: k_energy_partial<1><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-            case 2: k_energy_partial<2><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-            case 3: k_energy_partial<3><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-            case 4: k_energy_partial<4><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-            case 5: k_energy_partial<5><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-            case 6: k_energy_partial<6><<<nb, 256, 0, ctx->stream>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, ctx->partial); break;
-        }
+        dispatchN<EnergyPartial>(ctx->N, (const float *)ctx->q3, (const double *)ctx->M3d, (const double *)ctx->ew,
+                                 ctx->K32 * 32, ctx->partial, nb, ctx->stream);
         k_sum_partials<<<1, 256, 0, ctx->stream>>>(ctx->partial, nb, ctx->d_energy);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(E, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -2498,14 +2585,7 @@ int dgh_batch_get_energy(dgh_batch *b, int i, double *E) {
         const double *ew = u->ew + blk0 * 32 * 2;
         const int nb = u->energy_blocks;
         cudaStream_t st = u->stream;
-        switch (u->N) {
-            case 1: k_energy_partial<1><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-            case 2: k_energy_partial<2><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-            case 3: k_energy_partial<3><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-            case 4: k_energy_partial<4><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-            case 5: k_energy_partial<5><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-            case 6: k_energy_partial<6><<<nb, 256, 0, st>>>(q, u->M3, ew, nblk * 32, u->partial); break;
-        }
+        dispatchN<EnergyPartial>(u->N, q, (const double *)u->M3d, ew, nblk * 32, u->partial, nb, st);
         k_sum_partials<<<1, 256, 0, st>>>(u->partial, nb, u->d_energy);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(E, u->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -2992,13 +3072,13 @@ extern "C" {
 // Energy without any device allocation.
 //
 // Some callers cannot allocate device memory at the moment they want the
-// energy: code that runs while a CUDA graph is being captured (cudaMalloc is
-// not allowed inside a capture), or code embedded in a host framework whose
-// memory pool owns the whole device and forbids allocations outside it.  This
-// entry point therefore keeps its per-block partial sums in a fixed
-// file-scope device array instead of allocating them.  The array is
-// kNoAllocMaxPartials doubles (512 KiB) and stays resident on every GPU that
-// loads the library until the process exits.
+// energy: code embedded in a host framework whose memory pool owns the whole
+// device and forbids allocations outside it, or a monitoring loop on a
+// latency-critical path where cudaMalloc's implicit device synchronisation is
+// not acceptable.  This entry point therefore keeps its per-block partial
+// sums in a fixed file-scope device array instead of allocating them.  The
+// array is kNoAllocMaxPartials doubles (512 KiB) and stays resident on every
+// GPU that loads the library until the process exits.
 namespace {
 
 constexpr int64_t kNoAllocMaxPartials = 65536;
@@ -3032,13 +3112,15 @@ int noalloc_scratch(dgh_ctx *ctx, double **out) {
 }
 
 // One block per kNoAllocBlock (cell, field) items; block b writes partial[b].
+// FP64 throughout, as k_energy_partial: widened fields, FP64 mass matrix
+// (dynamic shared memory), FP64 sums.
 template <int N>
-__global__ void __launch_bounds__(kNoAllocBlock) k_energy_partial_fixed(const float *q, const float *Mref, const double *ew,
+__global__ void __launch_bounds__(kNoAllocBlock) k_energy_partial_fixed(const float *q, const double *Md, const double *ew,
                                                                         int64_t K, double *partial) {
     constexpr int NP = Ord<N>::NP;
-    __shared__ float sM[NP * NP];
+    extern __shared__ double sMf[];
     __shared__ double red[kNoAllocBlock];
-    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sM[i] = Mref[i];
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sMf[i] = Md[i];
     __syncthreads();
     const int64_t it = blockIdx.x * (int64_t)kNoAllocBlock + threadIdx.x;
     double acc = 0.0;
@@ -3047,9 +3129,9 @@ __global__ void __launch_bounds__(kNoAllocBlock) k_energy_partial_fixed(const fl
         const int fl = (int)(it % 4);
         const float *x = q + (k / 32) * (4 * NP * 32) + fl * NP * 32 + (k % 32);
         for (int n = 0; n < NP; ++n) {
-            float y = 0.f;
-            for (int m = 0; m < NP; ++m) y += sM[n * NP + m] * x[m * 32];
-            acc += (double)x[n * 32] * (double)y;
+            double y = 0.0;
+            for (int m = 0; m < NP; ++m) y += sMf[n * NP + m] * (double)x[m * 32];
+            acc += (double)x[n * 32] * y;
         }
         acc *= ew[2 * k + (fl == 0 ? 0 : 1)];
     }
@@ -3061,6 +3143,16 @@ __global__ void __launch_bounds__(kNoAllocBlock) k_energy_partial_fixed(const fl
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
+
+template <int N>
+struct EnergyFixed {
+    static int run(dgh_ctx *ctx, double *scratch, int nb, cudaStream_t s) {
+        const size_t smem = energy_smem(N);
+        cudaFuncSetAttribute(k_energy_partial_fixed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_energy_partial_fixed<N><<<nb, kNoAllocBlock, smem, s>>>(ctx->q3, ctx->M3d, ctx->ew, ctx->K32 * 32, scratch);
+        return DGH_OK;
+    }
+};
 
 }  // namespace
 
@@ -3078,15 +3170,12 @@ extern "C" int dgh_get_energy_noalloc(dgh_ctx *ctx, double *d_energy, void *stre
         int rc = noalloc_scratch(ctx, &scratch);
         if (rc) return rc;
         cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
-        const int nb = (int)nblocks;
-        switch (ctx->N) {
-            case 1: k_energy_partial_fixed<1><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-            case 2: k_energy_partial_fixed<2><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-            case 3: k_energy_partial_fixed<3><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-            case 4: k_energy_partial_fixed<4><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-            case 5: k_energy_partial_fixed<5><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
-            case 6: k_energy_partial_fixed<6><<<nb, kNoAllocBlock, 0, s>>>(ctx->q3, ctx->M3, ctx->ew, ctx->K32 * 32, scratch); break;
+        if (s != ctx->stream) {   // the fields are written on the context's stream: read them after that work
+            CK(cudaEventRecord(ctx->ev_order, ctx->stream));
+            CK(cudaStreamWaitEvent(s, ctx->ev_order, 0));
         }
+        const int nb = (int)nblocks;
+        dispatchN<EnergyFixed>(ctx->N, ctx, scratch, nb, s);
         k_sum_partials<<<1, 256, 0, s>>>(scratch, nb, d_energy);
         CK(cudaGetLastError());
         return DGH_OK;

@@ -133,6 +133,7 @@ __device__ __forceinline__ double ricker_integral_d(double t, double f, double t
 }  // namespace dgh
 #include "k3d.cuh"
 #include "k3d_tc.cuh"
+#include "k3d_tf32.cuh"
 #include "closure.cuh"
 namespace dgh {
 
@@ -700,14 +701,17 @@ __global__ void k_init_gaussian(float *q, const double *cellv, const double *rst
     qk[(3 * NP + n) * 32] = 0.f;
 }
 
-// Energy: per cell |J| [p^T M p /(2 rho c^2) + rho/2 sum u^T M u], FP64 accumulation.
+// Energy: per cell |J| [p^T M p /(2 rho c^2) + rho/2 sum u^T M u] (Sec. 4.1,
+// energy of the pressure-velocity system), all in FP64: the FP32 fields are
+// widened, the mass-matrix product uses the FP64 mass matrix Md (dynamic
+// shared memory, NP*NP doubles) and the sums are FP64.
 template <int N>
-__global__ void __launch_bounds__(256) k_energy_partial(const float *q, const float *Mref, const double *ew, int64_t K,
+__global__ void __launch_bounds__(256) k_energy_partial(const float *q, const double *Md, const double *ew, int64_t K,
                                                         double *partial) {
     constexpr int NP = Ord<N>::NP;
-    __shared__ float sM[NP * NP];
+    extern __shared__ double sMe[];
     __shared__ double red[256];
-    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sM[i] = Mref[i];
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sMe[i] = Md[i];
     __syncthreads();
     double acc = 0.0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < K * 4; it += (int64_t)gridDim.x * blockDim.x) {
@@ -716,9 +720,9 @@ __global__ void __launch_bounds__(256) k_energy_partial(const float *q, const fl
         const float *x = q + (k / 32) * (4 * NP * 32) + fl * NP * 32 + (k % 32);   // stride 32 between nodes
         double s = 0.0;
         for (int n = 0; n < NP; ++n) {
-            float y = 0.f;
-            for (int m = 0; m < NP; ++m) y += sM[n * NP + m] * x[m * 32];
-            s += (double)x[n * 32] * (double)y;
+            double y = 0.0;
+            for (int m = 0; m < NP; ++m) y += sMe[n * NP + m] * (double)x[m * 32];
+            s += (double)x[n * 32] * y;
         }
         acc += s * ew[2 * k + (fl == 0 ? 0 : 1)];
     }
@@ -729,6 +733,12 @@ __global__ void __launch_bounds__(256) k_energy_partial(const float *q, const fl
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// Dynamic shared memory of the energy kernels (the FP64 mass matrix).
+inline size_t energy_smem(int N) {
+    const int np = (N + 1) * (N + 2) * (N + 3) / 6;
+    return sizeof(double) * np * np;
 }
 
 __global__ void k_sum_partials(const double *partial, int n, double *out) {

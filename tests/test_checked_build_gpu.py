@@ -28,6 +28,8 @@ CASES = [
     (2, 6, 4, (0,) * 6, 0),
     (2, 3, 12, (0,) * 6, 0),
     (2, 4, 2, (0,) * 6, dgh.PREC_SPLIT_BF16),
+    (2, 3, 2, (1, 0, 0, 1, 0, 1), dgh.PREC_FP32_CUDA),
+    (3, 4, 6, (0,) * 6, dgh.PREC_FP32_CUDA),
 ]
 
 
