@@ -21,26 +21,29 @@
 // correction; the tensor core truncates the 13 low bits of its FP32
 // inputs, so hi and lo are rounded explicitly before they reach it).
 //
-// B300 design: one persistent CTA per SM, 14 warps in four roles.
+// B300 design: one persistent CTA per SM, 18 warps in four roles.
 //   warp 0     producer: claims tiles, prefetches the next tile into L2,
 //              TMA bulk-copies the tile's q and geometry into one of two
 //              shared-memory stages (a stage is held until the converters and
 //              the epilogue of its tile are done with it);
 //   warp 1     MMA issuer (one thread) and tensor-memory owner;
-//   warps 2-5  converters (thread = cell): flux differences (incoming
-//              traces read from L2 one slab ahead), contravariant fluxes,
-//              hi/lo split; the A operands go straight into tensor memory
-//              (tcgen05.st) in a ring of four 32-column slabs, so no
-//              shared-memory bandwidth is spent on them.  The store of slab
-//              s completes while slab s + 1 is computed;
-//   warps 6-13 epilogue, two warps per 32-cell block (thread = cell, each
+//   warps 2-9  converters, two warps per 32-cell block taking alternate
+//              slabs (thread = cell): flux differences (incoming traces read
+//              from L2 one slab ahead), contravariant fluxes, hi/lo split;
+//              the A operands go straight into tensor memory (tcgen05.st) in
+//              a ring of four 32-column slabs, so no shared-memory bandwidth
+//              is spent on them.  The store of a slab completes while the
+//              warp computes its next one;
+//   warps 10-17 epilogue, two warps per 32-cell block (thread = cell, each
 //              warp every other 4-node chunk): accumulators (tcgen05.ld) and
 //              the old state (from the stage) -> right-hand sides, LSERK
 //              update (res read from L2 one chunk ahead), then the trace
 //              pushes of the chunk face by face.
-// The per-thread state is kept small enough for 128 registers without
-// spills: with most of the SM's memory given to shared memory, a spilled
-// register would be reloaded from L2.
+// The work per cell is latency-bound, so the roles get as many warps as
+// the register file allows (18 warps: 96 registers each, as four
+// sub-partitions hold at most five warps of 96); the per-thread state is
+// kept small enough for that without spills (with most of the SM's memory
+// given to shared memory, a spilled register would be reloaded from L2).
 // An M = 128 tcgen05.mma costs about the same issue time for any N up to
 // 256 on this part, so products are grouped into as few instructions as
 // the accumulator layout allows (P D_j^T for all three j in one N = 3 NPAD
@@ -88,7 +91,8 @@ struct CfgTF {
     static constexpr int RING_COL = 2 * ACC;
     static_assert(RING_COL + 32 * 4 <= 512, "tensor memory");
     static_assert(RD <= 256 && NPAD % 16 == 0, "MMA N");
-    static constexpr int NTHR = 448;   // 14 warps
+    static constexpr int NTHR = 576;   // 18 warps
+    static constexpr int NCONV = 8;    // converter warps (two per 32-cell block)
     static constexpr int NEPI = 8;     // epilogue warps (two per 32-cell block)
     // kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128
     __host__ __device__ static constexpr uint32_t idesc(int n) {
@@ -115,6 +119,13 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float (&v)[2]) {
+    uint32_t r[2];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+    v[0] = __uint_as_float(r[0]);
+    v[1] = __uint_as_float(r[1]);
+}
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
     uint32_t r[4];
@@ -203,7 +214,7 @@ __device__ __forceinline__ void tf_load_tin(const float2 *__restrict__ tb, int k
 }
 
 template <int N>
-__global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const uint8_t *ops) {
+__global__ void __launch_bounds__(576, 1) k3d_tf32(Args3 A, StageCoef sc, const uint8_t *ops) {
     using G = CfgTF<N>;
     constexpr int NP = G::NP, NFP = G::NFP, NF = G::NF, NPAD = G::NPAD, QS = G::QS, TI = G::TI, GS = G::GS, CS = G::CS;
     extern __shared__ __align__(16) unsigned char sm_tf[];
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
     if (tid == 0) {
         for (int st = 0; st < 2; ++st) {
             mbar_init(&stage_full[st], 1);
-            mbar_init(&stage_empty[st], 128 + 32 * G::NEPI);   // converters and epilogue
+            mbar_init(&stage_empty[st], 32 * (G::NCONV + G::NEPI));   // converters and epilogue
             mbar_init(&acc_full[st], 2);      // the products' commit + the issuing thread's release
             mbar_init(&acc_empty[st], 32 * G::NEPI);
         }
@@ -272,13 +283,14 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
             auto claim = [&](int i) -> int64_t {
                 return i < A.max_tiles ? (int64_t)atomicAdd(A.tile_ctr, 1ull) : ntiles;
             };
+            // what the next stage copy reads; the incoming traces and res are
+            // prefetched by the converters, closer to their use (a prefetch a
+            // whole tile ahead is often evicted from L2 before it is read)
             auto prefetch = [&](int64_t t) {
                 for (int b = 0; b < 4; ++b) {
                     const int64_t gb = A.blk_begin + 4 * t + b;
                     if (gb >= A.blk_end) break;
                     prefetch_l2(A.q + gb * QS, QS * 4);
-                    prefetch_l2(A.res + gb * QS, QS * 4);
-                    prefetch_l2(A.tin + gb * TI, TI * 4);
                     prefetch_l2(A.geo + gb * GS, GS * 4);
                     prefetch_l2(A.conn + gb * CS, CS * 4);
                 }
@@ -381,19 +393,21 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
                 mbar_arrive(&acc_full[a]);
             }
         }
-    } else if (w < 6) {
+    } else if (w < 2 + G::NCONV) {
         // ------------------------------------------------------------ converters
-        const int b = w & 3;
+        const int b = w & 3, hc = (w - 2) >> 2;   // 32-cell block; this warp's slabs are those of parity hc
         const uint32_t trow = tbase + ((uint32_t)(32 * b) << 16);
-        uint32_t rc = 0;   // slabs produced
         for (int i = 0;; ++i) {
             const int st = i & 1;
             if (!tf_wait(&stage_full[st], (i >> 1) & 1, A.err, s_abort)) break;
             const int64_t t = s_tiles[i & 7];
-            if (t >= ntiles) {   // end: one empty slab tells the MMA issuer
-                const int slot = rc & 3;
-                if (rc >= 4 && !tf_wait(&ring_empty[slot], ((rc >> 2) + 1) & 1, A.err, s_abort)) break;
-                mbar_arrive(&ring_full[slot]);
+            uint32_t rc = (uint32_t)i * G::NSLAB + hc;   // ring position of this warp's first slab of the tile
+            if (t >= ntiles) {   // end: one empty slab (the tile's first) tells the MMA issuer
+                if (hc == 0) {
+                    const int slot = rc & 3;
+                    if (rc >= 4 && !tf_wait(&ring_empty[slot], ((rc >> 2) + 1) & 1, A.err, s_abort)) break;
+                    mbar_arrive(&ring_full[slot]);
+                }
                 break;
             }
             const int64_t gb = A.blk_begin + 4 * t + b;
@@ -401,6 +415,8 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
             const float *sQ = stage_q(st) + b * QS;
             const float *sG = stage_g(st) + b * GS;
             const float2 *__restrict__ tb = reinterpret_cast<const float2 *>(A.tin) + (valid ? gb : 0) * (TI / 2);
+            // this block's incoming traces are read from the first face slab on
+            if (hc == 0 && valid && lane == 0) prefetch_l2(tb, TI * 4);
             // A block past the end of the launch range computes on whatever its stage
             // slot holds: its rows of the products are never read (each output row
             // depends on its own A row only) and its tensor-memory rows are not stored.
@@ -408,37 +424,36 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
 #pragma unroll
             for (int q = 0; q < 9; ++q) g[q] = sG[q * 32 + lane];
             const float Zm = sG[15 * 32 + lane];
-            int cf[4];
+            int cf[4];        // connectivity words (p = 0 faces)
 #pragma unroll
             for (int f = 0; f < 4; ++f) cf[f] = A.conn[(valid ? gb : 0) * CS + f * 32 + lane];
-            float2 tcur[8], tnxt[8];   // incoming traces of the current and the next face slab
-            tf_load_tin<N>(tb, 0, lane, tnxt);
+            float2 tnxt[8];   // incoming traces of this warp's next face slab
+            tf_load_tin<N>(tb, hc, lane, tnxt);
             bool bad = false;
             int prev_slot = -1;   // ring slot stored but not yet signalled
-            for (int s = 0; s < G::NSLAB; ++s, ++rc) {
+            for (int s = hc; s < G::NSLAB; s += 2, rc += 2) {
                 uint32_t v[32];
                 if (s < 2 * G::NKV) {
                     const int kv = s >> 1;
-                    const bool odd = s & 1;
                     // (P, F_r) on even slabs, (F_s, F_t) on odd ones; K positions past the
                     // last node repeat it (zero operator rows there)
-                    const float ga = odd ? g[3] : g[0], gb_ = odd ? g[4] : g[1], gc = odd ? g[5] : g[2];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int n = min(8 * kv + k, NP - 1);
-                        const float p = sQ[n * 32 + lane], u = sQ[(NP + n) * 32 + lane], vv = sQ[(2 * NP + n) * 32 + lane],
+                        const float u = sQ[(NP + n) * 32 + lane], vv = sQ[(2 * NP + n) * 32 + lane],
                                     ww = sQ[(3 * NP + n) * 32 + lane];
-                        const float x0 = odd ? ga * u + gb_ * vv + gc * ww : p;
-                        const float x1 = odd ? g[6] * u + g[7] * vv + g[8] * ww : ga * u + gb_ * vv + gc * ww;
+                        const float x0 = hc ? g[3] * u + g[4] * vv + g[5] * ww : sQ[n * 32 + lane];
+                        const float x1 = hc ? g[6] * u + g[7] * vv + g[8] * ww : g[0] * u + g[1] * vv + g[2] * ww;
                         tf32_split(x0, v[k], v[8 + k]);
                         tf32_split(x1, v[16 + k], v[24 + k]);
                     }
                 } else {
                     const int kl = s - 2 * G::NKV;
                     const int f = kl / G::NKF, h = kl - f * G::NKF;
+                    float2 tcur[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) tcur[k] = tnxt[k];
-                    if (kl + 1 < 4 * G::NKF) tf_load_tin<N>(tb, kl + 1, lane, tnxt);
+                    if (kl + 2 < 4 * G::NKF) tf_load_tin<N>(tb, kl + 2, lane, tnxt);
                     float nx, ny, nz, fsc;
                     face_normal(g, f, nx, ny, nz, fsc);
                     const float zp = sG[(9 + f) * 32 + lane];
@@ -460,8 +475,10 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
                         tf32_split(fsc * dUn, v[k], v[8 + k]);
                         tf32_split(sgn * dP, v[16 + k], v[24 + k]);
                     }
-                    if (s == G::NSLAB - 1) mbar_arrive(&stage_empty[st]);   // last read of the stage
+                    // the epilogue of this tile reads res after the products; request it now
+                    if (kl == 0 && valid && lane == 0) prefetch_l2(A.res + gb * QS, QS * 4);
                 }
+                if (s + 2 >= G::NSLAB) mbar_arrive(&stage_empty[st]);   // this warp's last read of the stage
                 // the previous slab's store has had this slab's arithmetic to complete
                 if (prev_slot >= 0) {
                     if (valid) tmem_wait_st();
@@ -475,13 +492,13 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
                 prev_slot = slot;
             }
             if (bad) break;
-            if (valid) tmem_wait_st();   // the tile's last slab
+            if (valid) tmem_wait_st();   // the warp's last slab of the tile
             tc_fence_before();
             mbar_arrive(&ring_full[prev_slot]);
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int b = w & 3, h = (w - 6) >> 2;   // 32-cell block, parity of this warp's output-node chunks
+        const int b = w & 3, h = (w - 2 - G::NCONV) >> 2;   // 32-cell block, parity of this warp's output-node chunks
         const uint32_t trow = tbase + ((uint32_t)(32 * b) << 16);
         double tstage = 0.0;
         if (A.src.n > 0) tstage = sc.time[0] + sc.c_dt;
@@ -501,14 +518,9 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
 #pragma unroll
                 for (int q = 0; q < 9; ++q) g[q] = sG[q * 32 + lane];
                 const float rc2 = sG[13 * 32 + lane], irho = sG[14 * 32 + lane];
-                float nrm[4][3];   // outward unit normals
                 int cf[4];         // connectivity words: neighbour face and node order, or boundary face
 #pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    float fs_unused;
-                    face_normal(g, f, nrm[f][0], nrm[f][1], nrm[f][2], fs_unused);
-                    cf[f] = A.conn[gb * CS + f * 32 + lane];
-                }
+                for (int f = 0; f < 4; ++f) cf[f] = A.conn[gb * CS + f * 32 + lane];
                 const int64_t kcell = gb * 32 + lane;
                 bool has_src = false;
                 for (int si = 0; si < A.src.n; ++si) has_src |= A.src.cell[si] == kcell;
@@ -516,14 +528,15 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
                 float *__restrict__ rg = A.res + gb * QS;
                 float2 *__restrict__ tout = reinterpret_cast<float2 *>(A.tout);
                 const uint32_t tacc = trow + a * G::ACC;
-                // 4-node chunks, this warp every other one; res of the warp's next
+                // NC-node chunks, this warp every other one; res of the warp's next
                 // chunk is requested before the current chunk is processed
-                constexpr int NCH = (NP + 3) / 4;
-                float rcur[4][4], rnxt[4][4];
-                auto load_res = [&](int j, float (&rv)[4][4]) {   // past the last node: repeat it (unused)
+                constexpr int NC = 2;
+                constexpr int NCH = (NP + NC - 1) / NC;
+                float rcur[NC][4], rnxt[NC][4];
+                auto load_res = [&](int j, float (&rv)[NC][4]) {   // past the last node: repeat it (unused)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int n = min(4 * j + c, NP - 1);
+                    for (int c = 0; c < NC; ++c) {
+                        const int n = min(NC * j + c, NP - 1);
 #pragma unroll
                         for (int fl = 0; fl < 4; ++fl) rv[c][fl] = rg[(fl * NP + n) * 32 + lane];
                     }
@@ -532,27 +545,27 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
 #pragma unroll 1
                 for (int j = h; j < NCH; j += 2) {
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
+                    for (int c = 0; c < NC; ++c)
 #pragma unroll
                         for (int fl = 0; fl < 4; ++fl) rcur[c][fl] = rnxt[c][fl];
                     if (j + 2 < NCH) load_res(j + 2, rnxt);
-                    float ar[4], as_[4], at[4], adv[4];
-                    tmem_ld4(tacc + 4 * j, ar);
-                    tmem_ld4(tacc + NPAD + 4 * j, as_);
-                    tmem_ld4(tacc + 2 * NPAD + 4 * j, at);
-                    tmem_ld4(tacc + 3 * NPAD + 4 * j, adv);
-                    float qn[4][4];
+                    float ar[NC], as_[NC], at[NC], adv[NC];
+                    tmem_ld2(tacc + NC * j, ar);
+                    tmem_ld2(tacc + NPAD + NC * j, as_);
+                    tmem_ld2(tacc + 2 * NPAD + NC * j, at);
+                    tmem_ld2(tacc + 3 * NPAD + NC * j, adv);
+                    float qn[NC][4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int n = min(4 * j + c, NP - 1);
+                    for (int c = 0; c < NC; ++c) {
+                        const int n = min(NC * j + c, NP - 1);
 #pragma unroll
                         for (int fl = 0; fl < 4; ++fl) qn[c][fl] = sQ[(fl * NP + n) * 32 + lane];
                     }
                     tmem_wait_ld();
                     // right-hand sides and update
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int n = 4 * j + c;
+                    for (int c = 0; c < NC; ++c) {
+                        const int n = NC * j + c;
                         if (n >= NP) break;
                         float rhs[4];
                         rhs[0] = -rc2 * adv[c];
@@ -578,13 +591,15 @@ __global__ void __launch_bounds__(448, 1) k3d_tf32(Args3 A, StageCoef sc, const 
                     for (int f = 0; f < 4; ++f) {
                         const int cc = cf[f];
                         if (cc == kPadConn) continue;
+                        float nx, ny, nz, fs_unused;   // outward unit normal (recomputed: registers are scarce)
+                        face_normal(g, f, nx, ny, nz, fs_unused);
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int n = 4 * j + c;
+                        for (int c = 0; c < NC; ++c) {
+                            const int n = NC * j + c;
                             if (n >= NP) break;
                             const int m = sNf[f * NP + n];
                             if (m < 0) continue;
-                            const float un = nrm[f][0] * qn[c][1] + nrm[f][1] * qn[c][2] + nrm[f][2] * qn[c][3];
+                            const float un = nx * qn[c][1] + ny * qn[c][2] + nz * qn[c][3];
                             if (cc >= 0) {   // neighbour face (k', f'): its node order
                                 const int nb = cc >> 3;
                                 const int64_t kn = nb >> 2;
