@@ -31,9 +31,29 @@ WORKLOAD = {"workload": "cube48_N4_P6_gaussian", "mesh": "48^3 hex x 6 Kuhn tets
             "N": 4, "P": 6, "c": 1.0, "rho": 1.0, "pulse_width": 0.1}
 METRIC = "DOF-updates/s per RK stage"
 SEED = 2000
-# dram__bytes_read.sum + dram__bytes_write.sum of k3d_stage<4> for one full stage (interior and
-# boundary-cell launches) of this workload, from one ncu capture of the current kernel (one pass)
-K3D_TRAFFIC_BYTES = 2092811264 + 71113984
+# dram__bytes_read.sum + dram__bytes_write.sum of the benchmark's 3D kernel for one full stage
+# (interior and boundary-cell launches) of this workload, from one ncu capture (one pass).  The
+# figure belongs to the kernel source whose SHA-256 prefix is stored with it; when the source no
+# longer matches, the bench reports the traffic as null rather than a stale number.
+K3D_TRAFFIC = {"kernel": "k3d_tf32<4>", "bytes": 2508670000 + 71280640, "source_sha256": "76252bfe81baedac",
+               "captured": "2026-12-04, profiles/launches_cube48_N4_P6.md"}
+K3D_SOURCE = os.path.join(ROOT, "paper_1610_05023_b300", "csrc", "k3d_tf32.cuh")
+
+
+def kernel_source_sha():
+    import hashlib
+    with open(K3D_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def build_inputs(n=48):
@@ -41,6 +61,81 @@ def build_inputs(n=48):
     VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=SEED)
     x0 = W.seeded_point(SEED, [0.70, 0.65, 0.60], 0.05)
     return VX, EToV, x0
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1800.0
+
+
+def run_variants(dgh, g, VX, EToV, x0, stream, args, ndof, q_ref):
+    """The benchmark workload with the FP32 CUDA-core 3D kernel (the fallback
+    variant; same launch shapes, same warm-up and K steps, its 3D fields
+    compared with q_ref, the default path's after the same steps), and the
+    chosen precision form on its own workload."""
+    import torch
+    cc = dgh.Solver(VX, EToV, 4, 6, c=1.0, rho=1.0, stream=stream, precision=dgh.PREC_FP32_CUDA)
+    cc.init_gaussian(x0, 0.1)
+    cc.set_launch(**{k: g.launch[k] for k in ("tile2", "tile1", "thr2", "thr1")})
+    cc.step(args.warmup)
+    cc.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cc.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_cc = e0.elapsed_time(e1)
+    q_cc = cc.get_state(3)
+    diff = [float(np.linalg.norm(q_cc[:, f] - q_ref[:, f]) / max(np.linalg.norm(q_ref[:, f]), 1e-30)) for f in range(4)]
+    kt_cc = cc.time_kernels(20)
+    variants = {"fp32_cuda_cores": {"value": ndof * 5 * args.steps / (ms_cc * 1e-3), "ms_per_step": ms_cc / args.steps,
+                                    "k3d_launch_ms": kt_cc["k3d"], "rel_l2_vs_default_3d": diff,
+                                    "note": "DGH_PREC_FP32_CUDA: the same workload with FP32 CUDA-core "
+                                            "contractions (packed FP32 FMAs)"}}
+    cc.close()
+    form = precision_form_pair(dgh, min(args.steps, 100), args.warmup)
+    return variants, form
+
+
+def precision_form_pair(dgh, steps, warmup):
+    """The precision form's workload (N = 6, 32^3 x 6 tets, three layers,
+    HABC P = 4, seeded Gaussian) with the FP32 path and with the accepted
+    tensor-core arm (split BF16): DOF-updates/s of each over the same steps
+    (CUDA events on the solver's stream) and the relative L2 difference of
+    the split-BF16 3D fields from the FP32 ones."""
+    import torch
+    from paper_1610_05023_b300 import workloads as W
+    n = 32
+    VX, EToV = W.kuhn_mesh(n, 1.0, 0.02, seed=PREC_SEED)
+    c, rho = W.layered_material(VX, EToV, [-1 / 3, 1 / 3], [1.0, 1.5, 2.0], [1.0, 1.2, 1.5])
+    x0 = W.seeded_point(PREC_SEED, [0.75, 0.70, 0.80], 0.05)
+    out, ref = {}, None
+    for name, prec in (("fp32", dgh.PREC_FP32), ("split_bf16_tc", dgh.PREC_SPLIT_BF16)):
+        st = torch.cuda.Stream()
+        g = dgh.Solver(VX, EToV, 6, 4, c=c, rho=rho, stream=st, precision=prec)
+        g.init_gaussian(x0, 0.1)
+        g.step(warmup)
+        g.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.step(steps)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        q3 = g.get_state(3)
+        ref = q3 if ref is None else ref
+        out[name] = {"value": g.info["ndof"] * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "rel_l2_vs_fp32": [float(np.linalg.norm(q3[:, f] - ref[:, f]) / max(np.linalg.norm(ref[:, f]), 1e-30))
+                                        for f in range(4)]}
+        g.close()
+    return {"workload": "layered%d_N6_P4_gaussian" % n, "steps": steps, "arms": out,
+            "accepted_arm": "split_bf16_tc",
+            "speedup_vs_fp32": out["split_bf16_tc"]["value"] / out["fp32"]["value"],
+            "acceptance": "error vs the FP64 oracle <= 10% of the discretisation error (checked by "
+                          "tests/test_precision_gpu.py::test_precision_acceptance_rule)"}
 
 
 def peaks():
@@ -100,7 +195,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_oracle_sample_here(seconds_budget):
+def _cpu_oracle_sample_here(seconds_budget, threads=1):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     the same degree, HABC order, jitter and pulse on a 6^3-hex (1296-tet)
     cube, timed over whole LSERK4 steps (this process; its BLAS/OpenMP
@@ -124,23 +219,37 @@ def _cpu_oracle_sample_here(seconds_budget):
         el = time.perf_counter() - t0
         if el > seconds_budget or steps >= 50:
             break
-    return {"value": m.ndof() * 5 * steps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+    return {"value": m.ndof() * 5 * steps / el, "unit": METRIC, "cores": threads, "kind": "oracle",
             "sample": "%d LSERK4 steps of the same N=4, P=6, jittered Gaussian-pulse problem on a "
-                      "6^3-hex (1296-tet) cube, FP64 numpy, 1 thread (%.1f s)" % (steps, el),
+                      "6^3-hex (1296-tet) cube, FP64 numpy, BLAS/OpenMP pools of %d thread(s) (%.1f s)"
+                      % (steps, threads, el),
             "steps": steps, "seconds": el}
 
 
-def cpu_oracle_sample(seconds_budget=20.0):
+def cpu_oracle_sample(seconds_budget=20.0, threads=1):
     """Runs _cpu_oracle_sample_here in a child process whose BLAS and OpenMP
-    pools are limited to one thread (environment set before numpy loads)."""
+    pools hold `threads` threads (environment set before numpy loads)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
               "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        env[k] = "1"
+        env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-sample", str(seconds_budget)],
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-sample", str(seconds_budget),
+                          "--cpu-oracle-threads", str(threads)],
                          env=env, capture_output=True, text=True, check=True, cwd=ROOT)
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(seconds_budget=15.0):
+    """The oracle on all host cores (BLAS/OpenMP pools of nproc threads) and
+    on one; the all-cores run is the reported value."""
+    ncpu = os.cpu_count() or 1
+    allc = cpu_oracle_sample(seconds_budget, threads=ncpu)
+    one = cpu_oracle_sample(seconds_budget, threads=1)
+    out = {k: allc[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    out["cpu_model"] = cpu_model()
+    out["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
+    return out
 
 
 def replica_time_max(seconds, world, device=None):
@@ -165,13 +274,14 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per = max(10.0, 60.0 / max(args.steps + args.warmup, 1))
-    r = cpu_oracle_sample(per * args.steps)
+    per = min(60.0, max(10.0, 60.0 / max(args.steps + args.warmup, 1) * args.steps))
+    ncpu = os.cpu_count() or 1
+    r = cpu_oracle_sample(per, threads=ncpu)
     line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
             "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": r["sample"], "cpu_model": cpu_model()},
             "e2e": {"value": r["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -326,7 +436,16 @@ def run_precision_form(args):
             "data": "synthetic",
             "config": {"workload": "layered%d_N6_P4_gaussian" % n, "n_cells": 6 * n ** 3, "seed": PREC_SEED,
                        "bytes_per_tet": 4 * (16 * 84 + 16 * 28) + 100, "peak_gbs": peak, "peak_kind": peak_kind},
-            "arms": arms, "value": max(a["value"] for a in arms)}
+            "arms": arms}
+    # The form's number is its accepted arm: the fastest tensor-core arm that meets the
+    # acceptance rule (error against the FP64 oracle at most 10% of the discretisation error,
+    # checked by the tests: split BF16 meets it, BF16 and FP16 do not at N = 6).
+    acc = next(a for a in arms if a["precision"] == PREC_NAMES[3])
+    line.update({"value": acc["value"], "accepted_arm": acc["precision"],
+                 "speedup_vs_fp32": acc["value"] / arms[0]["value"],
+                 "acceptance": "split_bf16_tc: error vs the FP64 oracle <= 10% of the discretisation error "
+                               "(tests/test_precision_gpu.py::test_precision_acceptance_rule); bf16_tc and fp16_tc "
+                               "fail the rule and are listed for context only"})
     print(json.dumps(line), flush=True)
 
 
@@ -655,7 +774,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=48, help="hexes per axis (48 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the CUDA-core variant and the chosen precision form (shorter runs for profiling)")
     ap.add_argument("--cpu-oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-oracle-threads", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--closure-runs", type=int, default=64)
     ap.add_argument("--closure-train-n", type=int, default=24)
     ap.add_argument("--closure-eval-n", type=int, default=40)
@@ -668,7 +790,7 @@ def main():
                          "workload with the FP32 and tensor-core 3D kernels")
     args = ap.parse_args()
     if args.cpu_oracle_sample is not None:   # child process of cpu_oracle_sample()
-        print(json.dumps(_cpu_oracle_sample_here(args.cpu_oracle_sample)), flush=True)
+        print(json.dumps(_cpu_oracle_sample_here(args.cpu_oracle_sample, args.cpu_oracle_threads)), flush=True)
         return
     if args.impl == "reference":
         return run_reference(args)
@@ -728,6 +850,7 @@ def main():
     ms = replica_time_max(start.elapsed_time(end), world, device="cuda")
     value = replica_throughput(ndof * 5 * args.steps, world, ms * 1e-3)
 
+    q_after = g.get_state(3) if not args.no_variants else None   # for the variant comparison
     # per-kernel durations (events around each launch, direct launches)
     kt = g.time_kernels(20)
     K = info["n_cells"]
@@ -735,27 +858,42 @@ def main():
     bytes_per_tet = 4 * (16 * Np + 16 * Nfp) + 100          # algorithmic bytes per tet per stage
     achieved = K * bytes_per_tet / (kt["k3d"] * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    # the FP32 compute bound: 12 Np^2 + 32 Np Nfp algorithmic flops per tet per stage
-    # against the probe-measured FP32 CUDA-core peak of this GPU
-    flops_per_tet = 12 * Np * Np + 32 * Np * Nfp
-    fp32_ach = K * flops_per_tet / (kt["k3d"] * 1e-3) / 1e12
-    fp32_scalar, fp32_packed = dgh.fp32_probe()
+    # tensor pipe of the split-TF32 kernel: per 128-cell tile and product pass the MMAs
+    # cover sum(N x K) = 5 k-steps x 3 NPAD (stacked P D^T) + 15 x NPAD (F_j D_j^T) +
+    # 8 x NPAD (XU LIFT^T) + 12 x NPAD (signed dP LIFT_f^T, face 2 into three
+    # accumulators) with M = 128, NPAD = 48; three passes (hi hi, lo hi, hi lo)
+    npad = (Np + 15) // 16 * 16
+    mma_nk = (5 * 3 * npad + 15 * npad + 8 * npad + 12 * npad) * 8
+    tc_flops = 3 * 2 * 128 * mma_nk * ((K + 127) // 128)
+    tc_ach = tc_flops / (kt["k3d"] * 1e-3) / 1e12
+    tf32_peak = bf16_peak() * (1.1 / 2.25)    # measured BF16 x the nominal TF32 / BF16 ratio
+    sha = kernel_source_sha()
+    traffic = K3D_TRAFFIC["bytes"] if (args.n == 48 and K3D_TRAFFIC["bytes"] and sha == K3D_TRAFFIC["source_sha256"]) else None
 
-    # end to end through the public API: host initial state in, host fields out,
-    # both in pinned host memory (allocated and filled outside the timed region)
-    shape3 = g.shape(3)
-    q3 = torch.empty(shape3, dtype=torch.float64, pin_memory=True).numpy()
-    out = torch.empty(shape3, dtype=torch.float64, pin_memory=True).numpy()
-    g.get_state(3, out=q3)
-    e2e_steps = min(args.steps, 200)
+    # the same workload with the FP32 CUDA-core 3D kernel (the fallback variant)
+    variants, form = None, None
+    if not args.no_variants:
+        variants, form = run_variants(dgh, g, VX, EToV, x0, stream, args, ndof, q_after)
+    # end to end through the public API: the whole state (3D, face and edge levels) in from
+    # pinned host memory, K steps, the whole state back out (host arrays allocated and filled
+    # outside the timed region; FP64 as the API takes it, converted on the device)
+    host_in, host_out = {}, {}
+    for lv in (3, 2, 1):
+        shp = g.shape(lv)
+        host_in[lv] = torch.empty(shp, dtype=torch.float64, pin_memory=True).numpy()
+        host_out[lv] = torch.empty(shp, dtype=torch.float64, pin_memory=True).numpy()
+        g.get_state(lv, out=host_in[lv])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g.set_state(3, q3)
-    g.step(e2e_steps)
-    g.get_state(3, out=out)
+    for lv in (3, 2, 1):
+        g.set_state(lv, host_in[lv])
+    g.step(args.steps)
+    for lv in (3, 2, 1):
+        g.get_state(lv, out=host_out[lv])
     t1 = time.perf_counter()
-    e2e_value = replica_throughput(ndof * 5 * e2e_steps, world, replica_time_max(t1 - t0, world, device="cuda"))
-    state_bytes = q3.size * 8      # FP64 host arrays copied as they are (converted on the device)
+    e2e_value = replica_throughput(ndof * 5 * args.steps, world, replica_time_max(t1 - t0, world, device="cuda"))
+    state_bytes = sum(a.size * 8 for a in host_in.values())
+
 
     parts3 = 2 if info["n_tris"] > 0 else 1      # interior cells, then cells with HABC faces
     launches_per_step = 5 * (parts3 + (info["n_tris"] > 0) + (info["n_lines"] > 0) + (info["n_corners"] > 0)) + 1
@@ -767,30 +905,37 @@ def main():
                                                               "mesh": "%d^3 hex x 6 Kuhn tets" % args.n}),
                        ndof=ndof, n_cells=K, n_tris=info["n_tris"], n_lines=info["n_lines"],
                        n_corners=info["n_corners"], dt=info["dt"],
-                       l2_policy="inputs larger than L2 (state %.0f MB per array)" % (q3.size * 4 / 1e6),
+                       arithmetic="FP32 state; 3D volume and lift contractions as split-TF32 tcgen05 products "
+                                  "(hi*hi + lo*hi + hi*lo, FP32 accumulation; parity <= 1e-5 vs the FP64 oracle)",
+                       l2_policy="inputs larger than L2 (state %.0f MB per array)" % (host_in[3].size * 4 / 1e6),
                        launch={k: g.launch[k] for k in ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1")},
                        tuner_ms_per_step=list(tune_ms),
                        parallelism="replicas" if world > 1 else "single"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": K3D_TRAFFIC_BYTES if args.n == 48 else None,
-                     "traffic_over_algorithmic": K3D_TRAFFIC_BYTES / (K * bytes_per_tet) if args.n == 48 else None,
-                     "kernel": "k3d_stage<4>",
-                     "fp32": {"achieved_tflops": fp32_ach, "flops_per_tet": flops_per_tet,
-                              "peak_tflops": max(fp32_scalar, fp32_packed), "peak_kind": "measured (own FFMA probe)",
-                              "probe_ffma_tflops": fp32_scalar, "probe_ffma2_tflops": fp32_packed,
-                              "frac": fp32_ach / max(fp32_scalar, fp32_packed)},
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_over_algorithmic": traffic / (K * bytes_per_tet) if traffic else None,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s, both launches of "
+                                        "one stage, captured %s (kernel source sha256 %s); null when the source "
+                                        "has changed since" % (K3D_TRAFFIC["kernel"], K3D_TRAFFIC["captured"],
+                                                               K3D_TRAFFIC["source_sha256"])),
+                     "kernel": "k3d_tf32<4>", "kernel_source_sha256": sha,
+                     "tensor": {"achieved_tflops": tc_ach, "mma_flops_per_stage": tc_flops,
+                                "peak_tflops": tf32_peak, "peak_kind": "measured bf16 x nominal tf32/bf16 ratio",
+                                "frac": tc_ach / tf32_peak},
                      "peak_kind": peak_kind, "bytes_per_tet": bytes_per_tet,
                      "launch_ms": kt["k3d"]},
         "kernel_ms": kt,
-        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes / e2e_steps,
-                "d2h_bytes_per_step": state_bytes / e2e_steps, "steps": e2e_steps,
-                "note": "set_state(pinned host FP64) + step(n) + get_state(pinned host FP64) through the C ABI"},
+        "variants": variants,
+        "chosen_form": form,
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes / args.steps,
+                "d2h_bytes_per_step": state_bytes / args.steps, "steps": args.steps,
+                "note": "set_state of every level (pinned host FP64) + step(K) + get_state of every level "
+                        "(pinned host FP64) through the C ABI; the copies are amortised over the K steps"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = cpu_oracle_sample()
-        line["cpu_baseline"] = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.close()
