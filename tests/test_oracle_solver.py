@@ -489,3 +489,22 @@ def test_volume_energy_rate_with_boundary_faces():
                     kinds.add("HABC")
     assert kinds == {"interior", "p = 0", "HABC"}
     assert abs(dE - rate) <= 1e-10 * abs(rate)
+
+
+def test_ricker_spectrum_peaks_at_the_peak_frequency():
+    """Frequency convention of the Ricker wavelet (Sec. 4.1, eq.
+    validBench:ricker): its Fourier amplitude |S(f)| = |int s(t) e^{-2 pi i f t} dt|
+    has the closed form (2 / sqrt(pi)) (f^2 / f_p^3) exp(-f^2 / f_p^2), whose
+    maximum is at f = f_p.  The integral is taken numerically here (trapezoid
+    rule on a fine grid), independently of the oracle's formula, so a wrong
+    scale inside the exponent (a missing or extra pi, f instead of 2 pi f)
+    moves the peak and fails."""
+    from oracle.solver import ricker
+    for f_peak, ts in ((2.5, 0.5), (4.0, 0.3125)):
+        tau = np.linspace(-4.0 / f_peak, 4.0 / f_peak, 40001)
+        s = np.array([ricker(ts + x, f_peak, ts) for x in tau])
+        freqs = np.linspace(0.05, 3.0, 300) * f_peak
+        amp = np.array([abs(np.trapezoid(s * np.exp(-2j * np.pi * f * tau), tau)) for f in freqs])
+        closed = 2.0 / np.sqrt(np.pi) * freqs ** 2 / f_peak ** 3 * np.exp(-(freqs / f_peak) ** 2)
+        assert np.max(np.abs(amp - closed)) < 1e-8 * np.max(closed)
+        assert abs(freqs[np.argmax(amp)] - f_peak) <= (freqs[1] - freqs[0])
