@@ -34,11 +34,13 @@
 //              a ring of four 32-column slabs, so no shared-memory bandwidth
 //              is spent on them.  The store of a slab completes while the
 //              warp computes its next one;
-//   warps 10-17 epilogue, two warps per 32-cell block (thread = cell, each
-//              warp every other 4-node chunk): accumulators (tcgen05.ld) and
-//              the old state (from the stage) -> right-hand sides, LSERK
-//              update (res read from L2 one chunk ahead), then the trace
-//              pushes of the chunk face by face.
+//   warps 10-17 epilogue, two warps per 32-cell block (thread = cell):
+//              accumulators (tcgen05.ld) and the old state (from the stage)
+//              -> right-hand sides, LSERK update (each warp every other
+//              2-node chunk, res read from L2 one chunk ahead), the new state
+//              written to global memory and over the old one in the stage;
+//              then the trace pushes read from the stage, each warp two
+//              faces, node after node of the face.
 // The work per cell is latency-bound, so the roles get as many warps as
 // the register file allows (18 warps: 96 registers each, as four
 // sub-partitions hold at most five warps of 96); the per-thread state is
@@ -283,24 +285,14 @@ __global__ void __launch_bounds__(576, 1) k3d_tf32(Args3 A, StageCoef sc, const 
             auto claim = [&](int i) -> int64_t {
                 return i < A.max_tiles ? (int64_t)atomicAdd(A.tile_ctr, 1ull) : ntiles;
             };
-            // what the next stage copy reads; the incoming traces and res are
-            // prefetched by the converters, closer to their use (a prefetch a
-            // whole tile ahead is often evicted from L2 before it is read)
-            auto prefetch = [&](int64_t t) {
-                for (int b = 0; b < 4; ++b) {
-                    const int64_t gb = A.blk_begin + 4 * t + b;
-                    if (gb >= A.blk_end) break;
-                    prefetch_l2(A.q + gb * QS, QS * 4);
-                    prefetch_l2(A.geo + gb * GS, GS * 4);
-                    prefetch_l2(A.conn + gb * CS, CS * 4);
-                }
-            };
+            // No L2 prefetch of the next tile here: its stage copy runs about a tile
+            // period later, by when a prefetched line has often been evicted (the
+            // DRAM reads grew by a third with it).  The converters request the
+            // incoming traces and res of their own block closer to their use.
             int64_t next = claim(0);
-            if (next < ntiles) prefetch(next);
             for (int i = 0;; ++i) {
                 const int64_t t = next;
                 next = t < ntiles ? claim(i + 1) : ntiles;
-                if (next < ntiles) prefetch(next);
                 s_tiles[i & 7] = t < ntiles ? t : ntiles;
                 const int st = i & 1;
                 // stage st is free once both consumers of tile i - 2 are done with it
@@ -498,7 +490,7 @@ __global__ void __launch_bounds__(576, 1) k3d_tf32(Args3 A, StageCoef sc, const 
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int b = w & 3, h = (w - 2 - G::NCONV) >> 2;   // 32-cell block, parity of this warp's output-node chunks
+        const int b = w & 3, h = (w - 2 - G::NCONV) >> 2;   // 32-cell block; this warp's half of the work
         const uint32_t trow = tbase + ((uint32_t)(32 * b) << 16);
         double tstage = 0.0;
         if (A.src.n > 0) tstage = sc.time[0] + sc.c_dt;
@@ -511,25 +503,22 @@ __global__ void __launch_bounds__(576, 1) k3d_tf32(Args3 A, StageCoef sc, const 
             // the stage of tile i (complete since its converters ran; held until this arrival)
             if (!tf_wait(&stage_full[st], (i >> 1) & 1, A.err, s_abort)) break;
             const int64_t gb = A.blk_begin + 4 * t + b;
-            if (gb < A.blk_end) {
-                const float *sQ = stage_q(st) + b * QS;
-                const float *sG = stage_g(st) + b * GS;
-                float g[9];
+            const bool valid = gb < A.blk_end;
+            float *sQw = stage_q(st) + b * QS;   // old state in; the new state is written over it
+            const float *sG = stage_g(st) + b * GS;
+            float g[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) g[q] = sG[q * 32 + lane];
+            for (int q = 0; q < 9; ++q) g[q] = sG[q * 32 + lane];
+            if (valid) {
+                // ---- update: NC-node chunks, this warp every other one; res of the warp's
+                // next chunk is requested before the current chunk is processed
                 const float rc2 = sG[13 * 32 + lane], irho = sG[14 * 32 + lane];
-                int cf[4];         // connectivity words: neighbour face and node order, or boundary face
-#pragma unroll
-                for (int f = 0; f < 4; ++f) cf[f] = A.conn[gb * CS + f * 32 + lane];
                 const int64_t kcell = gb * 32 + lane;
                 bool has_src = false;
                 for (int si = 0; si < A.src.n; ++si) has_src |= A.src.cell[si] == kcell;
                 float *__restrict__ qg = A.q + gb * QS;
                 float *__restrict__ rg = A.res + gb * QS;
-                float2 *__restrict__ tout = reinterpret_cast<float2 *>(A.tout);
                 const uint32_t tacc = trow + a * G::ACC;
-                // NC-node chunks, this warp every other one; res of the warp's next
-                // chunk is requested before the current chunk is processed
                 constexpr int NC = 2;
                 constexpr int NCH = (NP + NC - 1) / NC;
                 float rcur[NC][4], rnxt[NC][4];
@@ -554,15 +543,7 @@ __global__ void __launch_bounds__(576, 1) k3d_tf32(Args3 A, StageCoef sc, const 
                     tmem_ld2(tacc + NPAD + NC * j, as_);
                     tmem_ld2(tacc + 2 * NPAD + NC * j, at);
                     tmem_ld2(tacc + 3 * NPAD + NC * j, adv);
-                    float qn[NC][4];
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const int n = min(NC * j + c, NP - 1);
-#pragma unroll
-                        for (int fl = 0; fl < 4; ++fl) qn[c][fl] = sQ[(fl * NP + n) * 32 + lane];
-                    }
                     tmem_wait_ld();
-                    // right-hand sides and update
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
                         const int n = NC * j + c;
@@ -582,43 +563,57 @@ __global__ void __launch_bounds__(576, 1) k3d_tf32(Args3 A, StageCoef sc, const 
                             const int idx = (fl * NP + n) * 32 + lane;
                             const float r = sc.a * rcur[c][fl] + sc.dt * rhs[fl];
                             rg[idx] = r;
-                            qn[c][fl] += sc.b * r;
-                            qg[idx] = qn[c][fl];
+                            const float qn = sQw[idx] + sc.b * r;
+                            qg[idx] = qn;
+                            sQw[idx] = qn;
                         }
                     }
-                    // new traces of the chunk's face nodes, face by face (f known at compile time)
+                }
+            }
+            // the accumulators of tile i are read: the products of tile i + 2 may start
+            tc_fence_before();
+            mbar_arrive(&acc_empty[a]);
+            if (valid) {
+                // both epilogue warps of this block have written their nodes' new state
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + b), "r"(64) : "memory");
+                // ---- new traces, face by face (this warp: faces 2h and 2h + 1), read from the stage
+#pragma unroll 1
+                for (int ff = 0; ff < 2; ++ff) {
+                    const int f = 2 * h + ff;
+                    const int cc = A.conn[gb * CS + f * 32 + lane];
+                    if (cc == kPadConn) continue;
+                    float nx, ny, nz, fs_unused;
+                    face_normal(g, f, nx, ny, nz, fs_unused);
+                    // neighbour face (k', f'): float2 slot of (k', f', node 0) and its node order;
+                    // boundary face: own trace for the face HABC solver
+                    const bool inner = cc >= 0;
+                    const int nb = cc >> 3;
+                    const int64_t kn = nb >> 2;
+                    const int64_t base = inner ? (((kn >> 5) * 4 + (nb & 3)) * NFP) * 32 + (kn & 31) : 0;
+                    const int pofs = (cc & 7) * NFP;
+                    const int64_t bf = inner ? 0 : (-1 - cc) >> 1;
+                    const bool ok = inner ? DGH_IN_RANGE(A.err, kn, A.kcells) : DGH_IN_RANGE(A.err, bf, A.nbfaces);
+                    float *__restrict__ tb = A.trb + bf * 2 * NFP;
+                    float2 *__restrict__ tout = reinterpret_cast<float2 *>(A.tout);
 #pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        const int cc = cf[f];
-                        if (cc == kPadConn) continue;
-                        float nx, ny, nz, fs_unused;   // outward unit normal (recomputed: registers are scarce)
-                        face_normal(g, f, nx, ny, nz, fs_unused);
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) {
-                            const int n = NC * j + c;
-                            if (n >= NP) break;
-                            const int m = sNf[f * NP + n];
-                            if (m < 0) continue;
-                            const float un = nx * qn[c][1] + ny * qn[c][2] + nz * qn[c][3];
-                            if (cc >= 0) {   // neighbour face (k', f'): its node order
-                                const int nb = cc >> 3;
-                                const int64_t kn = nb >> 2;
-                                const int mn = sFp[(cc & 7) * NFP + m];
-                                if (DGH_IN_RANGE(A.err, kn, A.kcells))
-                                    tout[(((kn >> 5) * 4 + (nb & 3)) * NFP + mn) * 32 + (kn & 31)] = make_float2(qn[c][0], -un);
-                            } else {         // boundary face: own trace for the face HABC solver
-                                const int64_t bf = (-1 - cc) >> 1;
-                                if (DGH_IN_RANGE(A.err, bf, A.nbfaces)) {
-                                    A.trb[bf * 2 * NFP + m] = qn[c][0];
-                                    A.trb[bf * 2 * NFP + NFP + m] = un;
-                                }
+                    for (int m = 0; m < NFP; ++m) {
+                        const int n = sFm[f * NFP + m];
+                        const float p = sQw[n * 32 + lane];
+                        const float un = nx * sQw[(NP + n) * 32 + lane] + ny * sQw[(2 * NP + n) * 32 + lane] +
+                                         nz * sQw[(3 * NP + n) * 32 + lane];
+                        if (ok) {
+                            if (inner) {
+                                tout[base + sFp[pofs + m] * 32] = make_float2(p, -un);
+                            } else {
+                                tb[m] = p;
+                                tb[NFP + m] = un;
                             }
                         }
                     }
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&acc_empty[a]);
+            // the stage was written through the generic proxy; the next copy into it is a TMA write
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&stage_empty[st]);
         }
     }
