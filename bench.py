@@ -35,7 +35,7 @@ SEED = 2000
 # (interior and boundary-cell launches) of this workload, from one ncu capture (one pass).  The
 # figure belongs to the kernel source whose SHA-256 prefix is stored with it; when the source no
 # longer matches, the bench reports the traffic as null rather than a stale number.
-K3D_TRAFFIC = {"kernel": "k3d_tf32<4>", "bytes": 2508670000 + 71280640, "source_sha256": "76252bfe81baedac",
+K3D_TRAFFIC = {"kernel": "k3d_tf32<4>", "bytes": 2128334000 + 70214270, "source_sha256": "8f7cc273f8a769e5",
                "captured": "2026-12-04, profiles/launches_cube48_N4_P6.md"}
 K3D_SOURCE = os.path.join(ROOT, "paper_1610_05023_b300", "csrc", "k3d_tf32.cuh")
 
