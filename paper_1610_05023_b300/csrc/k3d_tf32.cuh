@@ -22,10 +22,10 @@
 // inputs, so hi and lo are rounded explicitly before they reach it).
 //
 // B300 design: one persistent CTA per SM, 18 warps in four roles.
-//   warp 0     producer: claims tiles, prefetches the next tile into L2,
-//              TMA bulk-copies the tile's q and geometry into one of two
-//              shared-memory stages (a stage is held until the converters and
-//              the epilogue of its tile are done with it);
+//   warp 0     producer: claims tiles, TMA bulk-copies each tile's q and
+//              geometry into one of two shared-memory stages (a stage is
+//              held until the converters and the epilogue of its tile are
+//              done with it);
 //   warp 1     MMA issuer (one thread) and tensor-memory owner;
 //   warps 2-9  converters, two warps per 32-cell block taking alternate
 //              slabs (thread = cell): flux differences (incoming traces read
