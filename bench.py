@@ -730,13 +730,7 @@ def run_seam_form(args):
     import paper_1610_05023_b300 as dgh
     from paper_1610_05023_b300 import workloads as W
     torch.cuda.set_device(0)
-    VX, EToV = W.kuhn_mesh((56, 64, 24), (1.75, 2.0, 0.75), 0.02, seed=7000)
-    cen = VX[EToV].mean(axis=1)
-    z = cen[:, 2]
-    c = np.where(z < -0.25, 3.5, np.where(z < 0.25, 2.5, 1.5))
-    rho = np.where(z < -0.25, 2.4, np.where(z < 0.25, 2.1, 1.8))
-    inc = (cen[:, 0] > 1.0) & (np.abs(cen[:, 1]) < 0.5) & (z > -0.4) & (z < 0.1)
-    c[inc], rho[inc] = 4.5, 2.6
+    VX, EToV, c, rho = W.seam_standin(seed=7000)
     bc = (0, 0, 0, 0, 0, 1)
     rows = {}
     for P in (0, 3, 6):

@@ -120,3 +120,24 @@ def batch_problems(seed, count=48, n_range=(8, 24), orders=(3, 4, 5), habc_order
         xs = [(2.0 * u[4 + a] - 1.0) * src_box for a in range(3)]
         out.append({"n": n, "N": N, "P": P, "f0": f0, "xs": xs, "t_s": 1.25 / f0, "mesh_seed": seed + i})
     return out
+
+
+SEAM_DIMS = (56, 64, 24)
+SEAM_HALF = (1.75, 2.0, 0.75)
+
+
+def seam_standin(seed=7000):
+    """The heterogeneous stand-in for the paper's SEAM setting (Sec. 4.2):
+    box [-1.75,1.75] x [-2,2] x [-0.75,0.75], 56 x 64 x 24 hexahedra x 6 Kuhn
+    tets (jitter 2% h); three horizontal layers by tet centroid, (c, rho) =
+    (3.5, 2.4) for z < -0.25, (2.5, 2.1) for z < 0.25, (1.5, 1.8) above; a fast
+    inclusion (4.5, 2.6) where x > 1.0, |y| < 0.5, -0.4 < z < 0.1 (it touches
+    the +x face).  Returns (VX, EToV, c, rho)."""
+    VX, EToV = kuhn_mesh(SEAM_DIMS, SEAM_HALF, 0.02, seed=seed)
+    cen = VX[EToV].mean(axis=1)
+    z = cen[:, 2]
+    c = np.where(z < -0.25, 3.5, np.where(z < 0.25, 2.5, 1.5))
+    rho = np.where(z < -0.25, 2.4, np.where(z < 0.25, 2.1, 1.8))
+    inc = (cen[:, 0] > 1.0) & (np.abs(cen[:, 1]) < 0.5) & (z > -0.4) & (z < 0.1)
+    c[inc], rho[inc] = 4.5, 2.6
+    return VX, EToV, c, rho

@@ -96,6 +96,31 @@ def corner_block(n, size=12, inner=2):
     return tets, cen, pos
 
 
+def hex_tets_box(n3, lo, size):
+    """Tet ids of the hexes lo + [0, size) (per axis) of an (nx, ny, nz) Kuhn
+    mesh from workloads.kuhn_mesh (hex (i, j, k) = i + nx (j + ny k))."""
+    n3, lo, size = (np.broadcast_to(np.asarray(a, int), (3,)) for a in (n3, lo, size))
+    r = [np.arange(lo[a], lo[a] + size[a]) for a in range(3)]
+    I, J, K = np.meshgrid(*r, indexing="ij")
+    hexes = (I + n3[0] * (J + n3[1] * K)).ravel(order="F")
+    return (6 * hexes[:, None] + np.arange(6)).ravel()
+
+
+def box_block(n3, inner_lo, inner_size):
+    """(block tet ids, sampled tet ids, their positions in the block) for the
+    sampled hexes inner_lo + [0, inner_size) and a block reaching MARGIN hexes
+    beyond them on every side, clipped at the mesh's own faces (which stay
+    real domain faces of the block)."""
+    n3, ilo, isz = (np.broadcast_to(np.asarray(a, int), (3,)) for a in (n3, inner_lo, inner_size))
+    lo = np.maximum(ilo - MARGIN, 0)
+    hi = np.minimum(ilo + isz + MARGIN, n3)
+    tets = hex_tets_box(n3, lo, hi - lo)
+    cen = hex_tets_box(n3, ilo, isz)
+    pos = np.searchsorted(tets, cen)
+    assert np.array_equal(tets[pos], cen)
+    return tets, cen, pos
+
+
 def tri_nodes(m):
     """[K^tri, Np2, 3] node coordinates of a mesh's triangles in the order of
     its face-level state (the owning tet face's nodes)."""

@@ -12,7 +12,7 @@ import numpy as np
 from oracle.mesh import BC_DIRICHLET, BC_HABC
 from oracle.solver import Solver
 from paper_1610_05023_b300 import workloads as W
-from patch_sampling import MARGIN, hex_tets, patch_and_centre, patch_mesh
+from patch_sampling import MARGIN, box_block, corner_block, hex_tets, hex_tets_box, patch_and_centre, patch_mesh
 
 N48 = 48
 
@@ -95,3 +95,24 @@ def test_corner_block_levels_do_not_see_the_cut_within_one_step():
         for key, got in (("q3", b["q3"]), ("q2", b["q2"][j2]), ("q1", b["q1"][j1])):
             scale = np.abs(a[key]).max()
             assert np.abs(got - a[key]).max() <= 1e-14 * scale, key
+
+
+def test_box_block_indexing():
+    """The general block of an (nx, ny, nz) mesh agrees with the cubic
+    helpers, and its tets are those whose centroids lie in the block's and
+    the sampled hexes' boxes (mesh without jitter: hexes of size h)."""
+    t1, c1, p1 = box_block(N48, [20, 21, 22], 2)
+    t2, c2, p2 = patch_and_centre(N48, [20, 21, 22])
+    assert np.array_equal(t1, t2) and np.array_equal(c1, c2) and np.array_equal(p1, p2)
+    t1, c1, p1 = box_block(N48, [N48 - 2] * 3, 2)
+    t2, c2, p2 = corner_block(N48, size=2 + MARGIN)
+    assert np.array_equal(t1, t2) and np.array_equal(c1, c2) and np.array_equal(p1, p2)
+    n3 = (7, 9, 16)
+    VX, EToV = W.kuhn_mesh(n3, (0.5 * 7, 0.5 * 9, 0.5 * 16), 0.0)   # unit hexes, corner at -n/2
+    cen = VX[EToV].mean(axis=1) + 0.5 * np.asarray(n3)
+    tets, cs, pos = box_block(n3, [5, 1, 8], [2, 3, 4])
+    inside = lambda lo, hi: np.nonzero(np.all((cen > lo) & (cen < hi), axis=1))[0]
+    assert np.array_equal(tets, inside([0, 0, 3], [7, 9, 16]))          # clipped at +x, -y, +z
+    assert np.array_equal(cs, inside([5, 1, 8], [7, 4, 12]))
+    assert np.array_equal(tets[pos], cs)
+    assert np.array_equal(hex_tets_box(N48, [3, 4, 5], 2), hex_tets(N48, [3, 4, 5], 2))
