@@ -86,7 +86,7 @@ def run_variants(dgh, g, VX, EToV, x0, stream, args, ndof, q_ref):
     import torch
     cc = dgh.Solver(VX, EToV, 4, 6, c=1.0, rho=1.0, stream=stream, precision=dgh.PREC_FP32_CUDA)
     cc.init_gaussian(x0, 0.1)
-    cc.set_launch(**{k: g.launch[k] for k in ("tile2", "tile1", "thr2", "thr1")})
+    cc.set_launch(**{k: g.launch[k] for k in ("tile2", "tile1", "thr2", "thr1", "split3")})
     cc.step(args.warmup)
     cc.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -517,10 +517,12 @@ def run_closure_form(args):
     Evaluation on the 40^3 x 6 unjittered cube (N = 4, c = rho = 1, Gaussian
     pulse of width 0.12 at (0.35, -0.25, 0.30), t in [0, 1.5]): plain P = 2,
     P = 2 with the open-loop closure (MLP(x) - MLP(0), and the homogeneous
-    form), P = 2 with the closed-loop closure, plain P = 8, against a
-    large-domain reference whose inner mesh is the same cube (its boundary is
-    too far for reflections to return by t = 1.5).
-    Error(t)^2 = energy of the difference in the cube / initial energy."""
+    form), P = 2 with the closed-loop closure, plain P = 1, 2, 3, 4 and 8,
+    against a large-domain reference whose inner mesh is the same cube (its
+    boundary is too far for reflections to return by t = 1.5).
+    Error(t)^2 = energy of the difference in the cube / initial energy.
+    equal_reflection compares the closure's time per step with that of the
+    cheapest plain order that reflects no more than it does."""
     import torch
     import paper_1610_05023_b300 as dgh
     from paper_1610_05023_b300 import workloads as W
@@ -575,7 +577,7 @@ def run_closure_form(args):
     nst += (-nst) % nck
     dt = T / nst
     arms = {"P2": (2, None), "P2_closure": (2, w), "P2_closure_homogeneous": (2, wh),
-            "P2_closure_closed_loop": (2, wc), "P8": (8, None)}
+            "P2_closure_closed_loop": (2, wc), "P1": (1, None), "P3": (3, None), "P4": (4, None), "P8": (8, None)}
     solvers = {}
     for name, (P, wts) in arms.items():
         g = dgh.Solver(VXs, EToVs, 4, P, dt=dt)
@@ -605,8 +607,26 @@ def run_closure_form(args):
     summary = {}
     for name in arms:
         after = [e for t, e in zip(times, errs[name]) if t >= t_hit]
-        summary[name] = {"error_max_after_hit": max(after), "error_at_T": errs[name][-1],
-                         "ms_per_step": float(np.median(step_ms[name]))}
+        ndof = solvers[name].info["ndof"]
+        ms = float(np.median(step_ms[name]))
+        summary[name] = {"error_max_after_hit": max(after), "error_at_T": errs[name][-1], "ms_per_step": ms,
+                         "ndof": ndof, "dof_updates_per_s": ndof * 5 / (ms * 1e-3)}
+    # the closure against the plain method at equal reflection: the cheapest
+    # plain order whose error is at most the closed-loop closure's
+    ec = summary["P2_closure_closed_loop"]["error_max_after_hit"]
+    plain = sorted((summary[k]["ms_per_step"], k) for k in ("P1", "P2", "P3", "P4", "P8")
+                   if summary[k]["error_max_after_hit"] <= ec)
+    match = plain[0][1] if plain else None
+    equal = {"closure_arm": "P2_closure_closed_loop", "closure_error": ec,
+             "closure_ms_per_step": summary["P2_closure_closed_loop"]["ms_per_step"],
+             "cheapest_plain_at_or_below": match,
+             "plain_error": summary[match]["error_max_after_hit"] if match else None,
+             "plain_ms_per_step": summary[match]["ms_per_step"] if match else None}
+    equal["closure_speedup"] = (equal["plain_ms_per_step"] / equal["closure_ms_per_step"]) if match else None
+    equal["closure_wins"] = bool(match and equal["closure_speedup"] > 1.0)
+    equal["note"] = ("same physical problem and time step: time per step of the closed-loop closure (P = 2 chain) "
+                     "against the cheapest plain HABC order whose maximum reflection error after the wave reaches "
+                     "the faces is at most the closure's")
     line = {"form": "closure", "metric": "reflection error (energy norm, relative)",
             "config": {"train": "%d runs, %d^3 x 6 tets, N = 4, P = 8, shadow P = 2, T = 2.5, every 20 steps, "
                                 "1%% of the face nodes" % (n_runs, args.closure_train_n),
@@ -621,7 +641,7 @@ def run_closure_form(args):
                          "target_var_val": float(np.var(Yva)), "first_batches_mse": float(np.mean(hist[:20])),
                          "last_batches_mse": float(np.mean(hist[-20:])),
                          "closed_loop_rounds": rounds},
-            "errors": summary, "times": times, "error_curves": errs,
+            "errors": summary, "equal_reflection": equal, "times": times, "error_curves": errs,
             "seconds": {"record": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}
     print(json.dumps(line), flush=True)
     if args.closure_weights_out:
@@ -896,7 +916,7 @@ def main():
     state_bytes = sum(a.size * 8 for a in host_in.values())
 
 
-    parts3 = 2 if info["n_tris"] > 0 else 1      # interior cells, then cells with HABC faces
+    parts3 = 2 if (info["n_tris"] > 0 and g.launch["split3"]) else 1   # cells without, then with HABC faces
     launches_per_step = 5 * (parts3 + (info["n_tris"] > 0) + (info["n_lines"] > 0) + (info["n_corners"] > 0)) + 1
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -909,7 +929,8 @@ def main():
                        arithmetic="FP32 state; 3D volume and lift contractions as split-TF32 tcgen05 products "
                                   "(hi*hi + lo*hi + hi*lo, FP32 accumulation; parity <= 1e-5 vs the FP64 oracle)",
                        l2_policy="inputs larger than L2 (state %.0f MB per array)" % (host_in[3].size * 4 / 1e6),
-                       launch={k: g.launch[k] for k in ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1")},
+                       launch={k: g.launch[k] for k in ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1",
+                                                         "split3")},
                        tuner_ms_per_step=list(tune_ms),
                        parallelism="replicas" if world > 1 else "single"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -310,17 +310,21 @@ typedef struct dgh_launch {
     int32_t tile2, tile1, cta3_per_sm;
     int32_t grid3, grid2, grid1, occ3, sms;
     int32_t thr2, thr1;      /* threads per CTA of the 2D / 1D kernels: 32, 64, 128 or 256 */
+    int32_t sm3_div;         /* the persistent 3D grid covers sms / sm3_div SMs (1..16; 1 = all) */
+    int32_t split3;          /* 1: cells without and with HABC faces as two 3D launches per stage, so that
+                                the HABC chain may overlap the first; 0: one 3D launch per stage */
 } dgh_launch;
 
 int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *out);
 
-/* Sets tile2, tile1, cta3_per_sm, thr2 and thr1 (the other fields are ignored).  No
+/* Sets tile2, tile1, cta3_per_sm, thr2, thr1, sm3_div and split3 (the other fields are ignored).  No
  * result changes: every element's arithmetic is the same whatever the shape.
  * DGH_EINVAL if a value is out of range, tile2 * P > thr2, or a tile does not
  * fit in shared memory (the previous shape is kept). */
 int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in);
 
-/* Autotuner: coordinate search over thr2, tile2, thr1, tile1 and cta3_per_sm, each
+/* Autotuner: coordinate search over thr2, tile2, thr1, tile1, cta3_per_sm, split3
+ * (and, for the groups of a batch, which run concurrently, sm3_div), each
  * candidate timed with CUDA events over `steps` whole steps (best of two),
  * kept when at least 1% faster.  The fields, time and step count are saved
  * before and restored after (host copy of the state), so the search changes
@@ -458,11 +462,29 @@ int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n,
 int dgh_mlp_train(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
                   double *final_mse);
 
+/* dgh_closure_fit_homogeneous: the homogeneous form of the closure, fitted
+ * to raw features X [n][6] and targets Y [n] (host): per-feature RMS scales
+ * sigma_i and the target's sigma_y (FP64), directions u = x~ / |x~| with
+ * x~ = x / sigma and relative targets y / (sigma_y |x~|) (rows with zero
+ * features dropped), then dgh_mlp_train on (u, relative target).  w_out
+ * (host, 4680 floats) receives the 4673 network weights, 1/sigma_i and
+ * sigma_y: the layout dgh_closure_set_weights takes for this form.  The
+ * fitted correction sigma_y |x~| MLP(x~ / |x~|) is of degree one in the
+ * fields, as the linear equations require.  loss_hist and final_mse are in
+ * relative-target units.  DGH_EINVAL with fewer than 2 non-zero rows. */
+int dgh_closure_fit_homogeneous(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out,
+                                double *loss_hist, double *final_mse);
+
 /* Trains the closure on the rows this context has recorded
  * (dgh_closure_record): the same training as dgh_mlp_train on their
  * features and targets.  DGH_ESTATE without recording or with fewer than 2
  * rows. */
 int dgh_closure_train(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist, double *final_mse);
+
+/* The same rows fitted in the homogeneous form (dgh_closure_fit_homogeneous;
+ * w_out: 4680 floats). */
+int dgh_closure_train_homogeneous(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
+                                  double *final_mse);
 
 #ifdef __cplusplus
 }

@@ -76,7 +76,8 @@ class _TrainCfg(ctypes.Structure):
 
 class _Launch(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in
-                ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1", "occ3", "sms", "thr2", "thr1")]
+                ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1", "occ3", "sms", "thr2", "thr1",
+                 "sm3_div", "split3")]
 
 
 _lib = None
@@ -152,6 +153,11 @@ def load_library(path=LIB_PATH):
         "dgh_mlp_train": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
                                          ctypes.POINTER(_TrainCfg), ctypes.POINTER(ctypes.c_float), D, D]),
         "dgh_closure_train": (ctypes.c_int, [P, ctypes.POINTER(_TrainCfg), ctypes.POINTER(ctypes.c_float), D, D]),
+        "dgh_closure_train_homogeneous": (ctypes.c_int, [P, ctypes.POINTER(_TrainCfg), ctypes.POINTER(ctypes.c_float),
+                                                         D, D]),
+        "dgh_closure_fit_homogeneous": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                                       ctypes.c_int64, ctypes.POINTER(_TrainCfg),
+                                                       ctypes.POINTER(ctypes.c_float), D, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -200,23 +206,24 @@ def closure_eval(w, X):
     return y
 
 
+def _train_cfg(steps=2000, batch=4096, lr=1e-3, seed=1, beta1=0.9, beta2=0.999, eps=1e-8):
+    return _TrainCfg(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(seed))
+
+
 def closure_fit_homogeneous(X, Y, **train_kw):
-    """Train the homogeneous closure: per-feature RMS scales sigma, directions
-    u = x~ / |x~| (x~ = x / sigma), relative targets v = y / (sigma_y |x~|);
-    returns the 4680 values for Solver.closure_set_weights (rows with zero
-    features are dropped).  Keyword arguments go to mlp_train."""
-    X = np.asarray(X, np.float64)
-    Y = np.asarray(Y, np.float64)
-    sx = np.sqrt(np.mean(X * X, axis=0))
-    sx[sx <= 0] = 1.0
-    sy = float(np.sqrt(np.mean(Y * Y))) or 1.0
-    Xt = X / sx
-    s = np.linalg.norm(Xt, axis=1)
-    keep = s > 0
-    U = Xt[keep] / s[keep, None]
-    V = Y[keep] / (sy * s[keep])
-    w, hist, mse = mlp_train(U, V, **train_kw)
-    return np.concatenate([w, 1.0 / sx, [sy]]).astype(np.float32), hist, mse
+    """Train the homogeneous closure (dgh_closure_fit_homogeneous): returns
+    (the 4680 values for Solver.closure_set_weights, minibatch MSE history,
+    final MSE), the losses in relative-target units.  Keyword arguments as
+    mlp_train."""
+    lib = load_library()
+    X, Y = _f32(X), _f32(Y)
+    cfg = _train_cfg(**train_kw)
+    w = np.empty(MLP_NPARAM + MLP_IN + 1, np.float32)
+    hist = np.empty(max(int(cfg.steps), 1))
+    fin = ctypes.c_double()
+    _lib_check(lib.dgh_closure_fit_homogeneous(_fptr(X), _fptr(Y), X.shape[0], ctypes.byref(cfg), _fptr(w),
+                                               _dptr(hist), ctypes.byref(fin)))
+    return w, hist[:int(cfg.steps)], fin.value
 
 
 def mlp_loss_grad(w, X, Y):
@@ -511,15 +518,17 @@ class Solver:
         self._check(self._lib.dgh_closure_record(self._h, int(shadow_order), int(every), float(fraction),
                                                  int(max_samples), int(seed)))
 
-    def closure_train(self, steps=2000, batch=4096, lr=1e-3, seed=1, beta1=0.9, beta2=0.999, eps=1e-8):
-        """Train the closure on this solver's recorded rows (dgh_closure_train);
-        returns (weights, minibatch MSE history, final MSE) like mlp_train."""
-        cfg = _TrainCfg(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(seed))
-        w = np.empty(MLP_NPARAM, np.float32)
-        hist = np.empty(max(int(steps), 1))
+    def closure_train(self, homogeneous=False, **train_kw):
+        """Train the closure on this solver's recorded rows (dgh_closure_train,
+        or dgh_closure_train_homogeneous); returns (weights, minibatch MSE
+        history, final MSE) like mlp_train / closure_fit_homogeneous."""
+        cfg = _train_cfg(**train_kw)
+        w = np.empty(MLP_NPARAM + (MLP_IN + 1 if homogeneous else 0), np.float32)
+        hist = np.empty(max(int(cfg.steps), 1))
         fin = ctypes.c_double()
-        self._check(self._lib.dgh_closure_train(self._h, ctypes.byref(cfg), _fptr(w), _dptr(hist), ctypes.byref(fin)))
-        return w, hist[:int(steps)], fin.value
+        fn = self._lib.dgh_closure_train_homogeneous if homogeneous else self._lib.dgh_closure_train
+        self._check(fn(self._h, ctypes.byref(cfg), _fptr(w), _dptr(hist), ctypes.byref(fin)))
+        return w, hist[:int(cfg.steps)], fin.value
 
     def closure_samples(self, max_rows=None):
         """Recorded rows [n][7]: 6 features and the target.  Open-loop rows
@@ -540,7 +549,7 @@ class Solver:
         self._check(self._lib.dgh_get_launch(self._h, ctypes.byref(o)))
         return {f: getattr(o, f) for f, _ in _Launch._fields_}
 
-    def set_launch(self, tile2=None, tile1=None, cta3_per_sm=None, thr2=None, thr1=None):
+    def set_launch(self, tile2=None, tile1=None, cta3_per_sm=None, thr2=None, thr1=None, sm3_div=None, split3=None):
         cur = self.launch
         o = _Launch()
         o.tile2 = cur["tile2"] if tile2 is None else int(tile2)
@@ -548,6 +557,8 @@ class Solver:
         o.cta3_per_sm = cur["cta3_per_sm"] if cta3_per_sm is None else int(cta3_per_sm)
         o.thr2 = cur["thr2"] if thr2 is None else int(thr2)
         o.thr1 = cur["thr1"] if thr1 is None else int(thr1)
+        o.sm3_div = cur["sm3_div"] if sm3_div is None else int(sm3_div)
+        o.split3 = cur["split3"] if split3 is None else int(split3)
         self._check(self._lib.dgh_set_launch(self._h, ctypes.byref(o)))
 
     def tune(self, steps=5, cache=None):
@@ -559,7 +570,7 @@ class Solver:
         if cache:
             hit = tune_cache_load(cache).get(key)
             if hit is not None:
-                self.set_launch(**{k: hit[k] for k in TUNABLE})
+                self.set_launch(**{k: hit[k] for k in TUNABLE if k in hit})
                 return hit["ms_before"], hit["ms_after"]
         a, b = ctypes.c_double(), ctypes.c_double()
         self._check(self._lib.dgh_tune(self._h, int(steps), ctypes.byref(a), ctypes.byref(b)))
@@ -569,7 +580,7 @@ class Solver:
         return a.value, b.value
 
 
-TUNABLE = ("tile2", "tile1", "cta3_per_sm", "thr2", "thr1")
+TUNABLE = ("tile2", "tile1", "cta3_per_sm", "thr2", "thr1", "sm3_div", "split3")
 
 
 def tune_cache_key(info, precision):

@@ -135,10 +135,12 @@ struct dgh_ctx {
     // launch shapes
     int grid3 = 1, grid2 = 1, grid1 = 1, tile2 = 1, tile1 = 1, occ3 = 0, sms = 1;
     int cta3_per_sm = 0;              // tunable: persistent 3D CTAs per SM (0 = occupancy limit)
+    int sm3_div = 1;                  // tunable: the 3D grid covers sms / sm3_div SMs (concurrent batch groups)
+    int split3 = 1;                   // tunable: 1 = interior and HABC-face cells as two 3D launches per stage
     int thr2 = 128, thr1 = 256;       // tunable: threads per CTA of the 2D / 1D kernels
     int precision = DGH_PREC_FP32;    // arithmetic of the 3D contractions (DGH_PREC_*)
     uint8_t *tcops = nullptr;         // tensor-core operand images of D_r, D_s, D_t, LIFT (hi, then lo)
-    unsigned long long *tile_ctr = nullptr;   // [11] block counters of the 3D launches of a step
+    unsigned long long *tile_ctr = nullptr;   // [16] block counters of the 3D launches of a step
     size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
     int smem_optin = 0;
     // learned closure (inference on this context's chain)
@@ -458,7 +460,8 @@ struct Launch3 {
         sc.c_dt = kRkC[stage] * c->dt;
         sc.time = c->d_time;
         Args3 A = args3(c, cur);
-        A.tile_ctr = c->tile_ctr + (part == 0 ? 10 : stage * 2 + (part - 1));
+        // counters: parts 1, 2 of stage s at 2s, 2s+1, part 3 at 10+s (zeroed once per step), part 0 at 15
+        A.tile_ctr = c->tile_ctr + (part == 0 ? 15 : part == 3 ? 10 + stage : stage * 2 + (part - 1));
         if (part == 0) cudaMemsetAsync(A.tile_ctr, 0, sizeof(unsigned long long), st);
         if (part == 1) A.blk_end = c->Ki32;
         if (part == 2) A.blk_begin = c->Ki32;
@@ -515,7 +518,12 @@ struct Launch2 {
             k2d_stage<N, true><<<grid, thr, smem, st>>>(A, sc, tile);
         else
             k2d_stage<N, false><<<grid, thr, smem, st>>>(A, sc, tile);
-        if (!shadow && c->cl_on) {   // learned closure: exterior state 2 (r^- + MLP(features))
+        // Learned closure: exterior state 2 (r^- + MLP(features)) by its own
+        // kernel, at full occupancy.  Evaluated inside the face kernel's
+        // boundary loop instead, the MLP (4.5 k multiply-adds per node, 7.5
+        // nodes per thread of that kernel at P = 2) ran at 8 warps per SM and
+        // made the closed step 1.9 times as long as the plain one.
+        if (!shadow && c->cl_on) {
             const int64_t rows = c->T * c->Np2;
             const int blocks = (int)std::min<int64_t>((rows + 255) / 256, int64_t(4) * c->sms);
             k_closure_apply<<<blocks, 256, 0, st>>>(c->cl_w, c->cl_homog ? c->cl_w + MLP_NPARAM : nullptr,
@@ -658,8 +666,9 @@ struct Shapes {
         if (P && c->tile2 * P > c->thr2) return DGH_EINVAL;   // one thread per (triangle, set)
         const int sms = c->sms;
         const int per_sm = c->cta3_per_sm > 0 ? std::min(c->cta3_per_sm, std::max(c->occ3, 1)) : std::max(c->occ3, 1);
+        const int sms3 = std::max(1, c->sms / std::max(c->sm3_div, 1));
         const int64_t tiles3 = kern3_of(c->precision, N) == K3_CUDA ? c->K32 : (c->K32 + 3) / 4;
-        c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)per_sm * sms));
+        c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)per_sm * sms3));
         int nb2 = 0, nb1 = 0;
         if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, c->thr2, c->smem2);
         if (c->L) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k1d_stage<N, true>, c->thr1, c->smem1);
@@ -702,12 +711,18 @@ int enqueue_step(dgh_ctx *c, int cur, bool overlap, cudaStream_t ms = nullptr) {
     if (!ms) ms = c->stream;
     overlap = overlap && !c->no_overlap;
     cudaStream_t ss = overlap ? c->side : ms;
-    cudaMemsetAsync(c->tile_ctr, 0, 10 * sizeof(unsigned long long), ms);
+    cudaMemsetAsync(c->tile_ctr, 0, 15 * sizeof(unsigned long long), ms);
+    // split3 = 0: one 3D launch per stage over all cells (after the 2D kernel of
+    // the previous stage), no tail of a separate launch of the HABC-face cells
+    const bool split = overlap && c->split3 != 0 && c->T > 0;
     for (int s = 0; s < 5; ++s) {
-        int rc = dispatchN<Launch3>(c->N, c, cur, s, true, 1, ms);
-        if (rc) return rc;
+        int rc = DGH_OK;
+        if (split) {
+            rc = dispatchN<Launch3>(c->N, c, cur, s, true, 1, ms);
+            if (rc) return rc;
+        }
         if (overlap && s > 0) cudaStreamWaitEvent(ms, c->ev2d[s - 1], 0);
-        rc = dispatchN<Launch3>(c->N, c, cur, s, true, 2, ms);
+        rc = dispatchN<Launch3>(c->N, c, cur, s, true, split ? 2 : 3, ms);
         if (rc) return rc;
         if (overlap) {
             cudaEventRecord(c->ev3d[s], ms);
@@ -1329,7 +1344,7 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
         if ((rc = upload(ctx, ctx->corner, cor)) || (rc = upload(ctx, ctx->cornerZ, cz))) return fail(rc, "");
     }
     // ---------------------------------------------------------------- misc
-    if ((rc = dalloc(ctx, ctx->tile_ctr, 11)) || (rc = dalloc(ctx, ctx->d_time, 1)) || (rc = dalloc(ctx, ctx->d_step, 1)) ||
+    if ((rc = dalloc(ctx, ctx->tile_ctr, 16)) || (rc = dalloc(ctx, ctx->d_time, 1)) || (rc = dalloc(ctx, ctx->d_step, 1)) ||
         (rc = dalloc(ctx, ctx->srcvec, size_t(MAXSRC) * Np)) || (rc = dalloc(ctx, ctx->d_energy, 1)))
         return fail(rc, "");
     ctx->energy_blocks = 2 * 148;
@@ -1588,6 +1603,8 @@ int dgh_set_material(dgh_ctx *ctx, const double *c, const double *rho, size_t co
         n->tile2 = ctx->tile2;
         n->tile1 = ctx->tile1;
         n->cta3_per_sm = ctx->cta3_per_sm;
+        n->sm3_div = ctx->sm3_div;
+        n->split3 = ctx->split3;
         n->thr2 = ctx->thr2;
         n->thr1 = ctx->thr1;
         if (dispatchN<Shapes>(n->N, n) != DGH_OK) return give_up(DGH_EINVAL);
@@ -1996,6 +2013,8 @@ int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *o) {
         o->sms = ctx->sms;
         o->thr2 = ctx->thr2;
         o->thr1 = ctx->thr1;
+        o->sm3_div = ctx->sm3_div;
+        o->split3 = ctx->split3;
         return DGH_OK;
     });
 }
@@ -2003,22 +2022,30 @@ int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *o) {
 int dgh_set_launch(dgh_ctx *ctx, const dgh_launch *in) {
     return dgh_guarded(err_slot(ctx), [&]() -> int {
         auto thr_ok = [](int t) { return t == 32 || t == 64 || t == 128 || t == 256; };
-        if (!ctx || !in || in->tile2 < 1 || in->tile1 < 1 || in->cta3_per_sm < 0 || !thr_ok(in->thr2) || !thr_ok(in->thr1)) {
-            if (ctx) ctx->err = "tile2, tile1 must be >= 1, cta3_per_sm >= 0, thr2 / thr1 one of 32, 64, 128, 256";
+        if (!ctx || !in || in->tile2 < 1 || in->tile1 < 1 || in->cta3_per_sm < 0 || !thr_ok(in->thr2) ||
+            !thr_ok(in->thr1) || in->sm3_div < 1 || in->sm3_div > 16 || (in->split3 != 0 && in->split3 != 1)) {
+            if (ctx)
+                ctx->err = "tile2, tile1 must be >= 1, cta3_per_sm >= 0, thr2 / thr1 one of 32, 64, 128, 256, "
+                           "sm3_div in 1..16, split3 0 or 1";
             return DGH_EINVAL;
         }
         const int t2 = ctx->tile2, t1 = ctx->tile1, c3 = ctx->cta3_per_sm, h2 = ctx->thr2, h1 = ctx->thr1;
+        const int d3 = ctx->sm3_div, s3 = ctx->split3;
         ctx->tile2 = in->tile2;
         ctx->tile1 = in->tile1;
         ctx->cta3_per_sm = in->cta3_per_sm;
         ctx->thr2 = in->thr2;
         ctx->thr1 = in->thr1;
+        ctx->sm3_div = in->sm3_div;
+        ctx->split3 = in->split3;
         if (dispatchN<Shapes>(ctx->N, ctx) != DGH_OK) {
             ctx->tile2 = t2;
             ctx->tile1 = t1;
             ctx->cta3_per_sm = c3;
             ctx->thr2 = h2;
             ctx->thr1 = h1;
+            ctx->sm3_div = d3;
+            ctx->split3 = s3;
             dispatchN<Shapes>(ctx->N, ctx);
             ctx->err = "launch shape does not fit (shared memory, or tile2 * P > thr2)";
             return DGH_EINVAL;
@@ -2086,9 +2113,9 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
     if (rc) return rc;
     if (ms_before) *ms_before = best;
     for (dgh_ctx *c : cs) {
-        for (int param = 0; param < 5 && rc == DGH_OK; ++param) {
+        for (int param = 0; param < 7 && rc == DGH_OK; ++param) {
             int *slot = param == 0 ? &c->thr2 : param == 1 ? &c->tile2 : param == 2 ? &c->thr1 : param == 3 ? &c->tile1
-                                                                                                    : &c->cta3_per_sm;
+                        : param == 4 ? &c->cta3_per_sm : param == 5 ? &c->sm3_div : &c->split3;
             std::vector<int> cand;
             if ((param == 0 && c->T > 0) || (param == 2 && c->L > 0))
                 for (int v = 32; v <= 256; v *= 2) cand.push_back(v);
@@ -2098,6 +2125,9 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
                 for (int v = 1; v <= 32 && v <= c->L; v *= 2) cand.push_back(v);
             if (param == 4)
                 for (int v = 0; v <= c->occ3; ++v) cand.push_back(v);
+            if (param == 5 && cs.size() > 1)   // SM share of the 3D grid: only concurrent contexts can use the rest
+                for (int v = 1; v <= 4; v *= 2) cand.push_back(v);
+            if (param == 6 && c->T > 0 && !c->no_overlap) cand = {1, 0};
             if (param == 1 && c->T > 0) cand.push_back(k2d_tile_max(c->P, c->thr2));
             int keep = *slot, keep_tile2 = c->tile2;
             for (int v : cand) {
@@ -2738,7 +2768,11 @@ int dgh_closure_samples(dgh_ctx *ctx, float *out, int64_t max_rows, int64_t *cou
     });
 }
 
-int dgh_closure_train(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist, double *final_mse) {
+}  // extern "C"
+
+namespace {
+int closure_train_rows(dgh_ctx *ctx, bool homogeneous, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
+                       double *final_mse) {
     return dgh_guarded(err_slot(ctx), [&]() -> int {
         if (!ctx || !cfg || !w_out) return DGH_EINVAL;
         int64_t n = 0;
@@ -2755,10 +2789,23 @@ int dgh_closure_train(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, doub
             for (int i = 0; i < MLP_IN; ++i) X[size_t(r) * MLP_IN + i] = rows[size_t(r) * SAMPLE_W + i];
             Y[size_t(r)] = rows[size_t(r) * SAMPLE_W + MLP_IN];
         }
-        rc = dgh_mlp_train(X.data(), Y.data(), n, cfg, w_out, loss_hist, final_mse);
+        rc = homogeneous ? dgh_closure_fit_homogeneous(X.data(), Y.data(), n, cfg, w_out, loss_hist, final_mse)
+                         : dgh_mlp_train(X.data(), Y.data(), n, cfg, w_out, loss_hist, final_mse);
         if (rc) ctx->err = dgh_last_error(nullptr);
         return rc;
     });
+}
+}  // namespace
+
+extern "C" {
+
+int dgh_closure_train(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist, double *final_mse) {
+    return closure_train_rows(ctx, false, cfg, w_out, loss_hist, final_mse);
+}
+
+int dgh_closure_train_homogeneous(dgh_ctx *ctx, const dgh_train_cfg *cfg, float *w_out, double *loss_hist,
+                                  double *final_mse) {
+    return closure_train_rows(ctx, true, cfg, w_out, loss_hist, final_mse);
 }
 
 }  // extern "C"
@@ -2848,6 +2895,48 @@ int dgh_mlp_loss_grad(const float *w, const float *X, const float *Y, int64_t n,
         cudaMemcpy(grad, dg, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
         cudaError_t e = cudaMemcpy(loss, dl, sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return mlp_fail(std::string("mlp loss/grad: ") + cudaGetErrorString(e), DGH_ECUDA);
+        return DGH_OK;
+    });
+}
+
+int dgh_closure_fit_homogeneous(const float *X, const float *Y, int64_t n, const dgh_train_cfg *cfg, float *w_out,
+                                double *loss_hist, double *final_mse) {
+    return dgh_guarded(nullptr, [&]() -> int {
+        if (!X || !Y || n < 2 || !cfg || !w_out) return mlp_fail("closure fit: invalid arguments", DGH_EINVAL);
+        // per-feature RMS scales sigma_i and the target's sigma_y (FP64)
+        double sx[MLP_IN] = {0}, sy = 0.0;
+        for (int64_t r = 0; r < n; ++r) {
+            for (int i = 0; i < MLP_IN; ++i) sx[i] += double(X[r * MLP_IN + i]) * X[r * MLP_IN + i];
+            sy += double(Y[r]) * Y[r];
+        }
+        for (int i = 0; i < MLP_IN; ++i) {
+            sx[i] = std::sqrt(sx[i] / double(n));
+            if (!(sx[i] > 0.0)) sx[i] = 1.0;
+        }
+        sy = std::sqrt(sy / double(n));
+        if (!(sy > 0.0)) sy = 1.0;
+        // directions u = x~ / |x~| (x~ = x / sigma) and relative targets y / (sigma_y |x~|);
+        // rows with zero features carry no direction and are dropped
+        std::vector<float> U, V;
+        U.reserve(size_t(n) * MLP_IN);
+        V.reserve(size_t(n));
+        for (int64_t r = 0; r < n; ++r) {
+            double xt[MLP_IN], s2 = 0.0;
+            for (int i = 0; i < MLP_IN; ++i) {
+                xt[i] = X[r * MLP_IN + i] / sx[i];
+                s2 += xt[i] * xt[i];
+            }
+            const double sn = std::sqrt(s2);
+            if (!(sn > 0.0)) continue;
+            for (int i = 0; i < MLP_IN; ++i) U.push_back(float(xt[i] / sn));
+            V.push_back(float(Y[r] / (sy * sn)));
+        }
+        const int64_t m = int64_t(V.size());
+        if (m < 2) return mlp_fail("closure fit: fewer than 2 rows with non-zero features", DGH_EINVAL);
+        int rc = dgh_mlp_train(U.data(), V.data(), m, cfg, w_out, loss_hist, final_mse);
+        if (rc) return rc;
+        for (int i = 0; i < MLP_IN; ++i) w_out[MLP_NPARAM + i] = float(1.0 / sx[i]);
+        w_out[MLP_NPARAM + MLP_IN] = float(sy);
         return DGH_OK;
     });
 }

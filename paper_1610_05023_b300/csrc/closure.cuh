@@ -67,6 +67,31 @@ __global__ void k_mlp_zero(const float *wts, float *y0) {
     }
 }
 
+// The correction y of one feature row x (overwritten): MLP(x) - y0 with y0 =
+// MLP(0), or, with the homogeneous form (ssc = 1/sigma of the 6 features,
+// then sigma_y), sigma_y |x~| MLP(x~ / |x~|), x~ = x / sigma, 0 at x~ = 0.
+// w: the weights in shared memory.
+__device__ __forceinline__ float closure_y(const float *w, const float *ssc, bool homog, float y0,
+                                           float (&x)[MLP_IN]) {
+    float amp = 1.f, off = y0;   // y = amp * MLP(x') - off
+    if (homog) {
+        float s2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < MLP_IN; ++i) {
+            x[i] *= ssc[i];
+            s2 += x[i] * x[i];
+        }
+        const float sn = sqrtf(s2);
+        const float inv = sn > 1e-30f ? 1.0f / sn : 0.f;
+#pragma unroll
+        for (int i = 0; i < MLP_IN; ++i) x[i] *= inv;
+        amp = sn > 1e-30f ? ssc[MLP_IN] * sn : 0.f;
+        off = 0.f;
+    }
+    const float m = mlp_forward(w, x);
+    return amp == 0.f ? 0.f : amp * m - off;
+}
+
 // Inference: the correction y = MLP(feat) - MLP(0) for n feature rows (the
 // fields enter linearly, so no fields must give no correction; MLP(0) comes
 // from k_mlp_zero, the same code with the same weights, so y(0) = 0 exactly).
@@ -90,23 +115,7 @@ __global__ void __launch_bounds__(256) k_closure_apply(const float *wts, const f
         float x[MLP_IN];
 #pragma unroll
         for (int i = 0; i < MLP_IN; ++i) x[i] = feat[r * MLP_IN + i];
-        float amp = 1.f, off = y0;   // y = amp * MLP(x') - off
-        if (scales) {
-            float s2 = 0.f;
-#pragma unroll
-            for (int i = 0; i < MLP_IN; ++i) {
-                x[i] *= ssc[i];
-                s2 += x[i] * x[i];
-            }
-            const float sn = sqrtf(s2);
-            const float inv = sn > 1e-30f ? 1.0f / sn : 0.f;
-#pragma unroll
-            for (int i = 0; i < MLP_IN; ++i) x[i] *= inv;
-            amp = sn > 1e-30f ? ssc[MLP_IN] * sn : 0.f;
-            off = 0.f;
-        }
-        const float m = mlp_forward(sw, x);
-        const float y = amp == 0.f ? 0.f : amp * m - off;
+        const float y = closure_y(sw, ssc, scales != nullptr, y0, x);
         if (y_out) y_out[r] = y;
         if (tin3) {
             const int64_t t = r / np2;

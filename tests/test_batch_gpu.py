@@ -130,9 +130,10 @@ def test_solver_launch_shape_and_tune_change_no_result():
         g = dgh.Solver(VX, EToV, 3, 3)
         g.init_gaussian([0.1, -0.1, 0.2], 0.3)
         if mode == "shape":
-            g.set_launch(tile2=1, tile1=3, cta3_per_sm=1, thr2=32, thr1=64)
+            g.set_launch(tile2=1, tile1=3, cta3_per_sm=1, thr2=32, thr1=64, sm3_div=4, split3=0)
             L = g.launch
-            assert (L["tile2"], L["tile1"], L["cta3_per_sm"], L["thr2"], L["thr1"]) == (1, 3, 1, 32, 64)
+            assert ((L["tile2"], L["tile1"], L["cta3_per_sm"], L["thr2"], L["thr1"], L["sm3_div"], L["split3"])
+                    == (1, 3, 1, 32, 64, 4, 0))
         if mode == "tuned":
             g.tune(steps=2)
             assert g.info["step_count"] == 0
@@ -154,6 +155,10 @@ def test_set_launch_rejects_bad_shapes():
         g.set_launch(tile2=100000)   # shared memory of the 2D tile does not fit
     with pytest.raises(dgh.DghError):
         g.set_launch(thr2=48)
+    with pytest.raises(dgh.DghError):
+        g.set_launch(sm3_div=0)
+    with pytest.raises(dgh.DghError):
+        g.set_launch(split3=2)
     with pytest.raises(dgh.DghError):
         g.set_launch(tile2=17, thr2=32)   # one thread per (triangle, set): 17 * 2 > 32
     assert g.launch == before

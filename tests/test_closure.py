@@ -178,6 +178,40 @@ def test_closure_train_on_recorded_rows_equals_mlp_train():
     fresh = _solver(2)
     with pytest.raises(dgh.DghError):
         fresh.closure_train(steps=5)               # nothing recorded
+    # the homogeneous form on the same rows: the context-free fit, exactly
+    wh1, hh1, fh1 = g.closure_train(homogeneous=True, steps=50, batch=256, lr=1e-3, seed=5)
+    wh2, hh2, fh2 = dgh.closure_fit_homogeneous(S[:, :6], S[:, 6], steps=50, batch=256, lr=1e-3, seed=5)
+    assert wh1.shape == (C.NPARAM + C.NIN + 1,)
+    assert np.array_equal(wh1, wh2) and np.array_equal(hh1, hh2) and fh1 == fh2
+
+
+@pytest.mark.gpu
+def test_homogeneous_fit_follows_its_definition():
+    """dgh_closure_fit_homogeneous against its definition restated in FP64
+    numpy: per-feature RMS scales sigma_i and sigma_y, then dgh_mlp_train on
+    the directions x~ / |x~| (x~ = x / sigma) and relative targets
+    y / (sigma_y |x~|) of the rows with non-zero features.  The scales agree
+    to FP32 rounding; the network equals mlp_train's on those inputs up to
+    the last-bit differences that the two summation orders of sigma leave in
+    the inputs."""
+    X, Y = _data(21, 3000)
+    X = X * np.array([1.0, 3.0, 0.5, 2.0, 0.1, 7.0])
+    X[::97] = 0.0                                  # rows without a direction are dropped
+    kw = dict(steps=40, batch=512, lr=1e-3, seed=9)
+    wh, _, _ = dgh.closure_fit_homogeneous(X, Y, **kw)
+    Xd, Yd = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+    sx = np.sqrt(np.mean(Xd * Xd, axis=0))
+    sy = np.sqrt(np.mean(Yd * Yd))
+    assert np.allclose(wh[C.NPARAM:C.NPARAM + C.NIN], 1.0 / sx, rtol=1e-6)
+    assert abs(wh[-1] - sy) <= 1e-6 * sy
+    Xt = Xd / sx
+    s = np.linalg.norm(Xt, axis=1)
+    keep = s > 0
+    assert keep.sum() == len(X) - len(X[::97])
+    w2, _, _ = dgh.mlp_train(Xt[keep] / s[keep, None], Yd[keep] / (sy * s[keep]), **kw)
+    assert np.abs(wh[:C.NPARAM] - w2).max() <= 1e-4 * np.abs(w2).max()
+    with pytest.raises(dgh.DghError):
+        dgh.closure_fit_homogeneous(np.zeros((10, 6)), np.ones(10), steps=2)
 
 
 @pytest.mark.gpu
