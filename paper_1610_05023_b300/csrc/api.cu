@@ -2112,6 +2112,30 @@ int tune_contexts(const std::vector<dgh_ctx *> &cs, cudaStream_t st, int steps, 
     int rc = time_per_step(st, steps, run, best, err);
     if (rc) return rc;
     if (ms_before) *ms_before = best;
+    // concurrent contexts (the groups of a batch): first the SM share of every
+    // group's 3D grid at once, since one group alone leaving SMs free gains
+    // nothing while the others still take all of them
+    if (cs.size() > 1) {
+        int keep = cs[0]->sm3_div;
+        for (int v = 2; v <= 8 && rc == DGH_OK; v *= 2) {
+            for (dgh_ctx *c : cs) {
+                c->sm3_div = v;
+                dispatchN<Shapes>(c->N, c);
+            }
+            invalidate();
+            double ms = 0.0;
+            if ((rc = time_per_step(st, steps, run, ms, err))) break;
+            if (ms < 0.99 * best) {
+                best = ms;
+                keep = v;
+            }
+        }
+        for (dgh_ctx *c : cs) {
+            c->sm3_div = keep;
+            dispatchN<Shapes>(c->N, c);
+        }
+        invalidate();
+    }
     for (dgh_ctx *c : cs) {
         for (int param = 0; param < 7 && rc == DGH_OK; ++param) {
             int *slot = param == 0 ? &c->thr2 : param == 1 ? &c->tile2 : param == 2 ? &c->thr1 : param == 3 ? &c->tile1
