@@ -41,3 +41,45 @@ def test_noalloc_energy_rejects_null_output():
     with pytest.raises(dgh.DghError):
         g.energy_noalloc(0)
     g.close()
+
+
+def test_noalloc_energy_on_another_stream_follows_the_steps():
+    """A caller stream other than the solver's is ordered after the work
+    already enqueued on the solver's stream: called right after an
+    asynchronous step(40), with no synchronisation, it returns the energy of
+    the advanced fields."""
+    import torch
+    VX, EToV = W.kuhn_mesh(6, 1.0, 0.02, seed=32)
+    g = dgh.Solver(VX, EToV, 4, 3)
+    g.init_gaussian([0.2, 0.1, -0.1], 0.2)
+    e0 = g.energy()
+    other = torch.cuda.Stream()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.step(40)                                           # asynchronous on the solver's stream
+    g.energy_noalloc(out.data_ptr(), other)
+    other.synchronize()
+    got = float(out[0].item())
+    ref = g.energy()                                     # synchronises the solver's stream
+    assert ref != e0
+    assert abs(got - ref) <= TOL * ref, (got, ref, e0)
+    g.close()
+
+
+def test_noalloc_energy_rejects_a_mesh_above_its_scratch_limit():
+    """The static scratch holds 65,536 partial sums of 64 cells: a mesh of
+    89^3 x 6 = 4,229,814 cells (N = 1, no HABC) is above the 4,194,304-cell
+    limit, and the call returns DGH_EINVAL without touching the output; the
+    allocating energy still works."""
+    import torch
+    VX, EToV = W.kuhn_mesh(89, 1.0, 0.0, seed=33)
+    assert EToV.shape[0] > 4194304
+    g = dgh.Solver(VX, EToV, 1, 0)
+    g.init_gaussian([0.0, 0.0, 0.0], 0.3)
+    out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(dgh.DghError) as e:
+        g.energy_noalloc(out.data_ptr())
+    assert e.value.code == dgh.DGH_EINVAL
+    torch.cuda.synchronize()
+    assert float(out[0].item()) == -1.0
+    assert g.energy() > 0.0
+    g.close()
