@@ -889,7 +889,9 @@ def main():
     tc_ach = tc_flops / (kt["k3d"] * 1e-3) / 1e12
     tf32_peak = bf16_peak() * (1.1 / 2.25)    # measured BF16 x the nominal TF32 / BF16 ratio
     sha = kernel_source_sha()
-    traffic = K3D_TRAFFIC["bytes"] if (args.n == 48 and K3D_TRAFFIC["bytes"] and sha == K3D_TRAFFIC["source_sha256"]) else None
+    tf32 = g.launch["kern3"] == 1          # the 3D kernel of the FP32 path at this size
+    traffic = (K3D_TRAFFIC["bytes"] if (args.n == 48 and tf32 and K3D_TRAFFIC["bytes"] and
+                                        sha == K3D_TRAFFIC["source_sha256"]) else None)
 
     # the same workload with the FP32 CUDA-core 3D kernel (the fallback variant)
     variants, form = None, None
@@ -926,11 +928,13 @@ def main():
                                                               "mesh": "%d^3 hex x 6 Kuhn tets" % args.n}),
                        ndof=ndof, n_cells=K, n_tris=info["n_tris"], n_lines=info["n_lines"],
                        n_corners=info["n_corners"], dt=info["dt"],
-                       arithmetic="FP32 state; 3D volume and lift contractions as split-TF32 tcgen05 products "
-                                  "(hi*hi + lo*hi + hi*lo, FP32 accumulation; parity <= 1e-5 vs the FP64 oracle)",
+                       arithmetic=("FP32 state; 3D volume and lift contractions as split-TF32 tcgen05 products "
+                                   "(hi*hi + lo*hi + hi*lo, FP32 accumulation; parity <= 1e-5 vs the FP64 oracle)"
+                                   if g.launch["kern3"] == 1 else
+                                   "FP32 state and FP32 CUDA-core contractions (parity <= 1e-5 vs the FP64 oracle)"),
                        l2_policy="inputs larger than L2 (state %.0f MB per array)" % (host_in[3].size * 4 / 1e6),
                        launch={k: g.launch[k] for k in ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1",
-                                                         "split3")},
+                                                         "split3", "kern3")},
                        tuner_ms_per_step=list(tune_ms),
                        parallelism="replicas" if world > 1 else "single"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -940,10 +944,10 @@ def main():
                                         "one stage, captured %s (kernel source sha256 %s); null when the source "
                                         "has changed since" % (K3D_TRAFFIC["kernel"], K3D_TRAFFIC["captured"],
                                                                K3D_TRAFFIC["source_sha256"])),
-                     "kernel": "k3d_tf32<4>", "kernel_source_sha256": sha,
+                     "kernel": "k3d_tf32<4>" if tf32 else "k3d_stage<4>", "kernel_source_sha256": sha,
                      "tensor": {"achieved_tflops": tc_ach, "mma_flops_per_stage": tc_flops,
                                 "peak_tflops": tf32_peak, "peak_kind": "measured bf16 x nominal tf32/bf16 ratio",
-                                "frac": tc_ach / tf32_peak},
+                                "frac": tc_ach / tf32_peak} if tf32 else None,
                      "peak_kind": peak_kind, "bytes_per_tet": bytes_per_tet,
                      "launch_ms": kt["k3d"]},
         "kernel_ms": kt,

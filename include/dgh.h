@@ -79,13 +79,16 @@ extern "C" {
  * 2D/1D/0D levels) is FP32 in every mode.  The tensor-core modes run the
  * products on tcgen05 tensor cores with FP32 accumulation in tensor memory.
  * DGH_PREC_FP32 is the plain path held to the FP32 contract (relative L2
- * error <= 1e-5 per field against the FP64 oracle): for N <= 4 it runs the
- * split-TF32 tensor-core kernel (each operand to 2^-22, three products, a
- * few units of FP32 rounding), for N >= 5 the FP32 CUDA-core kernel.
- * DGH_PREC_FP32_CUDA forces the CUDA-core kernel at every order (packed
- * FP32 FMAs, no tensor cores); DGH_PREC_SPLIT_TF32 forces the split-TF32
- * kernel (N <= 4 only: DGH_EUNSUPPORTED otherwise). */
-#define DGH_PREC_FP32        0   /* FP32 contract: split TF32 (N <= 4), else CUDA cores */
+ * error <= 1e-5 per field against the FP64 oracle) and picks the faster of
+ * its two kernels: at N = 4 with at least 65,536 cells the split-TF32
+ * tensor-core kernel (each operand to 2^-22, three products, a few units of
+ * FP32 rounding), otherwise the FP32 CUDA-core kernel (measured faster at
+ * N = 1, 2, 3 at every size, and at N = 4 on small meshes; N >= 5 has no
+ * split-TF32 kernel).  DGH_PREC_FP32_CUDA forces the CUDA-core kernel at
+ * every order and size (packed FP32 FMAs, no tensor cores);
+ * DGH_PREC_SPLIT_TF32 forces the split-TF32 kernel (N <= 4 only:
+ * DGH_EUNSUPPORTED otherwise). */
+#define DGH_PREC_FP32        0   /* FP32 contract: split TF32 (N = 4, >= 65,536 cells), else CUDA cores */
 #define DGH_PREC_BF16_TC     1   /* BF16 operands, one product                    */
 #define DGH_PREC_FP16_TC     2   /* FP16 operands, one product                    */
 #define DGH_PREC_SPLIT_BF16  3   /* x = hi + lo in BF16, hi*hi + lo*hi + hi*lo    */
@@ -313,6 +316,7 @@ typedef struct dgh_launch {
     int32_t sm3_div;         /* the persistent 3D grid covers sms / sm3_div SMs (1..16; 1 = all) */
     int32_t split3;          /* 1: cells without and with HABC faces as two 3D launches per stage, so that
                                 the HABC chain may overlap the first; 0: one 3D launch per stage */
+    int32_t kern3;           /* read only: the 3D kernel, 0 FP32 CUDA cores, 1 split TF32, 2 BF16/FP16 */
 } dgh_launch;
 
 int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *out);

@@ -23,7 +23,7 @@ PREC_BF16_TC = 1
 PREC_FP16_TC = 2
 PREC_SPLIT_BF16 = 3
 PREC_FP32_CUDA = 4     # FP32 CUDA-core contractions at every order
-PREC_SPLIT_TF32 = 5    # split-TF32 tensor-core contractions (N <= 4)
+PREC_SPLIT_TF32 = 5    # split-TF32 tensor-core contractions (N <= 4; PREC_FP32's kernel at N = 4 on large meshes)
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ETIMEOUT", -6: "ESTATE",
            -7: "EUNSUPPORTED", -8: "EBOUNDS"}
@@ -77,7 +77,7 @@ class _TrainCfg(ctypes.Structure):
 class _Launch(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in
                 ("tile2", "tile1", "cta3_per_sm", "grid3", "grid2", "grid1", "occ3", "sms", "thr2", "thr1",
-                 "sm3_div", "split3")]
+                 "sm3_div", "split3", "kern3")]
 
 
 _lib = None
@@ -311,9 +311,10 @@ class Solver:
     BC_DIRICHLET for -x,+x,-y,+y,-z,+z), c and rho per cell (or scalars),
     dt > 0 fixed step (else cfl * the min-over-cells rule), stream a
     torch.cuda.Stream, an integer cudaStream_t or None, precision one of
-    PREC_FP32 (the FP32 contract: split-TF32 tensor-core products for
-    N <= 4, FP32 CUDA cores above), PREC_FP32_CUDA (FP32 CUDA cores at every
-    order), PREC_SPLIT_TF32 (split TF32, N <= 4), PREC_BF16_TC,
+    PREC_FP32 (the FP32 contract, with the faster of its two kernels:
+    split-TF32 tensor-core products at N = 4 with >= 65,536 cells, FP32 CUDA
+    cores otherwise), PREC_FP32_CUDA (FP32 CUDA cores at every order),
+    PREC_SPLIT_TF32 (split TF32, N <= 4), PREC_BF16_TC,
     PREC_FP16_TC, PREC_SPLIT_BF16 (the precision form's tensor-core products
     of the 3D volume and lift terms).
     """

@@ -350,13 +350,22 @@ int tc_code(int precision) {
 }
 
 // Which 3D kernel a context runs: the split-TF32 tensor-core kernel
-// (DGH_PREC_FP32 up to N = 4, DGH_PREC_SPLIT_TF32), the BF16/FP16
-// tensor-core kernel (the precision form) or the FP32 CUDA-core kernel.
+// (DGH_PREC_SPLIT_TF32, and DGH_PREC_FP32 where it is the faster one), the
+// BF16/FP16 tensor-core kernel (the precision form) or the FP32 CUDA-core
+// kernel.  Measured on B300 (whole steps, tuned shapes): at N = 4 the
+// split-TF32 kernel is the faster one from about 80 k cells (10-18% per
+// step at 83 k - 384 k cells, 20% at 663 k), while on small meshes its
+// per-launch prologue (operator images, tensor memory) and its 128-cell
+// tiles, one CTA per SM, cost more than they save; at N = 1, 2, 3 the
+// CUDA-core kernel is faster at every size (1.2-2.2x per 3D launch at
+// 384 k cells), their contractions being too short for the tensor core to
+// pay for the operand conversion.
 enum Kern3 { K3_CUDA = 0, K3_TF32 = 1, K3_TC = 2 };
 constexpr int kMaxTf32Order = 4;   // largest N whose operators and stage fit one CTA's shared memory
-int kern3_of(int precision, int N) {
+constexpr int64_t kTf32MinCells = 65536;   // DGH_PREC_FP32 at N = 4: split TF32 from this many cells
+int kern3_of(int precision, int N, int64_t K) {
     if (precision == DGH_PREC_SPLIT_TF32) return K3_TF32;
-    if (precision == DGH_PREC_FP32) return N <= kMaxTf32Order ? K3_TF32 : K3_CUDA;
+    if (precision == DGH_PREC_FP32) return (N == kMaxTf32Order && K >= kTf32MinCells) ? K3_TF32 : K3_CUDA;
     if (precision == DGH_PREC_FP32_CUDA) return K3_CUDA;
     return K3_TC;
 }
@@ -468,7 +477,7 @@ struct Launch3 {
         const int64_t nblk = A.blk_end - A.blk_begin;
         if (nblk <= 0) return DGH_OK;
         A.max_tiles = int(std::min<int64_t>(nblk, int64_t(1) << 30));
-        const int kern = kern3_of(c->precision, N);
+        const int kern = kern3_of(c->precision, N, c->K);
         if (kern == K3_TF32) {   // split-TF32 tensor-core kernel: tiles of four 32-cell blocks, one CTA per SM
             if constexpr (N <= kMaxTf32Order) {
                 const int grid = (int)std::min<int64_t>((nblk + 3) / 4, c->grid3);
@@ -618,7 +627,7 @@ struct SetAttrs {
         cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         c->smem_optin = optin;
         int nb = 0;
-        const int kern = kern3_of(c->precision, N);
+        const int kern = kern3_of(c->precision, N, c->K);
         if (kern == K3_CUDA) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_stage<N>, Cfg3<N>::NW * 32, c->smem3);
         } else if (kern == K3_TF32) {
@@ -667,7 +676,7 @@ struct Shapes {
         const int sms = c->sms;
         const int per_sm = c->cta3_per_sm > 0 ? std::min(c->cta3_per_sm, std::max(c->occ3, 1)) : std::max(c->occ3, 1);
         const int sms3 = std::max(1, c->sms / std::max(c->sm3_div, 1));
-        const int64_t tiles3 = kern3_of(c->precision, N) == K3_CUDA ? c->K32 : (c->K32 + 3) / 4;
+        const int64_t tiles3 = kern3_of(c->precision, N, c->K) == K3_CUDA ? c->K32 : (c->K32 + 3) / 4;
         c->grid3 = (int)std::max<int64_t>(1, std::min<int64_t>(tiles3, (int64_t)per_sm * sms3));
         int nb2 = 0, nb1 = 0;
         if (c->T) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k2d_stage<N, true>, c->thr2, c->smem2);
@@ -1207,7 +1216,7 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
             (rc = upload(ctx, ctx->fperm3, fperm)) || (rc = upload(ctx, ctx->nslot3, nslot)) ||
             (rc = upload(ctx, ctx->cellv, cellv)) || (rc = upload(ctx, ctx->rst, rst)) || (rc = upload(ctx, ctx->ew, ew)))
             return fail(rc, "");
-        const int kern = kern3_of(ctx->precision, N);
+        const int kern = kern3_of(ctx->precision, N, ctx->K);
         if (kern == K3_TC && (rc = upload(ctx, ctx->tcops, tc_operator_images(T3, ctx->precision)))) return fail(rc, "");
         if (kern == K3_TF32 && (rc = upload(ctx, ctx->tcops, tf32_operator_images(T3)))) return fail(rc, "");
         std::vector<int> c2d(ctx->can2dev.begin(), ctx->can2dev.end());
@@ -2000,6 +2009,8 @@ int dgh_load_state(dgh_ctx *ctx, const void *buf, size_t size) {
 
 
 // ---------------------------------------------------------------- launch shapes and tuning
+static int dispatch_kern3(const dgh_ctx *c) { return kern3_of(c->precision, c->N, c->K); }
+
 int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *o) {
     return dgh_guarded(err_slot(ctx), [&]() -> int {
         if (!ctx || !o) return DGH_EINVAL;
@@ -2015,6 +2026,7 @@ int dgh_get_launch(const dgh_ctx *ctx, dgh_launch *o) {
         o->thr1 = ctx->thr1;
         o->sm3_div = ctx->sm3_div;
         o->split3 = ctx->split3;
+        o->kern3 = dispatch_kern3(ctx);
         return DGH_OK;
     });
 }

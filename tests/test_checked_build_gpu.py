@@ -28,8 +28,10 @@ CASES = [
     (2, 6, 4, (0,) * 6, 0),
     (2, 3, 12, (0,) * 6, 0),
     (2, 4, 2, (0,) * 6, dgh.PREC_SPLIT_BF16),
-    (2, 3, 2, (1, 0, 0, 1, 0, 1), dgh.PREC_FP32_CUDA),
-    (3, 4, 6, (0,) * 6, dgh.PREC_FP32_CUDA),
+    (2, 3, 2, (1, 0, 0, 1, 0, 1), dgh.PREC_SPLIT_TF32),
+    (3, 4, 6, (0,) * 6, dgh.PREC_SPLIT_TF32),
+    (2, 1, 1, (0,) * 6, dgh.PREC_SPLIT_TF32),
+    (2, 2, 3, (0, 0, 0, 0, 0, 1), dgh.PREC_SPLIT_TF32),
 ]
 
 

@@ -21,9 +21,10 @@ from paper_1610_05023_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
 FINAL_NORM_TOL = 5e-5   # 200-step run, relative to each field's final (small) norm
-# the plain FP32 path's two 3D kernels: split-TF32 tensor-core products
-# (PREC_FP32 up to N = 4) and FP32 CUDA cores (PREC_FP32_CUDA, every N)
-FP32_KERNELS = [dgh.PREC_FP32, dgh.PREC_FP32_CUDA]
+# the plain FP32 path's two 3D kernels, each forced: split-TF32 tensor-core
+# products (PREC_SPLIT_TF32, N <= 4; PREC_FP32 picks it at N = 4 on large
+# meshes) and FP32 CUDA cores (PREC_FP32_CUDA; PREC_FP32 on small meshes)
+FP32_KERNELS = [dgh.PREC_SPLIT_TF32, dgh.PREC_FP32_CUDA]
 
 
 def _levels(Y):
@@ -99,10 +100,12 @@ def test_nodes_match_oracle(N):
 
 
 # ---------------------------------------------------------------- small case
-def test_parity_small_gaussian_all_levels():
+@pytest.mark.parametrize("prec", FP32_KERNELS)
+def test_parity_small_gaussian_all_levels(prec):
     """4^3 hexes x 6 = 384 tets, N = 3, HABC P = 3, Gaussian exp(-r^2/0.2^2)
-    at the origin, 200 LSERK4 steps: the first workload, at full length."""
-    m, o, g, dt = make_pair(4, 3, 3, jitter=0.02, seed=1000)
+    at the origin, 200 LSERK4 steps: the first workload, at full length,
+    with each 3D kernel of the FP32 path."""
+    m, o, g, dt = make_pair(4, 3, 3, jitter=0.02, seed=1000, precision=prec)
     Y = o.gaussian_state([0, 0, 0], 0.2)
     g.init_gaussian([0, 0, 0], 0.2)
     nst = 200
@@ -144,8 +147,8 @@ def test_parity_orders_random_state(N, P, prec):
     """Random smooth-in-time start of every level (all auxiliary paths active
     from step 0), 10 steps, both FP32 3D kernels: <= 1e-5 per field (B300:
     <= 1.6e-6 split TF32, <= 2.3e-7 CUDA cores)."""
-    if prec == dgh.PREC_FP32_CUDA and N > 4:
-        pytest.skip("PREC_FP32 already runs the CUDA-core kernel at this order")
+    if prec == dgh.PREC_SPLIT_TF32 and N > 4:
+        pytest.skip("no split-TF32 kernel above N = 4")
     m, o, g, dt = make_pair(2, N, P, jitter=0.04, seed=7 + N, precision=prec)
     Y = o.zero_state()
     for i, k in enumerate(("q3", "q2", "q1")):
