@@ -166,6 +166,17 @@ int dgh_init_gaussian(dgh_ctx *ctx, const double x0[3], double width, double amp
 int dgh_set_state(dgh_ctx *ctx, int level, const double *in, size_t count);
 int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count);
 
+/* dgh_set_state / dgh_get_state with FP32 host arrays, the precision of the
+ * device state: the same canonical layout and counts (count = number of
+ * floats), half the bytes over the host link, and the values pass unchanged
+ * (a get after a set returns the floats that were set; dgh_set_state rounds
+ * FP64 input to the same floats).  Synchronising; the host array may be
+ * pageable or pinned (pinned memory transfers at the full link rate).
+ * DGH_EINVAL on a size mismatch or a NULL array, DGH_ECUDA on a failed
+ * transfer. */
+int dgh_set_state_f32(dgh_ctx *ctx, int level, const float *in, size_t count);
+int dgh_get_state_f32(dgh_ctx *ctx, int level, float *out, size_t count);
+
 /* Like dgh_get_state but levels 2 and 1 return the full auxiliary pressures
  * p_a = p*_a + (r^- + r^+) (eq. proc:pi00Star) and
  * p_ab = p*_ab + C_ba Q_A,a + C_ab Q_B,b (eq. proc:pij0Star). */

@@ -102,6 +102,8 @@ def load_library(path=LIB_PATH):
         "dgh_init_gaussian": (ctypes.c_int, [P, D, ctypes.c_double, ctypes.c_double]),
         "dgh_set_state": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
         "dgh_get_state": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
+        "dgh_set_state_f32": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+        "dgh_get_state_f32": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
         "dgh_get_fields": (ctypes.c_int, [P, ctypes.c_int, D, ctypes.c_size_t]),
         "dgh_set_time": (ctypes.c_int, [P, ctypes.c_double]),
         "dgh_init_fields": (ctypes.c_int, [P, D, ctypes.c_size_t]),
@@ -390,21 +392,34 @@ class Solver:
         self._check(self._lib.dgh_init_gaussian(self._h, _dptr(x), float(width), float(amp)))
 
     def set_state(self, level, arr):
+        """Time-stepped variables of a level (canonical layout).  A float32
+        array goes through dgh_set_state_f32 unchanged (half the bytes);
+        anything else is taken as float64 (dgh_set_state)."""
+        if isinstance(arr, np.ndarray) and arr.dtype == np.float32:
+            a = np.ascontiguousarray(arr)
+            if a.shape != self.shape(level):
+                raise ValueError("state shape %s != %s" % (a.shape, self.shape(level)))
+            self._check(self._lib.dgh_set_state_f32(self._h, level, _fptr(a), a.size))
+            return
         a = np.ascontiguousarray(arr, dtype=np.float64)
         if a.shape != self.shape(level):
             raise ValueError("state shape %s != %s" % (a.shape, self.shape(level)))
         self._check(self._lib.dgh_set_state(self._h, level, _dptr(a), a.size))
 
-    def get_state(self, level, out=None):
-        """Time-stepped variables of a level (canonical layout, FP64); out: an
-        optional C-contiguous float64 array of the right shape to fill (e.g. in
-        pinned host memory)."""
+    def get_state(self, level, out=None, dtype=np.float64):
+        """Time-stepped variables of a level (canonical layout); out: an
+        optional C-contiguous float64 or float32 array of the right shape to
+        fill (e.g. in pinned host memory), else a new array of dtype.  float32
+        reads the device state unchanged (dgh_get_state_f32)."""
         shape = self.shape(level)
         if out is None:
-            out = np.empty(shape)
-        elif out.dtype != np.float64 or out.shape != shape or not out.flags.c_contiguous:
-            raise ValueError("out must be a C-contiguous float64 array of shape %s" % (shape,))
-        self._check(self._lib.dgh_get_state(self._h, level, _dptr(out), out.size))
+            out = np.empty(shape, dtype=dtype)
+        if out.dtype not in (np.float64, np.float32) or out.shape != shape or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 or float32 array of shape %s" % (shape,))
+        if out.dtype == np.float32:
+            self._check(self._lib.dgh_get_state_f32(self._h, level, _fptr(out), out.size))
+        else:
+            self._check(self._lib.dgh_get_state(self._h, level, _dptr(out), out.size))
         return out
 
     def get_fields(self, level):

@@ -90,6 +90,8 @@ struct dgh_ctx {
     cudaStream_t side = nullptr;      // HABC chain stream (overlaps the interior 3D work)
     cudaEvent_t ev3d[5] = {}, ev2d[5] = {}, evjoin = nullptr;
     cudaEvent_t ev_order = nullptr;   // orders a caller's stream after the context's work (no-allocation energy)
+    void *xfer = nullptr;             // staging buffer of the 3D state transfers (grown on demand)
+    size_t xfer_bytes = 0;
     int C = 0;
     int M = 1;
     double dt = 0.0, t0 = 0.0;
@@ -802,9 +804,10 @@ float *level_ptr(dgh_ctx *c, int level, bool res) {
 }
 
 // State transfers convert and reorder on the device: the host copies plain
-// FP64 arrays in canonical order, the kernels below map them to and from the
-// FP32 device layouts (cell-interleaved for the 3D fields).
-__global__ void k_scatter3(const double *src, float *q, const int *c2d, int64_t n, int per) {
+// FP64 (or FP32) arrays in canonical order, the kernels below map them to and
+// from the FP32 device layouts (cell-interleaved for the 3D fields).
+template <typename H>
+__global__ void k_scatter3(const H *src, float *q, const int *c2d, int64_t n, int per) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = i / per;
         const int r = (int)(i % per);
@@ -813,12 +816,13 @@ __global__ void k_scatter3(const double *src, float *q, const int *c2d, int64_t 
     }
 }
 
-__global__ void k_gather3(const float *q, double *dst, const int *c2d, int64_t n, int per) {
+template <typename H>
+__global__ void k_gather3(const float *q, H *dst, const int *c2d, int64_t n, int per) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = i / per;
         const int r = (int)(i % per);
         const int64_t kd = c2d[k];
-        dst[i] = (double)q[((kd >> 5) * per + r) * 32 + (kd & 31)];
+        dst[i] = (H)q[((kd >> 5) * per + r) * 32 + (kd & 31)];
     }
 }
 
@@ -836,11 +840,36 @@ int xfer_grid(const dgh_ctx *c, size_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)((n + 255) / 256), int64_t(8) * std::max(c->sms, 1)));
 }
 
+// Device staging buffer of the 3D state transfers (canonical order on the
+// host, cell-interleaved on the device): kept by the context and grown when a
+// larger one is needed, so repeated transfers of a large state do not map
+// and unmap hundreds of MB on every call.  Callers synchronise the context's
+// stream before returning, so one buffer serves every transfer.
+cudaError_t xfer_buffer(dgh_ctx *c, size_t bytes, void **p) {
+    if (c->xfer_bytes < bytes) {
+        if (c->xfer) {
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return e;
+            cudaFree(c->xfer);
+            c->xfer = nullptr;
+            c->xfer_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&c->xfer, bytes);
+        if (e != cudaSuccess) {
+            c->xfer = nullptr;
+            return e;
+        }
+        c->xfer_bytes = bytes;
+    }
+    *p = c->xfer;
+    return cudaSuccess;
+}
+
 // device array dptr (level layout) -> host doubles out (canonical), n values
 int copy_out_level(dgh_ctx *c, int level, const float *dptr, double *out, size_t n) {
     if (n == 0) return DGH_OK;
     double *tmp = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&tmp, n * sizeof(double), c->stream);
+    cudaError_t e = xfer_buffer(c, n * sizeof(double), (void **)&tmp);
     if (e == cudaSuccess) {
         if (level == 3)
             k_gather3<<<xfer_grid(c, n), 256, 0, c->stream>>>(dptr, tmp, c->can2dev_d, (int64_t)n, 4 * c->Np);
@@ -848,7 +877,6 @@ int copy_out_level(dgh_ctx *c, int level, const float *dptr, double *out, size_t
             k_f2d<<<xfer_grid(c, n), 256, 0, c->stream>>>(dptr, tmp, (int64_t)n);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-        cudaFreeAsync(tmp, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
     if (e != cudaSuccess) {
@@ -862,7 +890,7 @@ int copy_out_level(dgh_ctx *c, int level, const float *dptr, double *out, size_t
 int copy_in_level(dgh_ctx *c, int level, const double *in, float *dptr, size_t n) {
     if (n == 0) return DGH_OK;
     double *tmp = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&tmp, n * sizeof(double), c->stream);
+    cudaError_t e = xfer_buffer(c, n * sizeof(double), (void **)&tmp);
     if (e == cudaSuccess) {
         e = cudaMemcpyAsync(tmp, in, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) {
@@ -872,11 +900,60 @@ int copy_in_level(dgh_ctx *c, int level, const double *in, float *dptr, size_t n
                 k_d2f<<<xfer_grid(c, n), 256, 0, c->stream>>>(tmp, dptr, (int64_t)n);
             e = cudaGetLastError();
         }
-        cudaFreeAsync(tmp, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
     if (e != cudaSuccess) {
         c->err = std::string("host to device transfer: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    return DGH_OK;
+}
+
+// FP32 host arrays (canonical order) in the device precision: half the bytes
+// of the FP64 transfers.  Levels 2 and 1 have the canonical layout on the
+// device as well and are copied straight into the state; level 3 goes
+// through the staging buffer and the layout scatter / gather.
+int copy_in_level_f32(dgh_ctx *c, int level, const float *in, float *dptr, size_t n) {
+    if (n == 0) return DGH_OK;
+    cudaError_t e = cudaSuccess;
+    if (level != 3) {
+        e = cudaMemcpyAsync(dptr, in, n * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    } else {
+        float *tmp = nullptr;
+        e = xfer_buffer(c, n * sizeof(float), (void **)&tmp);
+        if (e == cudaSuccess) {
+            e = cudaMemcpyAsync(tmp, in, n * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) {
+                k_scatter3<<<xfer_grid(c, n), 256, 0, c->stream>>>(tmp, dptr, c->can2dev_d, (int64_t)n, 4 * c->Np);
+                e = cudaGetLastError();
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("host to device transfer: ") + cudaGetErrorString(e);
+        return DGH_ECUDA;
+    }
+    return DGH_OK;
+}
+
+int copy_out_level_f32(dgh_ctx *c, int level, const float *dptr, float *out, size_t n) {
+    if (n == 0) return DGH_OK;
+    cudaError_t e = cudaSuccess;
+    if (level != 3) {
+        e = cudaMemcpyAsync(out, dptr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    } else {
+        float *tmp = nullptr;
+        e = xfer_buffer(c, n * sizeof(float), (void **)&tmp);
+        if (e == cudaSuccess) {
+            k_gather3<<<xfer_grid(c, n), 256, 0, c->stream>>>(dptr, tmp, c->can2dev_d, (int64_t)n, 4 * c->Np);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("device to host transfer: ") + cudaGetErrorString(e);
         return DGH_ECUDA;
     }
     return DGH_OK;
@@ -959,6 +1036,7 @@ void dgh_destroy(dgh_ctx *ctx) {
     if (ctx->ev_order) cudaEventDestroy(ctx->ev_order);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     for (auto &b : ctx->bufs) cudaFree(b.p);
+    if (ctx->xfer) cudaFree(ctx->xfer);
     delete ctx->sh;
     delete ctx;
 }
@@ -1676,6 +1754,36 @@ int dgh_get_state(dgh_ctx *ctx, int level, double *out, size_t count) {
             return DGH_EINVAL;
         }
         return copy_out_level(ctx, level, level_ptr(ctx, level, false), out, n);
+    });
+}
+
+int dgh_set_state_f32(dgh_ctx *ctx, int level, const float *in, size_t count) {
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        ApiRange nvtx_range("dgh_set_state_f32");
+        if (!ctx || (!in && count)) return DGH_EINVAL;
+        size_t n;
+        if (level_count(ctx, level, n) || n != count) {
+            ctx->err = "state size mismatch";
+            return DGH_EINVAL;
+        }
+        if (n == 0) return DGH_OK;
+        int rc = copy_in_level_f32(ctx, level, in, level_ptr(ctx, level, false), n);
+        if (rc) return rc;
+        ctx->dirty = true;
+        return DGH_OK;
+    });
+}
+
+int dgh_get_state_f32(dgh_ctx *ctx, int level, float *out, size_t count) {
+    return dgh_guarded(err_slot(ctx), [&]() -> int {
+        ApiRange nvtx_range("dgh_get_state_f32");
+        if (!ctx || (!out && count)) return DGH_EINVAL;
+        size_t n;
+        if (level_count(ctx, level, n) || n != count) {
+            ctx->err = "state size mismatch";
+            return DGH_EINVAL;
+        }
+        return copy_out_level_f32(ctx, level, level_ptr(ctx, level, false), out, n);
     });
 }
 
