@@ -143,6 +143,7 @@ struct dgh_ctx {
     int precision = DGH_PREC_FP32;    // arithmetic of the 3D contractions (DGH_PREC_*)
     uint8_t *tcops = nullptr;         // tensor-core operand images of D_r, D_s, D_t, LIFT (hi, then lo)
     unsigned long long *tile_ctr = nullptr;   // [16] block counters of the 3D launches of a step
+    unsigned *tile_ctr2 = nullptr;            // [4] tile counters of the 2D kernel: main chain, shadow chain
     size_t smem3 = 0, smem2 = 0, smem1 = 0, smem0 = 0;
     int smem_optin = 0;
     // learned closure (inference on this context's chain)
@@ -273,6 +274,7 @@ Args2 args2(dgh_ctx *c, int cur, bool update, bool shadow = false) {
         A.cP = h->cP;
         A.invM = 1.0f / float(h->M);
         A.P = h->P;
+        A.tile_ctr = c->tile_ctr2 + 2;
         return A;
     }
     Args2 A;
@@ -300,6 +302,7 @@ Args2 args2(dgh_ctx *c, int cur, bool update, bool shadow = false) {
     A.err = c->d_err;
     A.kcells = c->K32 * 32;
     A.nbfaces = c->Fb;
+    A.tile_ctr = c->tile_ctr2;
     return A;
 }
 
@@ -1431,7 +1434,8 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
         if ((rc = upload(ctx, ctx->corner, cor)) || (rc = upload(ctx, ctx->cornerZ, cz))) return fail(rc, "");
     }
     // ---------------------------------------------------------------- misc
-    if ((rc = dalloc(ctx, ctx->tile_ctr, 16)) || (rc = dalloc(ctx, ctx->d_time, 1)) || (rc = dalloc(ctx, ctx->d_step, 1)) ||
+    if ((rc = dalloc(ctx, ctx->tile_ctr, 16)) || (rc = dalloc(ctx, ctx->tile_ctr2, 4)) ||
+        (rc = dalloc(ctx, ctx->d_time, 1)) || (rc = dalloc(ctx, ctx->d_step, 1)) ||
         (rc = dalloc(ctx, ctx->srcvec, size_t(MAXSRC) * Np)) || (rc = dalloc(ctx, ctx->d_energy, 1)))
         return fail(rc, "");
     ctx->energy_blocks = 2 * 148;

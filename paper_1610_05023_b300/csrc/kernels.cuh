@@ -87,6 +87,7 @@ struct Args2 {
     int64_t T;
     int *err;               // device error word (checked build)
     int64_t kcells, nbfaces;   // bounds of tri_face cells and tri_bface (checked build)
+    unsigned *tile_ctr;     // [2]: tiles claimed, CTAs done; zero at launch, reset to zero by the last CTA
 };
 
 struct Args1 {
@@ -208,7 +209,7 @@ struct Smem2 {
         dt = 0;
         lt = dt + 2 * NP2 * NPP;
         cp = lt + NP2 * NEP;
-        q = cp + 2 * 16;                       // c_a and 1 / (1 + c_a), a < MAXP
+        q = cp + 2 * 16;                       // c_a (a < MAXP), the claimed tile, 1 / (1 + c_a)
         res = q + al(tile * P * F + 4);
         g = res + al(tile * P * F + 4);
         q0 = g + tile * GEO2;
@@ -257,11 +258,18 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
     }
     for (int i = tid; i < NE; i += nth) sfm[i] = A.fmask[i];
     const int64_t ntiles = (A.T + tile_tris - 1) / tile_tris;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // Tiles are claimed from a device counter: a CTA that finishes early takes
+    // the next tile, so the CTAs of an SM drift out of step (one loads while
+    // another computes) and the last tiles spread over all CTAs.
+    volatile unsigned *s_tile = reinterpret_cast<unsigned *>(scp + MAXP);   // a free word after c_a
+    for (;;) {
+        if (tid == 0) *s_tile = atomicAdd(&A.tile_ctr[0], 1u);
+        __syncthreads();   // also: the previous tile's shared-memory reads are done
+        const int64_t tile = *s_tile;
+        if (tile >= ntiles) break;
         const int64_t t0 = tile * tile_tris;
         const int nt = (int)((A.T - t0) < tile_tris ? (A.T - t0) : tile_tris);
         const int nitem = nt * P;
-        __syncthreads();
         // every global input of the tile in one phase: contiguous blocks by the
         // whole CTA, the exterior states at the edge nodes by each item thread
         const int shq = block_load_async(sqb, A.q, t0 * P * F, nitem * F, tid, nth);
@@ -446,6 +454,15 @@ __global__ void __launch_bounds__(256) k2d_stage(Args2 A, StageCoef sc, int tile
                 const float *qa = sq + s * F + n;
                 gt[s * TR] = isp ? qa[0] + s0[tt * NP2 + n] : ge[tt * GEO2] * qa[NP2] + ge[tt * GEO2 + 1] * qa[2 * NP2];
             }
+        }
+    }
+    // the last CTA to finish leaves the counters at zero for the next launch
+    // (every CTA has made its last claim before it counts itself done)
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&A.tile_ctr[1], 1u) == gridDim.x - 1) {
+            atomicExch(&A.tile_ctr[0], 0u);
+            atomicExch(&A.tile_ctr[1], 0u);
         }
     }
 }
