@@ -623,13 +623,19 @@ struct SetAttrs {
         // The limit is a property of the kernel, shared by every context of
         // this N (whatever P and tile): the 2D/1D kernels get the device's
         // opt-in maximum once, so that no context lowers it below another's need.
+        // A refused attribute would otherwise surface only later, as a failed
+        // launch: the first failure is reported here.
+        cudaError_t first = cudaSuccess;
+        auto chk = [&](cudaError_t r) {
+            if (r != cudaSuccess && first == cudaSuccess) first = r;
+        };
         int optin = 0;
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-        cudaFuncSetAttribute(k3d_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3);
-        cudaFuncSetAttribute(k2d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        cudaFuncSetAttribute(k2d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        cudaFuncSetAttribute(k1d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        chk(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        chk(cudaFuncSetAttribute(k3d_stage<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem3));
+        chk(cudaFuncSetAttribute(k2d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        chk(cudaFuncSetAttribute(k2d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        chk(cudaFuncSetAttribute(k1d_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        chk(cudaFuncSetAttribute(k1d_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         c->smem_optin = optin;
         int nb = 0;
         const int kern = kern3_of(c->precision, N, c->K);
@@ -638,7 +644,7 @@ struct SetAttrs {
         } else if (kern == K3_TF32) {
             if constexpr (N <= kMaxTf32Order) {
                 // one CTA per SM: it owns all 512 tensor-memory columns
-                cudaFuncSetAttribute(k3d_tf32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CfgTF<N>::SMEM);
+                chk(cudaFuncSetAttribute(k3d_tf32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CfgTF<N>::SMEM));
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3d_tf32<N>, CfgTF<N>::NTHR, CfgTF<N>::SMEM);
                 nb = std::min(nb, 1);
                 c->smem3 = CfgTF<N>::SMEM;
@@ -646,7 +652,7 @@ struct SetAttrs {
         } else {
             // one CTA owns TCOLS tensor-memory columns (512 per SM)
             auto occ = [&](auto kern, size_t smem, int tcols) {
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                chk(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, smem);
                 nb = std::min(nb, 512 / tcols);
                 c->smem3 = smem;
@@ -661,6 +667,11 @@ struct SetAttrs {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         c->occ3 = nb;
         c->sms = sms;
+        if (first != cudaSuccess) {
+            cudaGetLastError();   // a non-sticky error: clear it so that a later call is not blamed
+            c->err = std::string("kernel shared-memory attributes: ") + cudaGetErrorString(first);
+            return DGH_ECUDA;
+        }
         return DGH_OK;
     }
 };
@@ -1444,7 +1455,7 @@ static int build_context(dgh_ctx *ctx, const std::vector<int64_t> &parts) {
     ctx->thr2 = 128;
     ctx->tile2 = k2d_tile_max(P, ctx->thr2);
     ctx->tile1 = std::max(1, 256 / std::max(1, P * P * Np1));
-    dispatchN<SetAttrs>(N, ctx);
+    if ((rc = dispatchN<SetAttrs>(N, ctx))) return fail(rc, "");
     if ((rc = dispatchN<Shapes>(N, ctx))) return fail(DGH_EUNSUPPORTED, "2D/1D tile does not fit in shared memory");
     {
         int lo = 0, hi = 0;
